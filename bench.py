@@ -1,0 +1,328 @@
+#!/usr/bin/env python
+"""Throughput of VOLDOR's generalized-EM loop on one GB300 per rank.
+
+A step is one whole window: bootstrap (triangulation from the given T_1) and
+5 EM iterations (for each of the T frames: minimal groups, P3P, dense scoring
+of every hypothesis against every pixel, meanshift; then E-step smoothing,
+MIE depth sweep, rigidness update) on the seeded 1242x375, T=8 driving-like
+window with FP16 flows and 8192 pose hypotheses per frame.
+
+  value   Mpixel*frame EM updates per second = H*W*T*iters / step time, with the
+          flows already resident in HBM; whole job (sum over ranks of units
+          / max over ranks of time).
+  e2e     the same through the C ABI with host buffers: host->device copy of
+          the flows (pinned), bootstrap, EM, device->host read of poses, depth
+          and rigidness, all inside the timed step.
+
+Multi-GPU: windows are independent, so ranks run replicas on their own
+windows (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpixel·frame EM updates/s at 1242x375 T=8; learned vs plain time-to-equal-pose-error"
+UNIT = "Mpixel*frame/s"
+MUFU_PER_SM_PER_CLK = 16          # 4 SFU lanes per SM sub-partition, 4 sub-partitions
+ALGO_MUFU_PER_PAIR = 4            # rcp (projection), lg2 + ex2 ((x/alpha)^beta), lg2 (log(1+mu/rho))
+NOMINAL_SMS, NOMINAL_MAX_MHZ = 152, 2070.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--iters", type=int, default=5)
+    ap.add_argument("--hyps", type=int, default=8192)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def rank_info():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def workload(rank):
+    from paper_2104_06789_gb300 import synthetic
+    return synthetic.driving(seed=3000 + rank)
+
+
+def config_dict(w, args, world):
+    return {"workload": w.name, "width": w.W, "height": w.H, "T": w.T, "em_iters": args.iters,
+            "hyps_per_frame": args.hyps, "groups_per_frame": 2 * args.hyps, "flows": "fp16",
+            "focal_px": w.K[0], "windows_per_rank": 1, "parallelism": f"replicas x{world}",
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5], parts[6], parts[7], parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = np.array([r[0] for r in rows])
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[2 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(r[1] for r in rows)),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample of the same window
+# ---------------------------------------------------------------------------
+def oracle_sample(w, S, iters, n_score_hyps=4, n_groups=64):
+    """Times the FP64 oracle on parts of one EM iteration of window `w` and
+    scales each part linearly to the full configuration: dense scoring of
+    n_score_hyps hypotheses per frame (cost linear in S), collection of
+    n_groups minimal groups per frame (linear in the 2S groups drawn), and one
+    pass of the per-pixel steps (E-step, MIE sweep, rigidness). Returns
+    (Mpixel*frame/s, seconds of CPU work, description)."""
+    import oracle
+    oracle.build()
+    flows = w.flows.astype(np.float16).astype(np.float64)
+    ow = oracle.OracleWindow(flows, w.K, S=n_groups * 4, G=n_groups, inv_depth_min=w.inv_depth_range[0],
+                             inv_depth_max=w.inv_depth_range[1])
+    ow.bootstrap(w.poses[0])
+    t0 = time.perf_counter()
+    for t in range(1, w.T + 1):
+        R = np.tile(w.poses[t - 1][:3, :3], (n_score_hyps, 1, 1))
+        tv = np.tile(w.poses[t - 1][:3, 3], (n_score_hyps, 1))
+        ow.score(t, R, tv)
+    t_score = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for t in range(1, w.T + 1):
+        ow.collect_hypotheses(0, t)
+    t_groups = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    em = ow.emissions()
+    q = ow.smooth(0, em)
+    ow.mie_sweep(0, q)
+    ow.rigidness()
+    t_pixel = time.perf_counter() - t0
+    per_iter = t_score * (S / n_score_hyps) + t_groups * (2 * S / n_groups) + t_pixel
+    value = w.H * w.W * w.T / per_iter / 1e6
+    desc = (f"one EM iteration of the same window, scaled: dense scoring timed on {n_score_hyps} hypotheses x "
+            f"{w.T} frames (x{S // n_score_hyps}), minimal groups on {n_groups} per frame "
+            f"(x{2 * S // n_groups}), E-step + MIE sweep + rigidness timed whole; "
+            f"{per_iter:.1f} s/iteration extrapolated from {t_score + t_groups + t_pixel:.1f} s measured")
+    return value, t_score + t_groups + t_pixel, desc
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank, _, world = rank_info()
+    if rank != 0:
+        return
+    w = workload(0)
+    steps = []
+    desc = ""
+    for i in range(args.warmup + args.steps):
+        v, secs, desc = oracle_sample(w, args.hyps, args.iters, n_score_hyps=2, n_groups=32)
+        if i >= args.warmup:
+            steps.append(v)
+    value = float(np.mean(steps))
+    units = w.H * w.W * w.T * args.iters
+    ms = units / (value * 1e6) * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(w, args, 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    from paper_2104_06789_gb300 import build, voldor
+
+    rank, local_rank, world = rank_info()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    w = workload(rank)
+    flows16 = np.ascontiguousarray(w.flows.astype(np.float16))
+    stream = torch.cuda.Stream()
+    params = voldor.default_params(hyps_per_frame=args.hyps, groups_per_frame=2 * args.hyps,
+                                   inv_depth_min=w.inv_depth_range[0], inv_depth_max=w.inv_depth_range[1],
+                                   seed=0, window_id=rank)
+    dev_flows = torch.from_numpy(flows16).to(f"cuda:{local_rank}")
+    torch.cuda.synchronize()
+    win = voldor.Window(dev_flows, w.K, params, stream=stream)
+    win.enable_timing(True)
+    T1 = w.poses[0]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local_rank}")
+
+    def step():
+        win.bootstrap(T1)
+        win.em_step(args.iters)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    score_ms, score_pairs = [], []
+    launches0 = win.kernel_launches()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(i & 0xFF)          # L2 flush between timed steps (not timed)
+            evs[i][0].record(stream)
+            step()
+            evs[i][1].record(stream)
+            ms, pairs = win.get_score_times()
+            score_ms.extend(ms.tolist())
+            score_pairs.extend(pairs.tolist())
+        torch.cuda.synchronize()
+    launches = win.kernel_launches() - launches0
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    if dist is not None:
+        tt = torch.tensor([total_ms], device=f"cuda:{local_rank}", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+        dist.barrier()
+    torch.cuda.synchronize()
+    units_per_step = w.H * w.W * w.T * args.iters
+    value = world * units_per_step * args.steps / (total_ms / 1e3) / 1e6
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pinned = torch.from_numpy(flows16).pin_memory()
+        host_win = voldor.Window(pinned, w.K, params, stream=stream)
+        P = np.zeros((w.T, 4, 4))
+        for i in range(args.warmup + args.steps):
+            if i == args.warmup:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+            host_win.set_flows(pinned)
+            host_win.bootstrap(T1)
+            host_win.em_step(args.iters)
+            P, D, Wm = host_win.get_pose_depth_rigidness()
+        e2e_s = time.perf_counter() - t0
+        e2e_s_max = e2e_s
+        if dist is not None:
+            tt = torch.tensor([e2e_s], device=f"cuda:{local_rank}", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s_max = float(tt.item())
+        host_win.destroy()
+        e2e = {"value": world * units_per_step * args.steps / e2e_s_max / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(flows16.nbytes),
+               "d2h_bytes_per_step": int(w.T * 16 * 8 + w.H * w.W * 4 + w.T * w.H * w.W * 4)}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    props = torch.cuda.get_device_properties(local_rank)
+    sms = props.multi_processor_count
+    peak = sms * MUFU_PER_SM_PER_CLK * NOMINAL_MAX_MHZ * 1e6 / 1e12      # T MUFU-ops/s
+    score_ms = np.array(score_ms)
+    score_pairs = np.array(score_pairs, dtype=np.float64)
+    achieved = float(np.mean(ALGO_MUFU_PER_PAIR * score_pairs / (score_ms * 1e-3)) / 1e12) if len(score_ms) else None
+    roofline = {"kernel": "k_score (dense hypothesis scoring)", "bound": "alu", "achieved": achieved,
+                "peak": peak, "unit": "T MUFU-op/s (4 algorithmic SFU ops per hypothesis-pixel pair)",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "peak_source": f"{sms} SMs x {MUFU_PER_SM_PER_CLK} SFU ops/clk x {NOMINAL_MAX_MHZ:.0f} MHz",
+                "launches_timed": int(len(score_ms)), "mean_launch_ms": float(score_ms.mean()) if len(score_ms) else None,
+                "share_of_step": float(score_ms.sum() / total_ms) if len(score_ms) else None}
+
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        v, secs, desc = oracle_sample(w, args.hyps, args.iters)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict(w, args, world), "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    win.destroy()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * voldor.h -- C ABI of the GB300 (sm_103a) implementation of VOLDOR's
+ * generalized-EM inference (Min, Yang, Dunn, "VOLDOR: Visual Odometry from
+ * Log-logistic Dense Optical flow Residuals", CVPR 2020).
+ *
+ * Problem statement (Sec. 3, Table 1): the input is a window of T dense optical
+ * flow fields X_1..X_T, X_t mapping image I_{t-1} to I_t and living on the
+ * pixel grid of I_{t-1}; the outputs are the relative camera poses
+ * T_1..T_T (T_t maps camera t-1 coordinates to camera t: x_t = R x_{t-1} + t),
+ * the depth map theta of I_0 (z-depth) and the rigidness maps W_1..W_T
+ * (per-pixel inlier probabilities on the grid of I_0).
+ *
+ * Conventions shared by every call:
+ *  - All calls are extern "C", take plain pointers and sizes, and return a
+ *    voldor_status. Nothing aborts, traps or throws across the ABI.
+ *  - Images are row-major: pixel j = y * width + x, x = column, y = row.
+ *  - Flow stacks are [T][H][W][2] with (u, v) interleaved, float32
+ *    (VOLDOR_FLOW_F32) or IEEE binary16 (VOLDOR_FLOW_F16).
+ *  - Poses are row-major 4x4 float64 matrices, T of them back to back.
+ *  - A context owns all of its device memory and works on the CUDA stream given
+ *    at creation (NULL = the legacy default stream). Host-side outputs are
+ *    caller-owned; calls that return host data synchronise that stream.
+ *  - One context must not be used from two host threads at once; separate
+ *    contexts are independent.
+ *  - After VOLDOR_ERR_CUDA the context is poisoned: every later call on it
+ *    returns VOLDOR_ERR_CUDA until it is destroyed.
+ */
+#ifndef VOLDOR_H
+#define VOLDOR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct voldor_ctx voldor_ctx;
+
+typedef enum {
+    VOLDOR_OK = 0,
+    VOLDOR_ERR_INVALID_ARG = 1,      /* bad size, NULL pointer, NaN/Inf input, unknown enum */
+    VOLDOR_ERR_CUDA = 2,             /* a CUDA runtime call failed; context poisoned */
+    VOLDOR_ERR_OOM = 3,              /* device allocation failed */
+    VOLDOR_ERR_NOT_BOOTSTRAPPED = 4, /* em_step / stage call before voldor_bootstrap or set_state */
+    VOLDOR_ERR_DEGENERATE = 5,       /* a frame had no weighted pose hypothesis and kept its pose */
+    VOLDOR_ERR_TIMEOUT = 6,          /* a bounded device-side wait gave up */
+    VOLDOR_ERR_INTERNAL = 7          /* a device-side consistency check failed */
+} voldor_status;
+
+enum { VOLDOR_FLOW_F32 = 0, VOLDOR_FLOW_F16 = 1 };
+enum { VOLDOR_BOOT_GIVEN_POSE = 0 };
+
+typedef struct { double fx, fy, cx, cy; } voldor_intrinsics;
+
+/* Method parameters. voldor_default_params() fills the paper's values
+ * (Sec. 6.1: a1 = 0.01, a2 = 0.09, b1 = -0.0022, b2 = 1.0, lambda = 0.15,
+ * gamma = 0.9, Sigma = diag(0.1 x3 translation, 0.004 x3 rotation)) and the
+ * numerical guards of this implementation. */
+typedef struct {
+    double a1, a2, b1, b2;        /* Fisk parameter functions A, B (Eqs. 5-6) */
+    double lambda_;               /* adaptive uniform outlier density (Eq. 7) */
+    double gamma;                 /* HMM transition probability (Eq. 11) */
+    double sigma_t, sigma_r;      /* pose kernel covariance diagonal, variances (Eq. 18) */
+    double inv_depth_min, inv_depth_max;  /* depth samples: uniform in inverse depth */
+    double x_min, x_max;          /* floor and cap of the squared flow residual, px^2 */
+    double beta_min;              /* floor of the Fisk shape B */
+    double ms_tol;                /* meanshift stops when |dx| < ms_tol */
+    int hyps_per_frame;           /* S: P3P pose hypotheses kept per frame (<= 65536) */
+    int groups_per_frame;         /* G: minimal groups drawn per frame (>= 1, <= 262144) */
+    int ms_max_iter;              /* meanshift iteration cap */
+    int pad_;
+    uint64_t seed, window_id;     /* Philox4x64-10 key of the window */
+} voldor_params;
+
+void voldor_default_params(voldor_params* p);
+
+/* Creates a context for a W x H image and T flows, copies the flow stack into
+ * library-owned device memory (converting nothing: F16 stays F16, F32 stays
+ * F32) and allocates the state (theta, W, smoothed W, poses, scratch).
+ *  flows:           T*H*W*2 elements of flow_dtype; host memory when
+ *                   flows_on_device == 0, device memory of the current device
+ *                   otherwise. Copied on `cuda_stream` (a cudaStream_t or NULL).
+ *  params:          NULL = voldor_default_params().
+ * Errors: INVALID_ARG (width < 2, height < 2, T < 1 or > 16, non-finite or
+ * non-positive focal lengths, invalid params), OOM, CUDA. *out is NULL on
+ * error. */
+voldor_status voldor_init_window(voldor_ctx** out, int width, int height, int T,
+                                 const voldor_intrinsics* K, const voldor_params* params,
+                                 const void* flows, int flow_dtype, int flows_on_device,
+                                 void* cuda_stream);
+
+/* Replaces the flow stack of an existing context (same size and dtype), with
+ * no allocation. The state is unchanged; call voldor_bootstrap next. */
+voldor_status voldor_set_flows(voldor_ctx* ctx, const void* flows, int flows_on_device);
+
+/* Bootstrap (Table 1, first three lines): W := 1 everywhere; T_1 := the given
+ * pose (mode VOLDOR_BOOT_GIVEN_POSE, Sec. 5.3 "from previous estimates");
+ * T_t := T_1 for t >= 2 (used only when a frame has no weighted hypothesis);
+ * theta by two-view triangulation of x_j + X_1^j along the ray of pixel j
+ * (least squares over the two projection equations, inverse depth clamped to
+ * [inv_depth_min, inv_depth_max], non-positive depth sent to the far end).
+ * Resets the iteration counter k to 0. T1_rowmajor_4x4: host, 16 doubles. */
+voldor_status voldor_bootstrap(voldor_ctx* ctx, int mode, const double* T1_rowmajor_4x4);
+
+/* Runs n_iters iterations of the VOLDOR loop (Table 1): for t = 1..T the pose
+ * update of Eq. 19 (Philox-drawn minimal groups, P3P, dense scoring of every
+ * hypothesis against every pixel, weighted meanshift on se(3)); the E-step
+ * with forward-backward smoothing of W (Eqs. 11-14); the MIE depth update by
+ * sampling-propagation along directed 1-D chains (Eq. 10, Fig. 5); the
+ * unsmoothed W update. Iteration k uses sweep direction
+ * [left->right, top->bottom, right->left, bottom->top][k mod 4] and smoothing
+ * along rows for even k mod 4, columns otherwise. Asynchronous on the
+ * context's stream except when it returns DEGENERATE or TIMEOUT, which it
+ * learns by synchronising at the end. Errors: NOT_BOOTSTRAPPED, CUDA,
+ * DEGENERATE (state stays valid), TIMEOUT. */
+voldor_status voldor_em_step(voldor_ctx* ctx, int n_iters);
+
+/* Copies the outputs into caller-owned host buffers and synchronises.
+ *  poses: T*16 doubles (T_t row-major 4x4), depth: H*W floats, rigidness:
+ *  T*H*W floats (unsmoothed W_t). Any pointer may be NULL to skip it. */
+voldor_status voldor_get_pose_depth_rigidness(voldor_ctx* ctx, double* poses, float* depth,
+                                              float* rigidness);
+
+/* Releases the context (NULL is ignored). */
+void voldor_destroy(voldor_ctx* ctx);
+
+const char* voldor_status_string(voldor_status s);
+
+/* ---------------------------------------------------------------------------
+ * Stage calls: the building blocks voldor_em_step runs, exposed for
+ * checkpoint/resume and for parity tests that feed the same state to both
+ * sides. All are asynchronous on the context's stream unless stated.
+ * ------------------------------------------------------------------------- */
+
+/* Overwrites the state: poses (T*16 doubles, host), depth (H*W floats, host),
+ * rigidness (T*H*W floats, host), iteration counter k. NULL leaves that part
+ * unchanged. Marks the context bootstrapped. Synchronises. */
+voldor_status voldor_set_state(voldor_ctx* ctx, const double* poses, const float* depth,
+                               const float* rigidness, int iteration);
+
+/* Pose update of frame t (1..T) at iteration k (Eqs. 15-19): Philox groups,
+ * P3P (FP64), dense scores L_h (FP32 per pair, FP64 sums), meanshift seeded at
+ * argmax L_h. Results stay readable through voldor_get_buffer. */
+voldor_status voldor_pose_update(voldor_ctx* ctx, int k, int t);
+
+/* Dense scoring alone (the spec kernel): scores n caller-given
+ * hypotheses of frame t against every valid pixel under the current state.
+ *  R: n*9 doubles row-major, tv: n*3 doubles (host); L: n doubles (host).
+ *  L_h = sum_j [pi_{t-1}(theta_j) valid] W_t^j log(rho/(rho+mu)), the Eq. 10
+ *  criterion with T_t = h. Synchronises. n <= hyps_per_frame. */
+voldor_status voldor_score_hypotheses(voldor_ctx* ctx, int t, int n, const double* R,
+                                      const double* tv, double* L);
+
+/* E-step of iteration k: emissions rho/(rho+mu) at the current theta and
+ * poses, then forward-backward along rows (k mod 4 in {0, 2}) or columns
+ * (Eqs. 11-14) into the smoothed map (buffer VOLDOR_BUF_SMOOTHED). */
+voldor_status voldor_rigidness_smooth(voldor_ctx* ctx, int k);
+
+/* M-step of iteration k: MIE sampling-propagation sweep (Eq. 10, Fig. 5)
+ * using the smoothed map; updates theta and the label map. */
+voldor_status voldor_depth_update(voldor_ctx* ctx, int k);
+
+/* Unsmoothed W update (Table 1, last line): W_t^j = rho/(rho+mu). */
+voldor_status voldor_rigidness_update(voldor_ctx* ctx);
+
+/* Readable / writable device buffers (host copies; synchronise). */
+enum {
+    VOLDOR_BUF_SMOOTHED = 0,  /* float [T][H][W] smoothed q(W_t^j = 1), read/write */
+    VOLDOR_BUF_LABELS = 1,    /* uint8 [H][W] last sweep's choice: 0 prev, 1 nbr, 2 smp */
+    VOLDOR_BUF_HYPS = 2,      /* double [S][12] last pose update's hypotheses: R (9), t (3) */
+    VOLDOR_BUF_HYP_INFO = 3,  /* int64 [S][2] group index, solution slot */
+    VOLDOR_BUF_HYP_WEIGHT = 4,/* double [S] group weight (product of W) */
+    VOLDOR_BUF_SCORES = 5,    /* double [S] dense scores L_h */
+    VOLDOR_BUF_POSE_INFO = 6, /* int32 [4] n_hyp, seed index, meanshift steps, status */
+    VOLDOR_BUF_DEPTH_SAMPLES = 7, /* float [H][W] last sweep's smp candidates */
+    VOLDOR_BUF_HYPS_F32 = 8   /* float [S][12] scoring form of the hypotheses */
+};
+voldor_status voldor_get_buffer(voldor_ctx* ctx, int which, void* host, size_t bytes);
+voldor_status voldor_set_buffer(voldor_ctx* ctx, int which, const void* host, size_t bytes);
+
+/* Per-launch device times (ms, CUDA events on the context's stream) of the
+ * dense-scoring kernel during the last voldor_em_step, in launch order, and
+ * (if `pairs` is not NULL) the (hypothesis, pixel) pairs each launch scored.
+ * Writes min(count, max) values; *count gets the number recorded. Requires
+ * timing to be enabled with voldor_enable_timing(ctx, 1) before the step.
+ * Synchronises. */
+voldor_status voldor_enable_timing(voldor_ctx* ctx, int on);
+voldor_status voldor_get_score_times(voldor_ctx* ctx, float* ms, long long* pairs, int max, int* count);
+
+/* Number of library kernels enqueued on this context so far (graph replays
+ * count every kernel node of the graph). */
+long long voldor_kernel_launches(const voldor_ctx* ctx);
+
+/* Device memory held by the context, bytes. */
+size_t voldor_device_bytes(const voldor_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VOLDOR_H */

@@ -1,0 +1,622 @@
+// Pose-update kernels (Sec. 5.2): Monte-Carlo minimal groups drawn with
+// Philox4x64-10, FP64 P3P per group (Eq. 17), order-preserving hypothesis
+// collection with se(3) logarithms, and the weighted Gaussian meanshift of
+// Eqs. 18-19 on a thread-block cluster.
+#include <cooperative_groups.h>
+
+#include "voldor_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace vd {
+
+// ---------------------------------------------------------------------------
+// FP64 helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double d3dot(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+__device__ __forceinline__ void d3cross(const double* a, const double* b, double* o)
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+__device__ __forceinline__ bool d3unit(double* a)
+{
+    const double n = sqrt(d3dot(a, a));
+    if (!(n > 0.0)) return false;
+    const double r = 1.0 / n;
+    a[0] *= r; a[1] *= r; a[2] *= r;
+    return true;
+}
+
+__device__ __forceinline__ double horner4(const double* c, double x)
+{
+    return (((c[4] * x + c[3]) * x + c[2]) * x + c[1]) * x + c[0];
+}
+
+// x = J^-1 F through the adjugate; false if J is singular.
+__device__ __forceinline__ bool solve3x3(const double* J, const double* F, double* x)
+{
+    const double c00 = J[4] * J[8] - J[5] * J[7];
+    const double c01 = J[5] * J[6] - J[3] * J[8];
+    const double c02 = J[3] * J[7] - J[4] * J[6];
+    const double det = J[0] * c00 + J[1] * c01 + J[2] * c02;
+    if (!(fabs(det) > 0.0)) return false;
+    const double c10 = J[2] * J[7] - J[1] * J[8];
+    const double c11 = J[0] * J[8] - J[2] * J[6];
+    const double c12 = J[1] * J[6] - J[0] * J[7];
+    const double c20 = J[1] * J[5] - J[2] * J[4];
+    const double c21 = J[2] * J[3] - J[0] * J[5];
+    const double c22 = J[0] * J[4] - J[1] * J[3];
+    const double id = 1.0 / det;
+    x[0] = (c00 * F[0] + c10 * F[1] + c20 * F[2]) * id;
+    x[1] = (c01 * F[0] + c11 * F[1] + c21 * F[2]) * id;
+    x[2] = (c02 * F[0] + c12 * F[1] + c22 * F[2]) * id;
+    return true;
+}
+
+// Largest real root of m^3 + A m^2 + B m + C (Cardano or trigonometric form),
+// refined by Newton steps.
+__device__ double cubic_max_root(double A, double B, double C)
+{
+    const double A3 = A / 3.0;
+    const double pp = B - A * A3;                         // y^3 + pp y + qq = 0, m = y - A/3
+    const double qq = 2.0 * A3 * A3 * A3 - A3 * B + C;
+    double y;
+    const double disc = 0.25 * qq * qq + pp * pp * pp / 27.0;
+    if (disc > 0.0) {
+        const double sq = sqrt(disc);
+        y = cbrt(-0.5 * qq + sq) + cbrt(-0.5 * qq - sq);
+    } else {
+        const double r = sqrt(fmax(-pp / 3.0, 0.0));
+        double arg = (r > 0.0) ? (-0.5 * qq) / (r * r * r) : 0.0;
+        arg = fmin(1.0, fmax(-1.0, arg));
+        y = 2.0 * r * cos(acos(arg) / 3.0);
+    }
+    double m = y - A3;
+    for (int it = 0; it < 4; ++it) {
+        const double f = ((m + A) * m + B) * m + C;
+        const double df = (3.0 * m + 2.0 * A) * m + B;
+        if (!(fabs(df) > 0.0)) break;
+        const double mn = m - f / df;
+        const double fn = ((mn + A) * mn + B) * mn + C;
+        if (!(fabs(fn) < fabs(f))) break;
+        m = mn;
+    }
+    return m;
+}
+
+// Real roots of a quartic (ascending coefficients) by Ferrari's method, each
+// polished by Newton steps on the quartic. Returns the count (<= 4).
+__device__ int quartic_real_roots(const double* a, double* roots)
+{
+    double amax = 0.0;
+    for (int i = 0; i < 4; ++i) amax = fmax(amax, fabs(a[i]));
+    if (!(fabs(a[4]) > 1e-14 * amax)) return 0;           // degenerate group
+    const double b = a[3] / a[4], c = a[2] / a[4], d = a[1] / a[4], e = a[0] / a[4];
+    const double bb = b * b;
+    const double P = c - 0.375 * bb;
+    const double Q = d - 0.5 * b * c + 0.125 * bb * b;
+    const double R = e - 0.25 * b * d + 0.0625 * bb * c - (3.0 / 256.0) * bb * bb;
+    double y[4];
+    int n = 0;
+    // y^4 + P y^2 + Q y + R = (y^2 + P/2 + m)^2 - 2m (y - Q/(4m))^2 for the
+    // resolvent root m of m^3 + P m^2 + (P^2/4 - R) m - Q^2/8 = 0
+    const double m = cubic_max_root(P, 0.25 * P * P - R, -0.125 * Q * Q);
+    if (m > 1e-300 && fabs(Q) > 0.0) {
+        const double sr = sqrt(2.0 * m);
+        const double h = Q / (2.0 * sr);
+        const double c1 = 0.5 * P + m - h, c2 = 0.5 * P + m + h;
+        const double D1 = 2.0 * m - 4.0 * c1, D2 = 2.0 * m - 4.0 * c2;
+        if (D1 >= 0.0) { const double q = sqrt(D1); y[n++] = 0.5 * (-sr + q); y[n++] = 0.5 * (-sr - q); }
+        if (D2 >= 0.0) { const double q = sqrt(D2); y[n++] = 0.5 * (sr + q); y[n++] = 0.5 * (sr - q); }
+    } else {
+        const double D = P * P - 4.0 * R;                 // biquadratic y^4 + P y^2 + R
+        if (D >= 0.0) {
+            const double z1 = 0.5 * (-P + sqrt(D)), z2 = 0.5 * (-P - sqrt(D));
+            if (z1 >= 0.0) { y[n++] = sqrt(z1); y[n++] = -sqrt(z1); }
+            if (z2 >= 0.0) { y[n++] = sqrt(z2); y[n++] = -sqrt(z2); }
+        }
+    }
+    for (int i = 0; i < n; ++i) {
+        double x = y[i] - 0.25 * b;
+        for (int it = 0; it < 3; ++it) {
+            const double f = horner4(a, x);
+            const double df = ((4.0 * a[4] * x + 3.0 * a[3]) * x + 2.0 * a[2]) * x + a[1];
+            if (!(fabs(df) > 0.0)) break;
+            const double xn = x - f / df;
+            if (!(fabs(horner4(a, xn)) < fabs(f))) break;
+            x = xn;
+        }
+        roots[i] = x;
+    }
+    return n;
+}
+
+// Frame spanned by a triangle: f1 along q3 - q1, f3 normal, f2 = f3 x f1
+// (columns of F, row-major).
+__device__ __forceinline__ bool tri_frame(const double* q1, const double* q2, const double* q3, double* F)
+{
+    double f1[3] = {q3[0] - q1[0], q3[1] - q1[1], q3[2] - q1[2]};
+    const double e[3] = {q2[0] - q1[0], q2[1] - q1[1], q2[2] - q1[2]};
+    if (!d3unit(f1)) return false;
+    double f3[3];
+    d3cross(f1, e, f3);
+    if (!d3unit(f3)) return false;
+    double f2[3];
+    d3cross(f3, f1, f2);
+    for (int r = 0; r < 3; ++r) { F[r * 3 + 0] = f1[r]; F[r * 3 + 1] = f2[r]; F[r * 3 + 2] = f3[r]; }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// P3P. With s_i the distances along the unit bearings b_i, the law of cosines
+// gives s_i^2 + s_k^2 - 2 c_ik s_i s_k = d_ik^2. With u = s2/s1, v = s3/s1:
+//   (ii)/(i):  v^2 - 2 c13 v = g(u),  g(u) = (d13/d12)(1 + u^2 - 2 c12 u) - 1
+//   with (iii): v D(u) = N(u),  N = d23 (1 + g) - d13 (u^2 + g),
+//                               D = 2 d13 (c13 - c23 u)
+//   and N^2 - 2 c13 N D - g D^2 = 0 is a quartic in u.
+// Each root is polished by Newton steps on the three distance equations; the
+// pose maps the world triangle onto the camera triangle. Solutions with all
+// s_i > 0 come back sorted by s1.
+// ---------------------------------------------------------------------------
+struct P3PSol {
+    double s1;
+    double Rt[12];
+};
+
+__device__ int p3p_solve(const double P[3][3], const double b[3][3], P3PSol* out)
+{
+    double e12[3], e13[3], e23[3];
+    for (int i = 0; i < 3; ++i) { e12[i] = P[0][i] - P[1][i]; e13[i] = P[0][i] - P[2][i]; e23[i] = P[1][i] - P[2][i]; }
+    const double d12 = d3dot(e12, e12), d13 = d3dot(e13, e13), d23 = d3dot(e23, e23);
+    if (!(d12 > 0.0 && d13 > 0.0 && d23 > 0.0)) return 0;
+    const double c12 = d3dot(b[0], b[1]), c13 = d3dot(b[0], b[2]), c23 = d3dot(b[1], b[2]);
+    const double K2 = d13 / d12;
+    const double g[3] = {K2 - 1.0, -2.0 * K2 * c12, K2};
+    const double N[3] = {(d23 - d13) * g[0] + d23, (d23 - d13) * g[1], (d23 - d13) * g[2] - d13};
+    const double D[2] = {2.0 * d13 * c13, -2.0 * d13 * c23};
+    double Q[5] = {0, 0, 0, 0, 0};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Q[i + j] += N[i] * N[j];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 2; ++j) Q[i + j] -= 2.0 * c13 * N[i] * D[j];
+    const double DD[3] = {D[0] * D[0], 2.0 * D[0] * D[1], D[1] * D[1]};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Q[i + j] -= g[i] * DD[j];
+    double us[4];
+    const int nr = quartic_real_roots(Q, us);
+    int n = 0;
+    for (int r = 0; r < nr; ++r) {
+        const double u = us[r];
+        if (!(u > 0.0)) continue;
+        const double Du = D[0] + D[1] * u;
+        if (Du == 0.0) continue;
+        const double v = (N[0] + (N[1] + N[2] * u) * u) / Du;
+        const double q1 = 1.0 + u * u - 2.0 * c12 * u;
+        if (!(q1 > 0.0)) continue;
+        double s[3];
+        s[0] = sqrt(d12 / q1);
+        s[1] = u * s[0];
+        s[2] = v * s[0];
+        if (!(s[0] > 0.0 && s[1] > 0.0 && s[2] > 0.0) || !isfinite(s[2])) continue;
+        for (int it = 0; it < 5; ++it) {
+            const double F[3] = {s[0] * s[0] + s[1] * s[1] - 2.0 * c12 * s[0] * s[1] - d12,
+                                 s[0] * s[0] + s[2] * s[2] - 2.0 * c13 * s[0] * s[2] - d13,
+                                 s[1] * s[1] + s[2] * s[2] - 2.0 * c23 * s[1] * s[2] - d23};
+            const double J[9] = {2.0 * (s[0] - c12 * s[1]), 2.0 * (s[1] - c12 * s[0]), 0.0,
+                                 2.0 * (s[0] - c13 * s[2]), 0.0, 2.0 * (s[2] - c13 * s[0]),
+                                 0.0, 2.0 * (s[1] - c23 * s[2]), 2.0 * (s[2] - c23 * s[1])};
+            double ds[3];
+            if (!solve3x3(J, F, ds)) break;
+            const double nsv[3] = {s[0] - ds[0], s[1] - ds[1], s[2] - ds[2]};
+            const double G0 = nsv[0] * nsv[0] + nsv[1] * nsv[1] - 2.0 * c12 * nsv[0] * nsv[1] - d12;
+            const double G1 = nsv[0] * nsv[0] + nsv[2] * nsv[2] - 2.0 * c13 * nsv[0] * nsv[2] - d13;
+            const double G2 = nsv[1] * nsv[1] + nsv[2] * nsv[2] - 2.0 * c23 * nsv[1] * nsv[2] - d23;
+            if (!(fabs(G0) + fabs(G1) + fabs(G2) < fabs(F[0]) + fabs(F[1]) + fabs(F[2]))) break;
+            s[0] = nsv[0]; s[1] = nsv[1]; s[2] = nsv[2];
+        }
+        if (!(s[0] > 0.0 && s[1] > 0.0 && s[2] > 0.0)) continue;
+        double Qc[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int c = 0; c < 3; ++c) Qc[i][c] = s[i] * b[i][c];
+        double Fw[9], Fc[9];
+        if (!tri_frame(P[0], P[1], P[2], Fw) || !tri_frame(Qc[0], Qc[1], Qc[2], Fc)) continue;
+        P3PSol sol;
+        sol.s1 = s[0];
+        double cw[3], cc[3];
+        for (int c = 0; c < 3; ++c) {
+            cw[c] = (P[0][c] + P[1][c] + P[2][c]) / 3.0;
+            cc[c] = (Qc[0][c] + Qc[1][c] + Qc[2][c]) / 3.0;
+        }
+        for (int r0 = 0; r0 < 3; ++r0) {
+            for (int c = 0; c < 3; ++c)
+                sol.Rt[r0 * 4 + c] = Fc[r0 * 3 + 0] * Fw[c * 3 + 0] + Fc[r0 * 3 + 1] * Fw[c * 3 + 1] + Fc[r0 * 3 + 2] * Fw[c * 3 + 2];
+        }
+        for (int r0 = 0; r0 < 3; ++r0)
+            sol.Rt[r0 * 4 + 3] = cc[r0] - (sol.Rt[r0 * 4 + 0] * cw[0] + sol.Rt[r0 * 4 + 1] * cw[1] + sol.Rt[r0 * 4 + 2] * cw[2]);
+        // insertion by s1
+        int pos = n;
+        while (pos > 0 && out[pos - 1].s1 > sol.s1) { out[pos] = out[pos - 1]; --pos; }
+        out[pos] = sol;
+        ++n;
+    }
+    return n;
+}
+
+// ---------------------------------------------------------------------------
+// Groups of frame t at iteration k: Philox(index g, t, k, POSE) gives
+// j_i = hi64(r_i * N); P3P on the 3D points in camera t-1 and the bearings of
+// the flow targets pi_{t-1} + X_t in camera t, all in FP64.
+// ---------------------------------------------------------------------------
+__device__ bool group_point(const DevParams& p, const DevState& s, const double* C, int t, long long j, double* P,
+                            double* bear)
+{
+    const int x = (int)(j % p.W), y = (int)(j / p.W);
+    const double th = (double)s.theta[j];
+    const double d[3] = {((double)x - p.cxd) / p.fxd, ((double)y - p.cyd) / p.fyd, 1.0};
+    double u, v;
+    if (t == 1) {
+        P[0] = th * d[0]; P[1] = th * d[1]; P[2] = th;
+        u = x; v = y;
+        if (!(P[2] > 0.0)) return false;
+    } else {
+        const double X = th * d[0], Y = th * d[1], Z = th;
+        for (int r = 0; r < 3; ++r) P[r] = C[r * 4 + 0] * X + C[r * 4 + 1] * Y + C[r * 4 + 2] * Z + C[r * 4 + 3];
+        if (!(P[2] > 0.0)) return false;
+        u = p.fxd * P[0] / P[2] + p.cxd;
+        v = p.fyd * P[1] / P[2] + p.cyd;
+    }
+    if (!(u >= 0.0 && u <= (double)(p.W - 1) && v >= 0.0 && v <= (double)(p.H - 1))) return false;
+    const int x0 = min((int)floor(u), p.W - 2), y0 = min((int)floor(v), p.H - 2);
+    const double ax = u - x0, ay = v - y0;
+    const size_t base = (size_t)(t - 1) * p.N + (size_t)y0 * p.W + x0;
+    const float2 f00 = load_flow(s.flows, p.flow_f16, base), f10 = load_flow(s.flows, p.flow_f16, base + 1);
+    const float2 f01 = load_flow(s.flows, p.flow_f16, base + p.W), f11 = load_flow(s.flows, p.flow_f16, base + p.W + 1);
+    const double w00 = (1 - ax) * (1 - ay), w10 = ax * (1 - ay), w01 = (1 - ax) * ay, w11 = ax * ay;
+    const double fu = w00 * f00.x + w10 * f10.x + w01 * f01.x + w11 * f11.x;
+    const double fv = w00 * f00.y + w10 * f10.y + w01 * f01.y + w11 * f11.y;
+    bear[0] = (u + fu - p.cxd) / p.fxd;
+    bear[1] = (v + fv - p.cyd) / p.fyd;
+    bear[2] = 1.0;
+    return d3unit(bear);
+}
+
+__global__ void k_p3p_groups(DevParams p, DevState s, int t)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= p.G) return;
+    const int k = *s.iter;
+    const U64x4 r = philox4x64_10((uint64_t)g, (uint64_t)t, (uint64_t)k, (uint64_t)kStreamPose, p.seed, p.window_id);
+    long long j[3];
+    for (int i = 0; i < 3; ++i) j[i] = (long long)__umul64hi(r.v[i], (uint64_t)p.N);
+    int n = 0;
+    double weight = 0.0;
+    P3PSol sols[kMaxSols];
+    if (j[0] != j[1] && j[0] != j[2] && j[1] != j[2]) {
+        const double* C = s.cum + 12 * (t - 1);
+        double P[3][3], b[3][3];
+        bool ok = true;
+        weight = 1.0;
+        for (int i = 0; i < 3 && ok; ++i) {
+            ok = group_point(p, s, C, t, j[i], P[i], b[i]);
+            weight *= (double)s.wmap[(size_t)(t - 1) * p.N + j[i]];
+        }
+        if (ok) n = p3p_solve(P, b, sols);
+        if (!ok) weight = 0.0;
+    }
+    s.grp_count[g] = n;
+    s.grp_weight[g] = weight;
+    double* o = s.grp_sols + (size_t)g * kMaxSols * 12;
+    for (int i = 0; i < n; ++i)
+        for (int q = 0; q < 12; ++q) o[i * 12 + q] = sols[i].Rt[q];
+}
+
+void launch_p3p_groups(const DevParams& p, const DevState& s, int t, cudaStream_t st)
+{
+    k_p3p_groups<<<(p.G + 127) / 128, 128, 0, st>>>(p, s, t);
+}
+
+// ---------------------------------------------------------------------------
+// Hypothesis collection: exclusive scan of the group solution counts (one
+// block), then one thread per group writes its solutions h = offset + i < S
+// with their scoring form and se(3) logarithm.
+// ---------------------------------------------------------------------------
+__global__ void k_hyp_scan(DevParams p, DevState s)
+{
+    __shared__ int wsum[32];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int seg = (p.G + nt - 1) / nt;
+    const int g0 = min(tid * seg, p.G), g1 = min(g0 + seg, p.G);
+    int local = 0;
+    for (int g = g0; g < g1; ++g) local += s.grp_count[g];
+    // block exclusive scan of `local`
+    const int lane = tid & 31, warp = tid >> 5;
+    int incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = nt >> 5;
+        int v = lane < nw ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        if (lane < nw) wsum[lane] = v;
+    }
+    __syncthreads();
+    int off = incl - local + (warp > 0 ? wsum[warp - 1] : 0);
+    for (int g = g0; g < g1; ++g) {
+        s.grp_offset[g] = off;
+        off += s.grp_count[g];
+    }
+    if (tid == nt - 1) *s.n_hyp = min(off, p.S);
+}
+
+// se(3) logarithm through the unit quaternion of R (Shepperd's selection):
+// phi = 2 atan2(|v|, w) v/|v|, rho = V^-1 t with
+// V^-1 = I - Phi/2 + (1 - (th/2) cot(th/2)) / th^2 Phi^2.
+__device__ void se3_log_quat(const double* Rt, double* p6)
+{
+    const double R00 = Rt[0], R01 = Rt[1], R02 = Rt[2];
+    const double R10 = Rt[4], R11 = Rt[5], R12 = Rt[6];
+    const double R20 = Rt[8], R21 = Rt[9], R22 = Rt[10];
+    const double tr = R00 + R11 + R22;
+    double w, x, y, z;
+    if (tr >= R00 && tr >= R11 && tr >= R22) {
+        w = 0.5 * sqrt(1.0 + tr);
+        const double f = 0.25 / w;
+        x = (R21 - R12) * f; y = (R02 - R20) * f; z = (R10 - R01) * f;
+    } else if (R00 >= R11 && R00 >= R22) {
+        x = 0.5 * sqrt(1.0 + R00 - R11 - R22);
+        const double f = 0.25 / x;
+        w = (R21 - R12) * f; y = (R01 + R10) * f; z = (R02 + R20) * f;
+    } else if (R11 >= R22) {
+        y = 0.5 * sqrt(1.0 - R00 + R11 - R22);
+        const double f = 0.25 / y;
+        w = (R02 - R20) * f; x = (R01 + R10) * f; z = (R12 + R21) * f;
+    } else {
+        z = 0.5 * sqrt(1.0 - R00 - R11 + R22);
+        const double f = 0.25 / z;
+        w = (R10 - R01) * f; x = (R02 + R20) * f; y = (R12 + R21) * f;
+    }
+    if (w < 0.0) { w = -w; x = -x; y = -y; z = -z; }
+    const double vn = sqrt(x * x + y * y + z * z);
+    const double th = 2.0 * atan2(vn, w);
+    const double scale = (vn > 1e-8) ? th / vn : (2.0 / w) * (1.0 - vn * vn / (3.0 * w * w));
+    const double phi[3] = {scale * x, scale * y, scale * z};
+    double c2;
+    if (th < 1e-4) c2 = 1.0 / 12.0 + th * th / 720.0;
+    else c2 = (1.0 - 0.5 * th * cos(0.5 * th) / sin(0.5 * th)) / (th * th);
+    const double t[3] = {Rt[3], Rt[7], Rt[11]};
+    double a[3], b[3];
+    d3cross(phi, t, a);
+    d3cross(phi, a, b);
+    for (int i = 0; i < 3; ++i) p6[i] = t[i] - 0.5 * a[i] + c2 * b[i];
+    p6[3] = phi[0]; p6[4] = phi[1]; p6[5] = phi[2];
+}
+
+// se(3) exponential: R = I + A Phi + B Phi^2, t = rho + B phi x rho + C phi x (phi x rho).
+__device__ void se3_exp_vec(const double* p6, double* Rt)
+{
+    const double* rho = p6;
+    const double* phi = p6 + 3;
+    const double th2 = d3dot(phi, phi), th = sqrt(th2);
+    double A, B, C;
+    if (th < 1e-4) {
+        A = 1.0 - th2 / 6.0 + th2 * th2 / 120.0;
+        B = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
+        C = 1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0;
+    } else {
+        A = sin(th) / th;
+        B = (1.0 - cos(th)) / th2;
+        C = (th - sin(th)) / (th2 * th);
+    }
+    const double wx = phi[0], wy = phi[1], wz = phi[2];
+    // Phi^2 = phi phi^T - th^2 I
+    Rt[0] = 1.0 + B * (wx * wx - th2); Rt[1] = -A * wz + B * wx * wy;       Rt[2] = A * wy + B * wx * wz;
+    Rt[4] = A * wz + B * wx * wy;       Rt[5] = 1.0 + B * (wy * wy - th2); Rt[6] = -A * wx + B * wy * wz;
+    Rt[8] = -A * wy + B * wx * wz;      Rt[9] = A * wx + B * wy * wz;       Rt[10] = 1.0 + B * (wz * wz - th2);
+    double a[3], b[3];
+    d3cross(phi, rho, a);
+    d3cross(phi, a, b);
+    Rt[3] = rho[0] + B * a[0] + C * b[0];
+    Rt[7] = rho[1] + B * a[1] + C * b[1];
+    Rt[11] = rho[2] + B * a[2] + C * b[2];
+}
+
+__global__ void k_hyp_write(DevParams p, DevState s)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= p.G) return;
+    const int cnt = s.grp_count[g], off = s.grp_offset[g];
+    const double q = p.fyd / p.fxd;
+    const double sc[3] = {1.0, q, 1.0};
+    for (int i = 0; i < cnt; ++i) {
+        const int h = off + i;
+        if (h >= p.S) break;
+        const double* Rt = s.grp_sols + ((size_t)g * kMaxSols + i) * 12;
+        double* oR = s.hyp_Rt + (size_t)h * 12;
+        for (int r = 0; r < 3; ++r) {
+            for (int c = 0; c < 3; ++c) oR[r * 3 + c] = Rt[r * 4 + c];
+            oR[9 + r] = Rt[r * 4 + 3];
+        }
+        float* f = s.hyp_f32 + (size_t)h * 12;
+        for (int r = 0; r < 3; ++r) {
+            for (int c = 0; c < 3; ++c) f[r * 3 + c] = (float)(sc[r] * (Rt[r * 4 + c] - (r == c ? 1.0 : 0.0)) / sc[c]);
+            f[9 + r] = (float)(sc[r] * Rt[r * 4 + 3]);
+        }
+        se3_log_quat(Rt, s.hyp_p + (size_t)h * 6);
+        s.hyp_w[h] = s.grp_weight[g];
+        s.hyp_info[(size_t)h * 2 + 0] = g;
+        s.hyp_info[(size_t)h * 2 + 1] = i;
+    }
+}
+
+void launch_hyp_collect(const DevParams& p, const DevState& s, cudaStream_t st)
+{
+    k_hyp_scan<<<1, 1024, 0, st>>>(p, s);
+    k_hyp_write<<<(p.G + 127) / 128, 128, 0, st>>>(p, s);
+}
+
+// Scoring form of caller-given hypotheses already copied to hyp_Rt.
+__global__ void k_hyp_from_rt(DevParams p, DevState s, int n)
+{
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h == 0) *s.n_hyp = n;
+    if (h >= n) return;
+    const double q = p.fyd / p.fxd;
+    const double sc[3] = {1.0, q, 1.0};
+    const double* R = s.hyp_Rt + (size_t)h * 12;
+    float* f = s.hyp_f32 + (size_t)h * 12;
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) f[r * 3 + c] = (float)(sc[r] * (R[r * 3 + c] - (r == c ? 1.0 : 0.0)) / sc[c]);
+        f[9 + r] = (float)(sc[r] * R[9 + r]);
+    }
+}
+
+void score_hyps_from_host(const DevParams& p, const DevState& s, int n, cudaStream_t st)
+{
+    k_hyp_from_rt<<<(n + 127) / 128 + 1, 128, 0, st>>>(p, s, n);
+}
+
+// ---------------------------------------------------------------------------
+// Meanshift (Eqs. 18-19): x <- sum_h w_h K(x - p_h) p_h / sum_h w_h K(x - p_h),
+// K(d) = exp(-d^T Sigma^-1 d / 2), seeded at argmax_h L_h (lowest index on
+// ties), on a cluster of kMeanshiftCtas CTAs. Distances and sums in FP64; the
+// Gaussian itself in FP32. Every CTA reduces the cluster's partial sums in the
+// same order, so all take the same steps; partial buffers alternate by
+// iteration parity so one cluster barrier per step suffices.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __cluster_dims__(kMeanshiftCtas, 1, 1) __launch_bounds__(kMeanshiftThreads, 1)
+k_meanshift(DevParams p, DevState s, int t)
+{
+    cg::cluster_group cluster = cg::this_cluster();
+    const unsigned rank = cluster.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    __shared__ double wred[32][8];
+    __shared__ double part[2][8];
+    __shared__ double xs[8];
+    __shared__ double bval[32];
+    __shared__ int bidx[32];
+    __shared__ int flag;
+    const int n = *s.n_hyp;
+    if (n == 0) {
+        if (rank == 0 && tid == 0) {
+            s.status[0] = 0; s.status[1] = -1; s.status[2] = 0; s.status[3] += 1;
+        }
+        return;   // uniform over the cluster: every CTA reads the same n
+    }
+    // argmax of L (lowest index on ties; NaN never wins)
+    double bv = -INFINITY;
+    int bi = 0x7fffffff;
+    for (int h = tid; h < n; h += blockDim.x) {
+        const double v = s.scores[h];
+        if (v > bv || (v == bv && h < bi)) { bv = v; bi = h; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { bval[warp] = bv; bidx[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+        double v = bval[0];
+        int i = bidx[0];
+        for (int w = 1; w < nwarp; ++w)
+            if (bval[w] > v || (bval[w] == v && bidx[w] < i)) { v = bval[w]; i = bidx[w]; }
+        if (i == 0x7fffffff) i = 0;
+        for (int c = 0; c < 6; ++c) xs[c] = s.hyp_p[(size_t)i * 6 + c];
+        bidx[0] = i;
+        flag = 0;
+    }
+    __syncthreads();
+    const int seed = bidx[0];
+    const double ivt = 1.0 / p.sigma_t, ivr = 1.0 / p.sigma_r;
+    int it = 0;
+    bool degenerate = false;
+    for (; it < p.ms_max_iter; ++it) {
+        double x[6];
+        for (int c = 0; c < 6; ++c) x[c] = xs[c];
+        double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int h = rank * blockDim.x + tid; h < n; h += kMeanshiftCtas * blockDim.x) {
+            const double* ph = s.hyp_p + (size_t)h * 6;
+            double m = 0.0;
+            for (int c = 0; c < 6; ++c) {
+                const double d = x[c] - ph[c];
+                m += d * d * (c < 3 ? ivt : ivr);
+            }
+            const double kw = s.hyp_w[h] * (double)expf(-0.5f * (float)m);
+            if (!(kw > 0.0)) continue;     // zero weight (or a non-finite hypothesis) adds nothing
+            acc[0] += kw;
+            for (int c = 0; c < 6; ++c) acc[1 + c] += kw * ph[c];
+        }
+        for (int c = 0; c < 7; ++c) acc[c] = warp_sum_d(acc[c]);
+        if (lane == 0)
+            for (int c = 0; c < 7; ++c) wred[warp][c] = acc[c];
+        __syncthreads();
+        const int buf = it & 1;
+        if (tid < 7) {
+            double v = 0.0;
+            for (int w = 0; w < nwarp; ++w) v += wred[w][tid];
+            part[buf][tid] = v;
+        }
+        cluster.sync();
+        if (tid == 0) {
+            double tot[7] = {0, 0, 0, 0, 0, 0, 0};
+            for (unsigned r = 0; r < kMeanshiftCtas; ++r) {
+                const double* pr = cluster.map_shared_rank(&part[buf][0], r);
+                for (int c = 0; c < 7; ++c) tot[c] += pr[c];
+            }
+            if (!(tot[0] > 0.0)) {
+                flag = (it == 0) ? 2 : 1;
+            } else {
+                double step = 0.0;
+                for (int c = 0; c < 6; ++c) {
+                    const double xn = tot[1 + c] / tot[0];
+                    step += (xn - xs[c]) * (xn - xs[c]);
+                    xs[c] = xn;
+                }
+                flag = (sqrt(step) < p.ms_tol) ? 1 : 0;
+            }
+        }
+        __syncthreads();
+        const int f = flag;
+        __syncthreads();
+        if (f == 2) { degenerate = true; break; }
+        if (f == 1) { ++it; break; }
+    }
+    cluster.sync();   // no CTA leaves while another may still read its partials
+    if (rank == 0 && tid == 0) {
+        s.status[0] = n;
+        s.status[1] = seed;
+        s.status[2] = it;
+        if (degenerate) {
+            s.status[3] += 1;
+        } else {
+            double x[6];
+            for (int c = 0; c < 6; ++c) x[c] = xs[c];
+            se3_exp_vec(x, s.poses + 12 * (t - 1));
+        }
+    }
+}
+
+void launch_meanshift(const DevParams& p, const DevState& s, int t, cudaStream_t st)
+{
+    k_meanshift<<<kMeanshiftCtas, kMeanshiftThreads, 0, st>>>(p, s, t);
+}
+
+}  // namespace vd

@@ -1,0 +1,171 @@
+// Dense hypothesis scoring: for every P3P hypothesis h of frame t,
+//   L_h = sum_j W_t^j log[rho_j(h) / (rho_j(h) + mu_j)]
+// over the pixels whose pi_{t-1} is valid -- the MIE criterion of Eq. 10 with
+// the pose as the free variable. Arithmetic-bound on the SFU (MUFU) and FP32
+// pipes.
+//
+// Per pair, with the pixel record (xb, yb2, w, ut, vt, beta, beta_k, Cp, wq)
+// and the hypothesis in scaled form (E, tt):
+//   a    = E (xb, yb2, 1) + tt w                (camera-t point / z_{t-1} - p)
+//   r_u  = (a_x - xb a_z) / (1 + a_z) - ut      (residual / fx, no cancellation
+//   r_v  = (a_y - yb2 a_z) / (1 + a_z) - vt      against the pixel position)
+//   xs   = r_u^2 + r_v^2                        (squared residual / fx^2)
+//   s    = beta log2(xs) + beta_k               (log2 of (x/alpha)^beta)
+//   r    = Cp xs (2^s + 2 + 2^-s)               (= mu / rho, Eqs. 3-4, 7)
+//   ell  = -log1p(r)
+// MUFU work: rcp, lg2, ex2, ex2, lg2 (for r >= 1/8); log1p(r) for r < 1/8 is
+// a Taylor polynomial on the FMA pipe, because lg2 near 1 has only absolute
+// accuracy. Sums: FP32 over 32 pixels, then FP64.
+#include "voldor_internal.cuh"
+
+namespace vd {
+
+__device__ __forceinline__ float mufu_rcp(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float mufu_lg2(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float mufu_ex2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+struct HypF {
+    float e0, e1, e2, e3, e4, e5, e6, e7, e8, t0, t1, t2;
+};
+
+// log1p(r) for r >= 0: Taylor series to r^9 below 1/8, ln2 * lg2(1 + r) above.
+__device__ __forceinline__ float log1p_pos(float r)
+{
+    float s = fmaf(r, -1.f / 9.f, 1.f / 8.f);
+    s = fmaf(r, s, -1.f / 7.f);
+    s = fmaf(r, s, 1.f / 6.f);
+    s = fmaf(r, s, -1.f / 5.f);
+    s = fmaf(r, s, 1.f / 4.f);
+    s = fmaf(r, s, -1.f / 3.f);
+    s = fmaf(r, s, 1.f / 2.f);
+    s = fmaf(r, -s, 1.f);
+    const float small = r * s;
+    const float big = 0.69314718055994531f * mufu_lg2(1.f + r);
+    return r < 0.125f ? small : big;
+}
+
+// -ell = log1p(mu/rho) of one (hypothesis, pixel) pair; ln 2 behind camera t.
+__device__ __forceinline__ float pair_term(const HypF& h, const float4 a, const float4 b, float xs_min, float xs_max)
+{
+    const float xb = a.x, yb2 = a.y, w = a.z, ut = a.w;
+    const float vt = b.x, beta = b.y, beta_k = b.z, Cp = b.w;
+    const float ax = fmaf(h.e0, xb, fmaf(h.e1, yb2, fmaf(h.t0, w, h.e2)));
+    const float ay = fmaf(h.e3, xb, fmaf(h.e4, yb2, fmaf(h.t1, w, h.e5)));
+    const float az = fmaf(h.e6, xb, fmaf(h.e7, yb2, fmaf(h.t2, w, h.e8)));
+    const float den = 1.f + az;
+    const float rd = mufu_rcp(den);
+    const float ru = fmaf(fmaf(-xb, az, ax), rd, -ut);
+    const float rv = fmaf(fmaf(-yb2, az, ay), rd, -vt);
+    const float xs = fminf(fmaxf(fmaf(ru, ru, rv * rv), xs_min), xs_max);
+    const float sg = fabsf(fmaf(beta, mufu_lg2(xs), beta_k));
+    const float r = Cp * xs * (mufu_ex2(sg) + (2.f + mufu_ex2(-sg)));
+    const float v = log1p_pos(r);
+    return den > 0.f ? v : 0.69314718055994531f;
+}
+
+__global__ void __launch_bounds__(kScoreThreads, 2) k_score(DevParams p, DevState s, int log_idx)
+{
+    const int n_hyp = *s.n_hyp;
+    const int n_pix = *s.pix_count;
+    if (log_idx >= 0 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        s.score_log[2 * log_idx] = n_hyp;
+        s.score_log[2 * log_idx + 1] = n_pix;
+    }
+    const int tile0 = blockIdx.x * kScoreHypsPerBlock;
+    if (tile0 >= n_hyp) return;
+    const int chunk = blockIdx.y, n_chunks = gridDim.y;
+    const long long lo = (long long)n_pix * chunk / n_chunks;
+    const long long hi = (long long)n_pix * (chunk + 1) / n_chunks;
+
+    HypF hy[kScoreHypsPerThread];
+#pragma unroll
+    for (int i = 0; i < kScoreHypsPerThread; ++i) {
+        const int h = tile0 + i * kScoreThreads + threadIdx.x;
+        const float* f = s.hyp_f32 + (size_t)min(h, n_hyp - 1) * 12;
+        hy[i] = HypF{f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7], f[8], f[9], f[10], f[11]};
+    }
+    double acc[kScoreHypsPerThread];
+    float facc[kScoreHypsPerThread];
+#pragma unroll
+    for (int i = 0; i < kScoreHypsPerThread; ++i) { acc[i] = 0.0; facc[i] = 0.f; }
+
+    const float xs_min = p.xs_min, xs_max = p.xs_max;
+    const float4* __restrict__ pix = reinterpret_cast<const float4*>(s.pix);
+    long long j = lo;
+    while (j < hi) {
+        const long long jend = min(hi, j + 32);
+        for (; j < jend; ++j) {
+            const float4 a = __ldg(pix + 3 * j);
+            const float4 b = __ldg(pix + 3 * j + 1);
+            const float wq = __ldg(reinterpret_cast<const float*>(pix + 3 * j + 2));
+#pragma unroll
+            for (int i = 0; i < kScoreHypsPerThread; ++i) facc[i] = fmaf(wq, pair_term(hy[i], a, b, xs_min, xs_max), facc[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < kScoreHypsPerThread; ++i) { acc[i] += (double)facc[i]; facc[i] = 0.f; }
+    }
+    const int S = p.S;
+#pragma unroll
+    for (int i = 0; i < kScoreHypsPerThread; ++i) {
+        const int h = tile0 + i * kScoreThreads + threadIdx.x;
+        if (h < n_hyp) s.partial[(size_t)chunk * S + h] = -acc[i];
+    }
+}
+
+// L_h = sum over chunks, in chunk order.
+__global__ void k_score_reduce(DevParams p, DevState s)
+{
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= *s.n_hyp) return;
+    double v = 0.0;
+    for (int c = 0; c < s.n_chunks; ++c) v += s.partial[(size_t)c * p.S + h];
+    s.scores[h] = v;
+}
+
+static int g_num_sms = 0;
+
+int score_chunks(int S, int N)
+{
+    if (g_num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || g_num_sms <= 0)
+            g_num_sms = 152;
+    }
+    const int tiles = (S + kScoreHypsPerBlock - 1) / kScoreHypsPerBlock;
+    // two resident blocks per SM, two waves
+    int chunks = (g_num_sms * 2 * 2 + tiles - 1) / tiles;
+    if (chunks > N) chunks = N;
+    return chunks < 1 ? 1 : chunks;
+}
+
+void launch_score(const DevParams& p, const DevState& s, int log_idx, cudaStream_t st)
+{
+    const int tiles = (p.S + kScoreHypsPerBlock - 1) / kScoreHypsPerBlock;
+    dim3 grid(tiles, s.n_chunks);
+    k_score<<<grid, kScoreThreads, 0, st>>>(p, s, log_idx < kScoreLogMax ? log_idx : -1);
+}
+
+void launch_score_reduce(const DevParams& p, const DevState& s, cudaStream_t st)
+{
+    k_score_reduce<<<(p.S + 255) / 256, 256, 0, st>>>(p, s);
+}
+
+}  // namespace vd

@@ -1,0 +1,599 @@
+// C ABI of the VOLDOR library (declared in include/voldor.h): context
+// lifetime, argument checking, the Table 1 iteration as a sequence of kernel
+// launches, CUDA-graph capture of voldor_em_step, and host readout.
+#include <cmath>
+#include <cstdio>
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "voldor_internal.cuh"
+
+using namespace vd;
+
+struct voldor_ctx {
+    int W = 0, H = 0, T = 0, N = 0, flow_dtype = 0;
+    voldor_params params{};
+    voldor_intrinsics K{};
+    DevParams dp{};
+    DevState ds{};
+    cudaStream_t stream = nullptr;
+    void* arena = nullptr;
+    size_t arena_bytes = 0;
+    size_t flows_bytes = 0;
+    int* flag_dev = nullptr;          // inside the arena: non-finite counter
+    bool bootstrapped = false;
+    bool poisoned = false;
+    bool timing = false;
+    std::map<long long, cudaGraphExec_t> graphs;
+    std::vector<cudaEvent_t> events;  // start/stop pairs of the timed graph
+    int last_pairs = 0;
+    int graph_pairs = 0;
+    std::map<long long, long long> graph_kernels;   // kernel nodes per cached graph
+    long long launches = 0;                          // kernels enqueued so far
+};
+
+namespace {
+
+const voldor_status kCuda = VOLDOR_ERR_CUDA;
+
+bool cuda_ok(voldor_ctx* c, cudaError_t e)
+{
+    if (e == cudaSuccess) return true;
+    if (c) c->poisoned = true;
+    return false;
+}
+
+bool launched(voldor_ctx* c) { return cuda_ok(c, cudaGetLastError()); }
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+bool params_ok(const voldor_params& p)
+{
+    if (!finite_pos(p.a1) || !std::isfinite(p.a2) || !std::isfinite(p.b1) || !std::isfinite(p.b2)) return false;
+    if (!std::isfinite(p.lambda_) || p.lambda_ < 0.0) return false;
+    if (!(p.gamma > 0.0 && p.gamma < 1.0)) return false;
+    if (!finite_pos(p.sigma_t) || !finite_pos(p.sigma_r)) return false;
+    if (!finite_pos(p.inv_depth_min) || !finite_pos(p.inv_depth_max) || !(p.inv_depth_max > p.inv_depth_min)) return false;
+    if (!finite_pos(p.x_min) || !finite_pos(p.x_max) || !(p.x_max > p.x_min)) return false;
+    if (!finite_pos(p.beta_min) || !(p.ms_tol >= 0.0) || !std::isfinite(p.ms_tol)) return false;
+    if (p.hyps_per_frame < 1 || p.hyps_per_frame > 65536) return false;
+    if (p.groups_per_frame < 1 || p.groups_per_frame > 262144) return false;
+    if (p.ms_max_iter < 1 || p.ms_max_iter > 100000) return false;
+    return true;
+}
+
+DevParams make_dev_params(const voldor_ctx& c)
+{
+    const voldor_params& p = c.params;
+    DevParams d{};
+    d.W = c.W; d.H = c.H; d.T = c.T; d.N = c.N;
+    d.S = p.hyps_per_frame; d.G = p.groups_per_frame; d.ms_max_iter = p.ms_max_iter;
+    d.flow_f16 = c.flow_dtype == VOLDOR_FLOW_F16;
+    d.fx = (float)c.K.fx; d.fy = (float)c.K.fy; d.cx = (float)c.K.cx; d.cy = (float)c.K.cy;
+    d.inv_fx = (float)(1.0 / c.K.fx); d.inv_fy = (float)(1.0 / c.K.fy);
+    d.fy_over_fx = (float)(c.K.fy / c.K.fx);
+    d.log2_a1 = (float)std::log2(p.a1);
+    d.a2_log2e = (float)(p.a2 / std::log(2.0));
+    d.b1 = (float)p.b1; d.b2 = (float)p.b2; d.beta_min = (float)p.beta_min;
+    d.lambda2 = (float)(p.lambda_ * p.lambda_);
+    d.x_min = (float)p.x_min; d.x_max = (float)p.x_max;
+    d.xs_min = (float)(p.x_min / (c.K.fx * c.K.fx));
+    d.xs_max = (float)(p.x_max / (c.K.fx * c.K.fx));
+    d.log2_fx2 = (float)std::log2(c.K.fx * c.K.fx);
+    d.inv_depth_min = (float)p.inv_depth_min; d.inv_depth_max = (float)p.inv_depth_max;
+    d.gamma = (float)p.gamma;
+    d.fxd = c.K.fx; d.fyd = c.K.fy; d.cxd = c.K.cx; d.cyd = c.K.cy;
+    d.sigma_t = p.sigma_t; d.sigma_r = p.sigma_r; d.ms_tol = p.ms_tol;
+    d.seed = p.seed; d.window_id = p.window_id;
+    return d;
+}
+
+// Carves every device buffer out of one allocation (or sizes it when base is
+// null). Returns the total size.
+size_t layout(voldor_ctx& c, char* base)
+{
+    const size_t N = (size_t)c.N, T = (size_t)c.T;
+    const size_t S = (size_t)c.params.hyps_per_frame, G = (size_t)c.params.groups_per_frame;
+    const int chunks = score_chunks((int)S, c.N);
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        char* p = base ? base + off : nullptr;
+        off += align256(bytes);
+        return p;
+    };
+    DevState& s = c.ds;
+    c.flows_bytes = T * N * (c.flow_dtype == VOLDOR_FLOW_F16 ? 4 : 8);
+    s.flows = take(c.flows_bytes);
+    s.theta = (float*)take(N * 4);
+    s.wmap = (float*)take(T * N * 4);
+    s.qs = (float*)take(T * N * 4);
+    s.poses = (double*)take(T * 12 * 8);
+    s.cum = (double*)take(T * 12 * 8);
+    s.frames = (FrameF*)take(T * sizeof(FrameF));
+    s.iter = (int*)take(4);
+    s.status = (int*)take(16);
+    c.flag_dev = (int*)take(4);
+    s.pix = (PixRec*)take(N * sizeof(PixRec));
+    s.pix_block_count = (int*)take(((N + kPixThreads - 1) / kPixThreads) * 4);
+    s.pix_count = (int*)take(4);
+    s.grp_sols = (double*)take(G * kMaxSols * 12 * 8);
+    s.grp_weight = (double*)take(G * 8);
+    s.grp_count = (int*)take(G * 4);
+    s.grp_offset = (int*)take(G * 4);
+    s.n_hyp = (int*)take(4);
+    s.hyp_Rt = (double*)take(S * 12 * 8);
+    s.hyp_f32 = (float*)take(S * 12 * 4);
+    s.hyp_p = (double*)take(S * 6 * 8);
+    s.hyp_w = (double*)take(S * 8);
+    s.hyp_info = (long long*)take(S * 2 * 8);
+    s.partial = (double*)take((size_t)chunks * S * 8);
+    s.scores = (double*)take(S * 8);
+    s.mie_prev_score = (float*)take(N * 4);
+    s.mie_smp = (float*)take(N * 4);
+    s.mie_smp_score = (float*)take(N * 4);
+    s.labels = (unsigned char*)take(N);
+    s.fb_fwd = (float*)take(T * N * 8);
+    s.score_log = (long long*)take((size_t)kScoreLogMax * 2 * 8);
+    s.n_chunks = chunks;
+    return off;
+}
+
+__global__ void k_count_nonfinite(const void* flows, int f16, size_t n, int* out)
+{
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int bad = 0;
+    for (; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        float2 v = f16 ? __half22float2(reinterpret_cast<const __half2*>(flows)[i]) : reinterpret_cast<const float2*>(flows)[i];
+        bad |= !(isfinite(v.x) && isfinite(v.y));
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicAdd(out, 1);
+}
+
+voldor_status upload_flows(voldor_ctx* c, const void* flows, int on_device)
+{
+    if (!cuda_ok(c, cudaMemcpyAsync((void*)c->ds.flows, flows, c->flows_bytes,
+                                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream)))
+        return kCuda;
+    if (!cuda_ok(c, cudaMemsetAsync(c->flag_dev, 0, 4, c->stream))) return kCuda;
+    const size_t n = (size_t)c->T * c->N;
+    k_count_nonfinite<<<304, 256, 0, c->stream>>>(c->ds.flows, c->flow_dtype == VOLDOR_FLOW_F16, n, c->flag_dev);
+    c->launches += 1;
+    if (!launched(c)) return kCuda;
+    int bad = 0;
+    if (!cuda_ok(c, cudaMemcpyAsync(&bad, c->flag_dev, 4, cudaMemcpyDeviceToHost, c->stream))) return kCuda;
+    if (!cuda_ok(c, cudaStreamSynchronize(c->stream))) return kCuda;
+    if (bad) return VOLDOR_ERR_INVALID_ARG;
+    return VOLDOR_OK;
+}
+
+// One pose update of frame t (iteration counter already set on the device).
+bool enqueue_pose_update(voldor_ctx* c, int t, cudaEvent_t ev0, cudaEvent_t ev1, int log_idx)
+{
+    const DevParams& p = c->dp;
+    const DevState& s = c->ds;
+    cudaStream_t st = c->stream;
+    launch_frame_setup(p, s, st);
+    launch_pose_prep(p, s, t, st);
+    launch_p3p_groups(p, s, t, st);
+    launch_hyp_collect(p, s, st);
+    if (ev0 && !cuda_ok(c, cudaEventRecord(ev0, st))) return false;
+    launch_score(p, s, log_idx, st);
+    if (ev1 && !cuda_ok(c, cudaEventRecord(ev1, st))) return false;
+    launch_score_reduce(p, s, st);
+    launch_meanshift(p, s, t, st);
+    return launched(c);
+}
+
+bool enqueue_smooth(voldor_ctx* c)
+{
+    launch_frame_setup(c->dp, c->ds, c->stream);
+    launch_emissions(c->dp, c->ds, c->ds.qs, c->stream);
+    launch_forward_backward(c->dp, c->ds, c->stream);
+    return launched(c);
+}
+
+bool enqueue_depth(voldor_ctx* c)
+{
+    launch_frame_setup(c->dp, c->ds, c->stream);
+    launch_mie(c->dp, c->ds, c->stream);
+    return launched(c);
+}
+
+bool enqueue_rigidness(voldor_ctx* c)
+{
+    launch_frame_setup(c->dp, c->ds, c->stream);
+    launch_emissions(c->dp, c->ds, c->ds.wmap, c->stream);
+    return launched(c);
+}
+
+// Table 1, one iteration, reading k from the device counter and advancing it.
+bool enqueue_iteration(voldor_ctx* c, int pair_base)
+{
+    for (int t = 1; t <= c->T; ++t) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        int log_idx = -1;
+        if (c->timing) {
+            const int idx = pair_base + t - 1;
+            e0 = c->events[2 * idx];
+            e1 = c->events[2 * idx + 1];
+            log_idx = idx;
+        }
+        if (!enqueue_pose_update(c, t, e0, e1, log_idx)) return false;
+    }
+    if (!enqueue_smooth(c) || !enqueue_depth(c) || !enqueue_rigidness(c)) return false;
+    launch_advance_iteration(c->ds, c->stream);
+    return launched(c);
+}
+
+bool ensure_events(voldor_ctx* c, int pairs)
+{
+    while ((int)c->events.size() < 2 * pairs) {
+        cudaEvent_t e;
+        if (!cuda_ok(c, cudaEventCreate(&e))) return false;
+        c->events.push_back(e);
+    }
+    return true;
+}
+
+voldor_status read_status_word(voldor_ctx* c, int* host4)
+{
+    if (!cuda_ok(c, cudaMemcpyAsync(host4, c->ds.status, 16, cudaMemcpyDeviceToHost, c->stream))) return kCuda;
+    if (!cuda_ok(c, cudaStreamSynchronize(c->stream))) return kCuda;
+    return VOLDOR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void voldor_default_params(voldor_params* p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->a1 = 0.01; p->a2 = 0.09; p->b1 = -0.0022; p->b2 = 1.0;
+    p->lambda_ = 0.15; p->gamma = 0.9;
+    p->sigma_t = 0.1; p->sigma_r = 0.004;
+    p->inv_depth_min = 1.0 / 40.0; p->inv_depth_max = 1.0;
+    p->x_min = 1e-6; p->x_max = 1e12; p->beta_min = 0.05;
+    p->ms_tol = 1e-10;
+    p->hyps_per_frame = 256; p->groups_per_frame = 512; p->ms_max_iter = 100;
+    p->seed = 0; p->window_id = 0;
+}
+
+const char* voldor_status_string(voldor_status s)
+{
+    switch (s) {
+        case VOLDOR_OK: return "ok";
+        case VOLDOR_ERR_INVALID_ARG: return "invalid argument";
+        case VOLDOR_ERR_CUDA: return "CUDA error (context poisoned)";
+        case VOLDOR_ERR_OOM: return "device out of memory";
+        case VOLDOR_ERR_NOT_BOOTSTRAPPED: return "context not bootstrapped";
+        case VOLDOR_ERR_DEGENERATE: return "a frame had no weighted pose hypothesis";
+        case VOLDOR_ERR_TIMEOUT: return "device-side wait timed out";
+        case VOLDOR_ERR_INTERNAL: return "internal consistency check failed";
+    }
+    return "unknown status";
+}
+
+voldor_status voldor_init_window(voldor_ctx** out, int width, int height, int T, const voldor_intrinsics* K,
+                                 const voldor_params* params, const void* flows, int flow_dtype, int flows_on_device,
+                                 void* cuda_stream)
+{
+    if (!out) return VOLDOR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!K || !flows || width < 2 || height < 2 || T < 1 || T > kMaxT) return VOLDOR_ERR_INVALID_ARG;
+    if ((long long)width * height > 0x7fffffffLL) return VOLDOR_ERR_INVALID_ARG;
+    if (!finite_pos(K->fx) || !finite_pos(K->fy) || !std::isfinite(K->cx) || !std::isfinite(K->cy))
+        return VOLDOR_ERR_INVALID_ARG;
+    if (flow_dtype != VOLDOR_FLOW_F32 && flow_dtype != VOLDOR_FLOW_F16) return VOLDOR_ERR_INVALID_ARG;
+    voldor_params p;
+    if (params) p = *params; else voldor_default_params(&p);
+    if (!params_ok(p)) return VOLDOR_ERR_INVALID_ARG;
+
+    voldor_ctx* c = new (std::nothrow) voldor_ctx();
+    if (!c) return VOLDOR_ERR_OOM;
+    c->W = width; c->H = height; c->T = T; c->N = width * height;
+    c->flow_dtype = flow_dtype; c->params = p; c->K = *K;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->dp = make_dev_params(*c);
+    const size_t bytes = layout(*c, nullptr);
+    cudaError_t e = cudaMalloc(&c->arena, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return e == cudaErrorMemoryAllocation ? VOLDOR_ERR_OOM : VOLDOR_ERR_CUDA;
+    }
+    c->arena_bytes = bytes;
+    layout(*c, (char*)c->arena);
+    if (!cuda_ok(c, cudaMemsetAsync(c->arena, 0, bytes, c->stream))) { voldor_destroy(c); return kCuda; }
+    voldor_status st = upload_flows(c, flows, flows_on_device);
+    if (st != VOLDOR_OK) { voldor_destroy(c); return st; }
+    *out = c;
+    return VOLDOR_OK;
+}
+
+voldor_status voldor_set_flows(voldor_ctx* c, const void* flows, int flows_on_device)
+{
+    if (!c || !flows) return VOLDOR_ERR_INVALID_ARG;
+    if (c->poisoned) return kCuda;
+    return upload_flows(c, flows, flows_on_device);
+}
+
+voldor_status voldor_bootstrap(voldor_ctx* c, int mode, const double* T1)
+{
+    if (!c) return VOLDOR_ERR_INVALID_ARG;
+    if (c->poisoned) return kCuda;
+    if (mode != VOLDOR_BOOT_GIVEN_POSE || !T1) return VOLDOR_ERR_INVALID_ARG;
+    for (int i = 0; i < 12; ++i)
+        if (!std::isfinite(T1[i])) return VOLDOR_ERR_INVALID_ARG;
+    launch_bootstrap(c->dp, c->ds, T1, c->stream);
+    c->launches += 1;
+    if (!cuda_ok(c, cudaMemsetAsync(c->ds.status, 0, 16, c->stream))) return kCuda;
+    if (!launched(c)) return kCuda;
+    c->bootstrapped = true;
+    return VOLDOR_OK;
+}
+
+voldor_status voldor_em_step(voldor_ctx* c, int n_iters)
+{
+    if (!c || n_iters < 0) return VOLDOR_ERR_INVALID_ARG;
+    if (c->poisoned) return kCuda;
+    if (!c->bootstrapped) return VOLDOR_ERR_NOT_BOOTSTRAPPED;
+    if (n_iters == 0) return VOLDOR_OK;
+    const long long key = (long long)n_iters * 2 + (c->timing ? 1 : 0);
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+        if (c->timing && !ensure_events(c, n_iters * c->T)) return kCuda;
+        cudaStream_t cap = c->stream;
+        bool own = false;
+        if (cap == nullptr) {   // the legacy stream cannot be captured
+            if (!cuda_ok(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking))) return kCuda;
+            own = true;
+        }
+        cudaStream_t saved = c->stream;
+        c->stream = cap;
+        cudaGraph_t g = nullptr;
+        bool ok = cuda_ok(c, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        if (ok) {
+            for (int i = 0; i < n_iters && ok; ++i) ok = enqueue_iteration(c, i * c->T);
+            cudaError_t ee = cudaStreamEndCapture(cap, &g);
+            ok = ok && cuda_ok(c, ee);
+        }
+        c->stream = saved;
+        if (own) cudaStreamDestroy(cap);
+        if (!ok) { if (g) cudaGraphDestroy(g); c->poisoned = true; return kCuda; }
+        size_t n_nodes = 0;
+        long long n_kernels = 0;
+        if (cudaGraphGetNodes(g, nullptr, &n_nodes) == cudaSuccess && n_nodes > 0) {
+            std::vector<cudaGraphNode_t> nodes(n_nodes);
+            if (cudaGraphGetNodes(g, nodes.data(), &n_nodes) == cudaSuccess)
+                for (size_t q = 0; q < n_nodes; ++q) {
+                    cudaGraphNodeType ty;
+                    if (cudaGraphNodeGetType(nodes[q], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++n_kernels;
+                }
+        }
+        cudaGraphExec_t ge = nullptr;
+        if (!cuda_ok(c, cudaGraphInstantiate(&ge, g, 0))) { cudaGraphDestroy(g); return kCuda; }
+        cudaGraphDestroy(g);
+        it = c->graphs.emplace(key, ge).first;
+        c->graph_kernels[key] = n_kernels;
+        if (c->timing) c->graph_pairs = n_iters * c->T;
+    }
+    int zero = 0;
+    (void)zero;
+    if (!cuda_ok(c, cudaMemsetAsync(c->ds.status + 3, 0, 4, c->stream))) return kCuda;
+    if (c->timing && !cuda_ok(c, cudaMemsetAsync(c->ds.score_log, 0, (size_t)kScoreLogMax * 16, c->stream))) return kCuda;
+    if (!cuda_ok(c, cudaGraphLaunch(it->second, c->stream))) return kCuda;
+    c->launches += c->graph_kernels[key];
+    c->last_pairs = c->timing ? n_iters * c->T : 0;
+    int st4[4];
+    voldor_status rs = read_status_word(c, st4);
+    if (rs != VOLDOR_OK) return rs;
+    return st4[3] ? VOLDOR_ERR_DEGENERATE : VOLDOR_OK;
+}
+
+voldor_status voldor_get_pose_depth_rigidness(voldor_ctx* c, double* poses, float* depth, float* rigidness)
+{
+    if (!c) return VOLDOR_ERR_INVALID_ARG;
+    if (c->poisoned) return kCuda;
+    std::vector<double> p12;
+    if (poses) {
+        p12.resize((size_t)c->T * 12);
+        if (!cuda_ok(c, cudaMemcpyAsync(p12.data(), c->ds.poses, p12.size() * 8, cudaMemcpyDeviceToHost, c->stream))) return kCuda;
+    }
+    if (depth && !cuda_ok(c, cudaMemcpyAsync(depth, c->ds.theta, (size_t)c->N * 4, cudaMemcpyDeviceToHost, c->stream))) return kCuda;
+    if (rigidness && !cuda_ok(c, cudaMemcpyAsync(rigidness, c->ds.wmap, (size_t)c->T * c->N * 4, cudaMemcpyDeviceToHost, c->stream)))
+        return kCuda;
+    if (!cuda_ok(c, cudaStreamSynchronize(c->stream))) return kCuda;
+    if (poses) {
+        for (int t = 0; t < c->T; ++t) {
+            for (int q = 0; q < 12; ++q) poses[16 * t + q] = p12[12 * t + q];
+            poses[16 * t + 12] = 0; poses[16 * t + 13] = 0; poses[16 * t + 14] = 0; poses[16 * t + 15] = 1;
+        }
+    }
+    return VOLDOR_OK;
+}
+
+void voldor_destroy(voldor_ctx* c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    if (c->arena) cudaFree(c->arena);
+    cudaGetLastError();
+    delete c;
+}
+
+voldor_status voldor_set_state(voldor_ctx* c, const double* poses, const float* depth, const float* rigidness, int iteration)
+{
+    if (!c || iteration < 0) return VOLDOR_ERR_INVALID_ARG;
+    if (c->poisoned) return kCuda;
+    if (poses) {
+        std::vector<double> p12((size_t)c->T * 12);
+        for (int t = 0; t < c->T; ++t)
+            for (int q = 0; q < 12; ++q) {
+                p12[12 * t + q] = poses[16 * t + q];
+                if (!std::isfinite(p12[12 * t + q])) return VOLDOR_ERR_INVALID_ARG;
+            }
+        if (!cuda_ok(c, cudaMemcpyAsync(c->ds.poses, p12.data(), p12.size() * 8, cudaMemcpyHostToDevice, c->stream))) return kCuda;
+        if (!cuda_ok(c, cudaStreamSynchronize(c->stream))) return kCuda;
+    }
+    if (depth && !cuda_ok(c, cudaMemcpyAsync(c->ds.theta, depth, (size_t)c->N * 4, cudaMemcpyHostToDevice, c->stream))) return kCuda;
+    if (rigidness && !cuda_ok(c, cudaMemcpyAsync(c->ds.wmap, rigidness, (size_t)c->T * c->N * 4, cudaMemcpyHostToDevice, c->stream)))
+        return kCuda;
+    launch_set_iteration(c->ds, iteration, c->stream);
+    if (!launched(c)) return kCuda;
+    if (!cuda_ok(c, cudaStreamSynchronize(c->stream))) return kCuda;
+    c->bootstrapped = true;
+    return VOLDOR_OK;
+}
+
+voldor_status voldor_pose_update(voldor_ctx* c, int k, int t)
+{
+    if (!c || k < 0 || t < 1) return VOLDOR_ERR_INVALID_ARG;
+    if (c->poisoned) return kCuda;
+    if (t > c->T) return VOLDOR_ERR_INVALID_ARG;
+    if (!c->bootstrapped) return VOLDOR_ERR_NOT_BOOTSTRAPPED;
+    if (!cuda_ok(c, cudaMemsetAsync(c->ds.status, 0, 16, c->stream))) return kCuda;
+    launch_set_iteration(c->ds, k, c->stream);
+    if (!enqueue_pose_update(c, t, nullptr, nullptr, -1)) return kCuda;
+    int st4[4];
+    voldor_status rs = read_status_word(c, st4);
+    if (rs != VOLDOR_OK) return rs;
+    return st4[3] ? VOLDOR_ERR_DEGENERATE : VOLDOR_OK;
+}
+
+voldor_status voldor_score_hypotheses(voldor_ctx* c, int t, int n, const double* R, const double* tv, double* L)
+{
+    if (!c || t < 1 || n < 1 || !R || !tv || !L) return VOLDOR_ERR_INVALID_ARG;
+    if (c->poisoned) return kCuda;
+    if (t > c->T || n > c->params.hyps_per_frame) return VOLDOR_ERR_INVALID_ARG;
+    if (!c->bootstrapped) return VOLDOR_ERR_NOT_BOOTSTRAPPED;
+    std::vector<double> h((size_t)n * 12);
+    for (int i = 0; i < n; ++i) {
+        for (int q = 0; q < 9; ++q) h[12 * i + q] = R[9 * i + q];
+        for (int q = 0; q < 3; ++q) h[12 * i + 9 + q] = tv[3 * i + q];
+        for (int q = 0; q < 12; ++q)
+            if (!std::isfinite(h[12 * i + q])) return VOLDOR_ERR_INVALID_ARG;
+    }
+    if (!cuda_ok(c, cudaMemcpyAsync(c->ds.hyp_Rt, h.data(), h.size() * 8, cudaMemcpyHostToDevice, c->stream))) return kCuda;
+    launch_frame_setup(c->dp, c->ds, c->stream);
+    launch_pose_prep(c->dp, c->ds, t, c->stream);
+    score_hyps_from_host(c->dp, c->ds, n, c->stream);
+    launch_score(c->dp, c->ds, -1, c->stream);
+    launch_score_reduce(c->dp, c->ds, c->stream);
+    c->launches += 6;
+    if (!launched(c)) return kCuda;
+    if (!cuda_ok(c, cudaMemcpyAsync(L, c->ds.scores, (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream))) return kCuda;
+    if (!cuda_ok(c, cudaStreamSynchronize(c->stream))) return kCuda;
+    return VOLDOR_OK;
+}
+
+voldor_status voldor_rigidness_smooth(voldor_ctx* c, int k)
+{
+    if (!c || k < 0) return VOLDOR_ERR_INVALID_ARG;
+    if (c->poisoned) return kCuda;
+    if (!c->bootstrapped) return VOLDOR_ERR_NOT_BOOTSTRAPPED;
+    launch_set_iteration(c->ds, k, c->stream);
+    return enqueue_smooth(c) ? VOLDOR_OK : kCuda;
+}
+
+voldor_status voldor_depth_update(voldor_ctx* c, int k)
+{
+    if (!c || k < 0) return VOLDOR_ERR_INVALID_ARG;
+    if (c->poisoned) return kCuda;
+    if (!c->bootstrapped) return VOLDOR_ERR_NOT_BOOTSTRAPPED;
+    launch_set_iteration(c->ds, k, c->stream);
+    return enqueue_depth(c) ? VOLDOR_OK : kCuda;
+}
+
+voldor_status voldor_rigidness_update(voldor_ctx* c)
+{
+    if (!c) return VOLDOR_ERR_INVALID_ARG;
+    if (c->poisoned) return kCuda;
+    if (!c->bootstrapped) return VOLDOR_ERR_NOT_BOOTSTRAPPED;
+    return enqueue_rigidness(c) ? VOLDOR_OK : kCuda;
+}
+
+static bool buffer_of(voldor_ctx* c, int which, void** dev, size_t* bytes, bool* writable)
+{
+    const size_t N = (size_t)c->N, T = (size_t)c->T, S = (size_t)c->params.hyps_per_frame;
+    *writable = false;
+    switch (which) {
+        case VOLDOR_BUF_SMOOTHED: *dev = c->ds.qs; *bytes = T * N * 4; *writable = true; return true;
+        case VOLDOR_BUF_LABELS: *dev = c->ds.labels; *bytes = N; return true;
+        case VOLDOR_BUF_HYPS: *dev = c->ds.hyp_Rt; *bytes = S * 12 * 8; return true;
+        case VOLDOR_BUF_HYP_INFO: *dev = c->ds.hyp_info; *bytes = S * 2 * 8; return true;
+        case VOLDOR_BUF_HYP_WEIGHT: *dev = c->ds.hyp_w; *bytes = S * 8; return true;
+        case VOLDOR_BUF_SCORES: *dev = c->ds.scores; *bytes = S * 8; return true;
+        case VOLDOR_BUF_POSE_INFO: *dev = c->ds.status; *bytes = 16; return true;
+        case VOLDOR_BUF_DEPTH_SAMPLES: *dev = c->ds.mie_smp; *bytes = N * 4; return true;
+        case VOLDOR_BUF_HYPS_F32: *dev = c->ds.hyp_f32; *bytes = S * 12 * 4; return true;
+    }
+    return false;
+}
+
+voldor_status voldor_get_buffer(voldor_ctx* c, int which, void* host, size_t bytes)
+{
+    if (!c || !host) return VOLDOR_ERR_INVALID_ARG;
+    if (c->poisoned) return kCuda;
+    void* dev;
+    size_t size;
+    bool w;
+    if (!buffer_of(c, which, &dev, &size, &w) || bytes > size) return VOLDOR_ERR_INVALID_ARG;
+    if (!cuda_ok(c, cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, c->stream))) return kCuda;
+    if (!cuda_ok(c, cudaStreamSynchronize(c->stream))) return kCuda;
+    return VOLDOR_OK;
+}
+
+voldor_status voldor_set_buffer(voldor_ctx* c, int which, const void* host, size_t bytes)
+{
+    if (!c || !host) return VOLDOR_ERR_INVALID_ARG;
+    if (c->poisoned) return kCuda;
+    void* dev;
+    size_t size;
+    bool w;
+    if (!buffer_of(c, which, &dev, &size, &w) || !w || bytes > size) return VOLDOR_ERR_INVALID_ARG;
+    if (!cuda_ok(c, cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, c->stream))) return kCuda;
+    if (!cuda_ok(c, cudaStreamSynchronize(c->stream))) return kCuda;
+    return VOLDOR_OK;
+}
+
+voldor_status voldor_enable_timing(voldor_ctx* c, int on)
+{
+    if (!c) return VOLDOR_ERR_INVALID_ARG;
+    c->timing = on != 0;
+    return VOLDOR_OK;
+}
+
+voldor_status voldor_get_score_times(voldor_ctx* c, float* ms, long long* pairs, int max, int* count)
+{
+    if (!c || !count || (max > 0 && !ms)) return VOLDOR_ERR_INVALID_ARG;
+    if (c->poisoned) return kCuda;
+    if (!cuda_ok(c, cudaStreamSynchronize(c->stream))) return kCuda;
+    *count = c->last_pairs;
+    for (int i = 0; i < c->last_pairs && i < max; ++i)
+        if (!cuda_ok(c, cudaEventElapsedTime(&ms[i], c->events[2 * i], c->events[2 * i + 1]))) return kCuda;
+    if (pairs) {
+        const int n = std::min(std::min(c->last_pairs, max), kScoreLogMax);
+        std::vector<long long> log((size_t)2 * (n > 0 ? n : 1));
+        if (n > 0) {
+            if (!cuda_ok(c, cudaMemcpy(log.data(), c->ds.score_log, (size_t)n * 16, cudaMemcpyDeviceToHost))) return kCuda;
+            for (int i = 0; i < n; ++i) pairs[i] = log[2 * i] * log[2 * i + 1];
+        }
+    }
+    return VOLDOR_OK;
+}
+
+long long voldor_kernel_launches(const voldor_ctx* c) { return c ? c->launches : 0; }
+
+size_t voldor_device_bytes(const voldor_ctx* c) { return c ? c->arena_bytes : 0; }
+
+}  // extern "C"

@@ -1,0 +1,260 @@
+// Internal declarations of the sm_103a VOLDOR library: device parameter block,
+// context layout, device helpers shared by the kernels, and the host-side
+// launchers each translation unit provides.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "voldor.h"
+
+namespace vd {
+
+constexpr int kMaxT = 16;
+constexpr int kMaxSols = 4;            // P3P has at most four solutions
+constexpr int kScoreThreads = 256;     // dense scoring block
+constexpr int kScoreHypsPerThread = 4;
+constexpr int kScoreHypsPerBlock = kScoreThreads * kScoreHypsPerThread;
+constexpr int kMeanshiftCtas = 8;      // thread-block cluster of the meanshift
+constexpr int kMeanshiftThreads = 1024;
+constexpr int kPixThreads = 256;
+constexpr int kScoreLogMax = 1024;
+
+// Everything a kernel needs to know about the window, by value.
+struct DevParams {
+    int W, H, T, N;
+    int S, G, ms_max_iter, flow_f16;
+    float fx, fy, cx, cy, inv_fx, inv_fy, fy_over_fx;
+    float log2_a1, a2_log2e, b1, b2, beta_min, lambda2;
+    float x_min, x_max;                 // px^2
+    float xs_min, xs_max;               // scaled by 1/fx^2
+    float log2_fx2;
+    float inv_depth_min, inv_depth_max;
+    float gamma;
+    double fxd, fyd, cxd, cyd;
+    double sigma_t, sigma_r, ms_tol;
+    uint64_t seed, window_id;
+};
+
+// FP32 form of the poses of frame t used by per-pixel work:
+// C_{t-1} = (Rc, tc) and T_t in the cancellation-free scaled form
+// E = S_y (R_t - I) S_y^-1, tt = S_y t_t with S_y = diag(1, fy/fx, 1).
+struct FrameF {
+    float Rc[9];
+    float tc[3];
+    float E[9];
+    float tt[3];
+};
+
+// Per-pixel record of a frame for dense scoring (three float4 = 48 B).
+//  a = {xb, yb2, w, ut}: normalised coords x/z, (fy/fx) y/z, inverse depth 1/z
+//      in camera t-1, observed flow u / fx
+//  b = {vt, beta, beta_k, Cp}: observed flow v / fx, Fisk shape, beta *
+//      log2(fx^2 / alpha), mu / beta * fx^2
+//  c = {wq, 0, 0, 0}: rigidness weight W_t^j
+struct PixRec {
+    float4 a, b, c;
+};
+
+// Device state of a window (all pointers are device memory).
+struct DevState {
+    const void* flows;        // [T][H][W] float2 or __half2
+    float* theta;             // [H][W]
+    float* wmap;              // [T][H][W] unsmoothed W
+    float* qs;                // [T][H][W] smoothed q (also emission scratch)
+    double* poses;            // [T][12] row-major [R | t]
+    double* cum;              // [T][12] C_{t-1} = T_{t-1} ... T_1 (FP64)
+    FrameF* frames;           // [T]
+    int* iter;                // [1] iteration counter k
+    int* status;              // [4] n_hyp, seed, meanshift steps, status bits
+    // dense scoring scratch
+    PixRec* pix;              // [N] compacted valid pixels of the current frame
+    int* pix_block_count;     // [ceil(N / kPixThreads)]
+    int* pix_count;           // [1]
+    // P3P
+    double* grp_sols;         // [G][4][12]
+    double* grp_weight;       // [G]
+    int* grp_count;           // [G]
+    int* grp_offset;          // [G]
+    int* n_hyp;               // [1]
+    double* hyp_Rt;           // [S][12]
+    float* hyp_f32;           // [S][12] scoring form
+    double* hyp_p;            // [S][6] se(3) log
+    double* hyp_w;            // [S]
+    long long* hyp_info;      // [S][2]
+    double* partial;          // [n_chunks][S]
+    double* scores;           // [S]
+    // depth sweep
+    float* mie_prev_score;    // [N]
+    float* mie_smp;           // [N]
+    float* mie_smp_score;     // [N]
+    unsigned char* labels;    // [N]
+    float* fb_fwd;            // [T][H][W] forward messages
+    long long* score_log;     // [kScoreLogMax][2] (n_hyp, n_pix) of timed scoring launches
+    int n_chunks;             // dense scoring pixel chunks
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11).
+// ---------------------------------------------------------------------------
+struct U64x4 { uint64_t v[4]; };
+
+__device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                                uint64_t k0, uint64_t k1)
+{
+    const uint64_t mA = 0xD2E7470EE14C6C93ULL, mB = 0xCA5A826395121157ULL;
+    const uint64_t wA = 0x9E3779B97F4A7C15ULL, wB = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t hiA = __umul64hi(mA, c0), loA = mA * c0;
+        const uint64_t hiB = __umul64hi(mB, c2), loB = mB * c2;
+        const uint64_t n0 = hiB ^ c1 ^ k0;
+        const uint64_t n2 = hiA ^ c3 ^ k1;
+        c0 = n0; c1 = loB; c2 = n2; c3 = loA;
+        k0 += wA; k1 += wB;
+    }
+    U64x4 o;
+    o.v[0] = c0; o.v[1] = c1; o.v[2] = c2; o.v[3] = c3;
+    return o;
+}
+
+enum { kStreamPose = 1, kStreamDepth = 2 };
+
+// ---------------------------------------------------------------------------
+// Flow access.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 load_flow(const void* flows, int flow_f16, size_t idx)
+{
+    if (flow_f16) {
+        const __half2 h = reinterpret_cast<const __half2*>(flows)[idx];
+        return __half22float2(h);
+    }
+    return reinterpret_cast<const float2*>(flows)[idx];
+}
+
+// Bilinear lookup of frame t (0-based ft) at (u, v); false outside
+// [0, W-1] x [0, H-1].
+__device__ __forceinline__ bool flow_bilinear(const DevParams& p, const void* flows, int ft, float u, float v,
+                                              float2& out)
+{
+    if (!(u >= 0.f && u <= (float)(p.W - 1) && v >= 0.f && v <= (float)(p.H - 1))) return false;
+    int x0 = min((int)floorf(u), p.W - 2);
+    int y0 = min((int)floorf(v), p.H - 2);
+    const float ax = u - (float)x0, ay = v - (float)y0;
+    const size_t base = (size_t)ft * p.N + (size_t)y0 * p.W + x0;
+    const float2 f00 = load_flow(flows, p.flow_f16, base);
+    const float2 f10 = load_flow(flows, p.flow_f16, base + 1);
+    const float2 f01 = load_flow(flows, p.flow_f16, base + p.W);
+    const float2 f11 = load_flow(flows, p.flow_f16, base + p.W + 1);
+    const float w00 = (1.f - ax) * (1.f - ay), w10 = ax * (1.f - ay), w01 = (1.f - ax) * ay, w11 = ax * ay;
+    out.x = w00 * f00.x + w10 * f10.x + w01 * f01.x + w11 * f11.x;
+    out.y = w00 * f00.y + w10 * f10.y + w01 * f01.y + w11 * f11.y;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Per-pixel geometry of frame t (1-based) at depth `depth`: the point in
+// camera t-1 as (xb, yb2, w) and pi_{t-1}. False if P_z <= 0 or pi_{t-1}
+// leaves the image.
+// ---------------------------------------------------------------------------
+struct PixGeom {
+    float xb, yb2, w;    // x/z, (fy/fx) y/z, 1/z in camera t-1
+    float2 vob;          // observed flow at pi_{t-1}
+};
+
+__device__ __forceinline__ bool pixel_geometry(const DevParams& p, const FrameF& fr, const void* flows, int t,
+                                               int x, int y, float depth, PixGeom& g)
+{
+    const float dx = ((float)x - p.cx) * p.inv_fx;
+    const float dy = ((float)y - p.cy) * p.inv_fy;
+    float u, v;
+    if (t == 1) {
+        if (!(depth > 0.f)) return false;
+        g.xb = dx;
+        g.yb2 = p.fy_over_fx * dy;
+        g.w = 1.f / depth;
+        u = (float)x;
+        v = (float)y;
+    } else {
+        const float X = depth * dx, Y = depth * dy, Z = depth;
+        const float Px = fmaf(fr.Rc[0], X, fmaf(fr.Rc[1], Y, fmaf(fr.Rc[2], Z, fr.tc[0])));
+        const float Py = fmaf(fr.Rc[3], X, fmaf(fr.Rc[4], Y, fmaf(fr.Rc[5], Z, fr.tc[1])));
+        const float Pz = fmaf(fr.Rc[6], X, fmaf(fr.Rc[7], Y, fmaf(fr.Rc[8], Z, fr.tc[2])));
+        if (!(Pz > 0.f)) return false;
+        const float iz = 1.f / Pz;
+        const float xb = Px * iz, yb = Py * iz;
+        g.xb = xb;
+        g.yb2 = p.fy_over_fx * yb;
+        g.w = iz;
+        u = fmaf(p.fx, xb, p.cx);
+        v = fmaf(p.fy, yb, p.cy);
+    }
+    return flow_bilinear(p, flows, t - 1, u, v, g.vob);
+}
+
+// Fisk constants of an observed flow (Eqs. 5-7): beta, beta * log2(fx^2/alpha)
+// and Cp = fx^2 * mu / beta, with mu = F(lambda^2 |v|^2) written as
+// mu / beta = ys / (x_mu (1 + ys)^2), ys = 2^-|beta log2(x_mu / alpha)|.
+struct FiskConst {
+    float beta, beta_k, Cp;
+};
+
+__device__ __forceinline__ FiskConst fisk_const(const DevParams& p, float2 vob)
+{
+    const float n = sqrtf(vob.x * vob.x + vob.y * vob.y);
+    const float log2_alpha = fmaf(p.a2_log2e, n, p.log2_a1);
+    const float beta = fmaxf(fmaf(p.b1, n, p.b2), p.beta_min);
+    const float xmu = fminf(fmaxf(p.lambda2 * n * n, p.x_min), p.x_max);
+    const float smu = beta * (log2f(xmu) - log2_alpha);
+    const float ys = exp2f(-fabsf(smu));
+    const float g = 1.f + ys;
+    FiskConst c;
+    c.beta = beta;
+    c.beta_k = beta * (p.log2_fx2 - log2_alpha);
+    c.Cp = (p.fx * p.fx) * ys / (xmu * g * g);
+    return c;
+}
+
+// log[rho/(rho+mu)] (Eq. 10 term) of the residual between the rigid flow under
+// frame pose fr and the observation, accurate FP32 (library log/exp). Returns
+// log(1/2) when the point is behind camera t (the model's rho := mu).
+__device__ __forceinline__ float pixel_ell(const DevParams& p, const FrameF& fr, const PixGeom& g,
+                                           const FiskConst& fc)
+{
+    const float ax = fmaf(fr.E[0], g.xb, fmaf(fr.E[1], g.yb2, fmaf(fr.tt[0], g.w, fr.E[2])));
+    const float ay = fmaf(fr.E[3], g.xb, fmaf(fr.E[4], g.yb2, fmaf(fr.tt[1], g.w, fr.E[5])));
+    const float az = fmaf(fr.E[6], g.xb, fmaf(fr.E[7], g.yb2, fmaf(fr.tt[2], g.w, fr.E[8])));
+    const float den = 1.f + az;
+    if (!(den > 0.f)) return -0.69314718055994531f;
+    const float rd = 1.f / den;
+    const float ru = fmaf(fmaf(-g.xb, az, ax), rd, -g.vob.x * p.inv_fx);
+    const float rv = fmaf(fmaf(-g.yb2, az, ay), rd, -g.vob.y * p.inv_fx);
+    const float xs = fminf(fmaxf(fmaf(ru, ru, rv * rv), p.xs_min), p.xs_max);
+    const float s = fmaf(fc.beta, log2f(xs), fc.beta_k);
+    const float e = exp2f(fabsf(s));
+    const float r = fc.Cp * xs * (e + 2.f + 1.f / e);     // mu / rho
+    return -log1pf(r);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (one translation unit each).
+// ---------------------------------------------------------------------------
+void launch_frame_setup(const DevParams& p, const DevState& s, cudaStream_t st);
+void launch_bootstrap(const DevParams& p, const DevState& s, const double* T1, cudaStream_t st);
+void launch_pose_prep(const DevParams& p, const DevState& s, int t, cudaStream_t st);
+void launch_p3p_groups(const DevParams& p, const DevState& s, int t, cudaStream_t st);
+void launch_hyp_collect(const DevParams& p, const DevState& s, cudaStream_t st);
+void launch_score(const DevParams& p, const DevState& s, int log_idx, cudaStream_t st);
+void launch_score_reduce(const DevParams& p, const DevState& s, cudaStream_t st);
+void launch_meanshift(const DevParams& p, const DevState& s, int t, cudaStream_t st);
+void launch_emissions(const DevParams& p, const DevState& s, float* out, cudaStream_t st);
+void launch_forward_backward(const DevParams& p, const DevState& s, cudaStream_t st);
+void launch_mie(const DevParams& p, const DevState& s, cudaStream_t st);
+void launch_set_iteration(const DevState& s, int k, cudaStream_t st);
+void launch_advance_iteration(const DevState& s, cudaStream_t st);
+int score_chunks(int S, int N);
+void score_hyps_from_host(const DevParams& p, const DevState& s, int n, cudaStream_t st);
+
+}  // namespace vd

@@ -172,8 +172,11 @@ def _make_window(prims, K, Ms, W, H, patches, rng, name, inv_range, noise=True):
             u = fx * Pc[:, 0] / z + cx
             v = fy * Pc[:, 1] / z + cy
         fl = np.stack([u.reshape(H, W) - xs, v.reshape(H, W) - ys], -1)
-        bad = ~np.isfinite(fl).all(-1) | (z.reshape(H, W) <= 1e-3)
-        fl[bad] = 0.0
+        # points passing (almost) through camera t's image plane have no
+        # meaningful flow: they get an outlier flow, as a flow network would
+        bad = (~np.isfinite(fl).all(-1) | (z.reshape(H, W) <= 0.5)
+               | (np.abs(fl).max(-1) > max(W, H)))
+        fl[bad] = rng.uniform(-20.0, 20.0, size=(int(bad.sum()), 2))
         rig = ~moving.reshape(H, W) & ~bad
         for (x0, y0, x1, y1) in patches:
             disp = rng.uniform(-8.0, 8.0, size=2)
@@ -289,7 +292,7 @@ def driving(seed=3000, W=1242, H=375, f=718.0, T=8, noise=True, nonrigid=True):
         z = 0.0
         while z < 80:
             seg = rng.uniform(6, 20)
-            x = side * rng.uniform(3.0, 12.0)
+            x = side * rng.uniform(5.0, 15.0)
             height = rng.uniform(4.0, 20.0)
             prims.append(_Plane([x, cam_h - height / 2, z + seg / 2], [-side, 0, 0],
                                 [0, 0, 1.0], [0, 1.0, 0], seg / 2, height / 2))
@@ -303,19 +306,29 @@ def driving(seed=3000, W=1242, H=375, f=718.0, T=8, noise=True, nonrigid=True):
                             hw, height / 2))
     prims.append(_Plane([0, 0, 80.0], [0, 0, -1.0]))
     M0 = np.eye(4)
-    n_static = len(prims)
-    # cars until ~15% of frame-0 pixels are non-rigid
-    for _ in range(12):
-        _, _, oid = _render(prims, K, M0, W, H, 0)
-        frac = np.mean(oid >= n_static)
-        if frac >= 0.15:
+    # cars until ~15% of frame-0 pixels are non-rigid: each new car is tested
+    # against the depth of everything placed so far
+    _, depth, _ = _render(prims, K, M0, W, H, 0)
+    depth = depth.ravel()
+    car = np.zeros(depth.shape, bool)
+    fx_, fy_, cx_, cy_ = K
+    xs_, ys_ = np.meshgrid(np.arange(W, dtype=float), np.arange(H, dtype=float))
+    dirs = np.stack([(xs_ - cx_) / fx_, (ys_ - cy_) / fy_, np.ones_like(xs_)], -1).reshape(-1, 3)
+    for _ in range(16):
+        if car.mean() >= 0.15:
             break
         x = rng.uniform(-5.0, 5.0)
-        z = rng.uniform(6.0, 30.0)
+        z = rng.uniform(8.0, 35.0)
         lo = np.array([x - 0.9, cam_h - 1.5, z])
         hi = np.array([x + 0.9, cam_h, z + 4.5])
-        vel = np.array([rng.uniform(-0.15, 0.15), 0.0, rng.uniform(-1.5, 1.5)])
-        prims.append(_Box(lo, hi, vel))
+        # same-direction traffic near the camera, oncoming traffic only far ahead
+        vz = rng.uniform(0.2, 2.0) if z < 20 else rng.uniform(-1.0, 2.0)
+        box = _Box(lo, hi, np.array([rng.uniform(-0.1, 0.1), 0.0, vz]))
+        th = box.hit(np.zeros(3), dirs, 0)
+        closer = th < depth
+        depth = np.where(closer, th, depth)
+        car |= closer
+        prims.append(box)
 
     def step(r):
         return _rot([0, 1.0, 0], np.deg2rad(r.uniform(-1.0, 1.0))), np.array([0.0, 0.0, -1.0])

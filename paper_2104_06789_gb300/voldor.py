@@ -1,0 +1,268 @@
+"""Python binding of libvoldor.so (include/voldor.h): argument marshalling only.
+
+Every step of the inference runs in the library's CUDA kernels. Host arrays
+are numpy; device arrays may be torch CUDA tensors (their data pointers are
+passed through). There is no fallback: if the library or a GPU is missing,
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvoldor.so")
+
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_BOOTSTRAPPED, ERR_DEGENERATE, ERR_TIMEOUT, ERR_INTERNAL = range(8)
+FLOW_F32, FLOW_F16 = 0, 1
+BOOT_GIVEN_POSE = 0
+(BUF_SMOOTHED, BUF_LABELS, BUF_HYPS, BUF_HYP_INFO, BUF_HYP_WEIGHT, BUF_SCORES, BUF_POSE_INFO,
+ BUF_DEPTH_SAMPLES, BUF_HYPS_F32) = range(9)
+
+
+class VoldorError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("a1", C.c_double), ("a2", C.c_double), ("b1", C.c_double), ("b2", C.c_double),
+        ("lambda_", C.c_double), ("gamma", C.c_double),
+        ("sigma_t", C.c_double), ("sigma_r", C.c_double),
+        ("inv_depth_min", C.c_double), ("inv_depth_max", C.c_double),
+        ("x_min", C.c_double), ("x_max", C.c_double), ("beta_min", C.c_double),
+        ("ms_tol", C.c_double),
+        ("hyps_per_frame", C.c_int), ("groups_per_frame", C.c_int),
+        ("ms_max_iter", C.c_int), ("pad_", C.c_int),
+        ("seed", C.c_uint64), ("window_id", C.c_uint64),
+    ]
+
+
+class Intrinsics(C.Structure):
+    _fields_ = [("fx", C.c_double), ("fy", C.c_double), ("cx", C.c_double), ("cy", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Loads libvoldor.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2104_06789_gb300.build.build() first")
+        L = C.CDLL(LIB_PATH)
+        vp, i, d, sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+        P = C.POINTER
+        sig = {
+            "voldor_default_params": (None, [P(Params)]),
+            "voldor_status_string": (C.c_char_p, [i]),
+            "voldor_init_window": (i, [P(vp), i, i, i, P(Intrinsics), P(Params), vp, i, i, vp]),
+            "voldor_set_flows": (i, [vp, vp, i]),
+            "voldor_bootstrap": (i, [vp, i, P(d)]),
+            "voldor_em_step": (i, [vp, i]),
+            "voldor_get_pose_depth_rigidness": (i, [vp, P(d), P(C.c_float), P(C.c_float)]),
+            "voldor_destroy": (None, [vp]),
+            "voldor_set_state": (i, [vp, P(d), P(C.c_float), P(C.c_float), i]),
+            "voldor_pose_update": (i, [vp, i, i]),
+            "voldor_score_hypotheses": (i, [vp, i, i, P(d), P(d), P(d)]),
+            "voldor_rigidness_smooth": (i, [vp, i]),
+            "voldor_depth_update": (i, [vp, i]),
+            "voldor_rigidness_update": (i, [vp]),
+            "voldor_get_buffer": (i, [vp, i, vp, sz]),
+            "voldor_set_buffer": (i, [vp, i, vp, sz]),
+            "voldor_enable_timing": (i, [vp, i]),
+            "voldor_get_score_times": (i, [vp, P(C.c_float), P(C.c_longlong), i, P(i)]),
+            "voldor_kernel_launches": (C.c_longlong, [vp]),
+            "voldor_device_bytes": (sz, [vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_string(s):
+    return lib().voldor_status_string(int(s)).decode()
+
+
+def _check(st, where, allow=()):
+    if st != OK and st not in allow:
+        raise VoldorError(st, where)
+    return st
+
+
+def _f64(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f32(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def default_params(**overrides) -> Params:
+    p = Params()
+    lib().voldor_default_params(C.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def _flow_arg(flows):
+    """(pointer, on_device, dtype, keepalive) of a numpy array or torch tensor."""
+    if hasattr(flows, "data_ptr") and hasattr(flows, "is_cuda"):
+        import torch
+        t = flows.contiguous()
+        dt = {torch.float32: FLOW_F32, torch.float16: FLOW_F16}[t.dtype]
+        if t.is_cuda:
+            return C.c_void_p(t.data_ptr()), 1, dt, t
+        a = t.numpy()
+    else:
+        a = np.asarray(flows)
+    if a.dtype == np.float16:
+        a = np.ascontiguousarray(a)
+        return C.c_void_p(a.ctypes.data), 0, FLOW_F16, a
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return C.c_void_p(a.ctypes.data), 0, FLOW_F32, a
+
+
+class Window:
+    """One VOLDOR window (a voldor_ctx)."""
+
+    def __init__(self, flows, K, params: Params | None = None, stream=None):
+        shape = tuple(flows.shape)
+        assert len(shape) == 4 and shape[3] == 2, "flows must be [T][H][W][2]"
+        self.T, self.H, self.W = shape[:3]
+        ptr, on_dev, dt, keep = _flow_arg(flows)
+        self.flow_dtype = dt
+        self.params = params if params is not None else default_params()
+        self.K = Intrinsics(*[float(v) for v in K])
+        h = C.c_void_p()
+        st = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+        self._stream = stream
+        _check(lib().voldor_init_window(C.byref(h), self.W, self.H, self.T, C.byref(self.K), C.byref(self.params),
+                                        ptr, dt, on_dev, C.c_void_p(st)), "voldor_init_window")
+        self._h = h
+
+    # -- lifetime -----------------------------------------------------------
+    def destroy(self):
+        if getattr(self, "_h", None):
+            lib().voldor_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    # -- main calls -------------------------------------------------------------
+    def set_flows(self, flows):
+        ptr, on_dev, dt, keep = _flow_arg(flows)
+        assert dt == self.flow_dtype
+        _check(lib().voldor_set_flows(self._h, ptr, on_dev), "voldor_set_flows")
+
+    def bootstrap(self, T1):
+        T1, p = _f64(T1)
+        _check(lib().voldor_bootstrap(self._h, BOOT_GIVEN_POSE, p), "voldor_bootstrap")
+
+    def em_step(self, n_iters, allow_degenerate=True):
+        allow = (ERR_DEGENERATE,) if allow_degenerate else ()
+        return _check(lib().voldor_em_step(self._h, int(n_iters)), "voldor_em_step", allow)
+
+    def get_pose_depth_rigidness(self, poses=True, depth=True, rigidness=True):
+        P = np.zeros((self.T, 4, 4)) if poses else None
+        D = np.zeros((self.H, self.W), np.float32) if depth else None
+        Wm = np.zeros((self.T, self.H, self.W), np.float32) if rigidness else None
+        nul = lambda a, t: a.ctypes.data_as(C.POINTER(t)) if a is not None else None
+        _check(lib().voldor_get_pose_depth_rigidness(self._h, nul(P, C.c_double), nul(D, C.c_float),
+                                                     nul(Wm, C.c_float)), "voldor_get_pose_depth_rigidness")
+        return P, D, Wm
+
+    # -- stage calls ------------------------------------------------------------
+    def set_state(self, poses=None, depth=None, rigidness=None, iteration=0):
+        keep = []
+
+        def arg(a, conv):
+            if a is None:
+                return None
+            a, p = conv(a)
+            keep.append(a)
+            return p
+
+        _check(lib().voldor_set_state(self._h, arg(poses, _f64), arg(depth, _f32), arg(rigidness, _f32),
+                                      int(iteration)), "voldor_set_state")
+
+    def pose_update(self, k, t):
+        return _check(lib().voldor_pose_update(self._h, int(k), int(t)), "voldor_pose_update", (ERR_DEGENERATE,))
+
+    def score_hypotheses(self, t, R, tv):
+        R, pR = _f64(R)
+        tv, pt = _f64(tv)
+        n = R.shape[0]
+        L = np.zeros(n)
+        _check(lib().voldor_score_hypotheses(self._h, int(t), n, pR, pt, L.ctypes.data_as(C.POINTER(C.c_double))),
+               "voldor_score_hypotheses")
+        return L
+
+    def rigidness_smooth(self, k):
+        _check(lib().voldor_rigidness_smooth(self._h, int(k)), "voldor_rigidness_smooth")
+
+    def depth_update(self, k):
+        _check(lib().voldor_depth_update(self._h, int(k)), "voldor_depth_update")
+
+    def rigidness_update(self):
+        _check(lib().voldor_rigidness_update(self._h), "voldor_rigidness_update")
+
+    def get_buffer(self, which, shape, dtype):
+        out = np.zeros(shape, dtype=dtype)
+        _check(lib().voldor_get_buffer(self._h, which, C.c_void_p(out.ctypes.data), out.nbytes), "voldor_get_buffer")
+        return out
+
+    def set_buffer(self, which, arr):
+        arr = np.ascontiguousarray(arr)
+        _check(lib().voldor_set_buffer(self._h, which, C.c_void_p(arr.ctypes.data), arr.nbytes), "voldor_set_buffer")
+
+    def enable_timing(self, on=True):
+        _check(lib().voldor_enable_timing(self._h, int(bool(on))), "voldor_enable_timing")
+
+    def get_score_times(self, max_n=1024):
+        """(ms per scoring launch, pairs per launch) of the last timed em_step."""
+        ms = np.zeros(max_n, np.float32)
+        pairs = np.zeros(max_n, np.int64)
+        n = C.c_int(0)
+        _check(lib().voldor_get_score_times(self._h, ms.ctypes.data_as(C.POINTER(C.c_float)),
+                                            pairs.ctypes.data_as(C.POINTER(C.c_longlong)), max_n, C.byref(n)),
+               "voldor_get_score_times")
+        m = min(n.value, max_n)
+        return ms[:m], pairs[:m]
+
+    def kernel_launches(self):
+        return int(lib().voldor_kernel_launches(self._h))
+
+    def device_bytes(self):
+        return lib().voldor_device_bytes(self._h)
+
+    # -- convenience readers of the stage buffers -----------------------------------
+    def hypotheses(self):
+        S = self.params.hyps_per_frame
+        info = self.get_buffer(BUF_POSE_INFO, (4,), np.int32)
+        n = int(info[0])
+        hyps = self.get_buffer(BUF_HYPS, (S, 12), np.float64)[:n]
+        hinfo = self.get_buffer(BUF_HYP_INFO, (S, 2), np.int64)[:n]
+        w = self.get_buffer(BUF_HYP_WEIGHT, (S,), np.float64)[:n]
+        L = self.get_buffer(BUF_SCORES, (S,), np.float64)[:n]
+        return dict(R=hyps[:, :9].reshape(-1, 3, 3), t=hyps[:, 9:], group=hinfo[:, 0], slot=hinfo[:, 1],
+                    weight=w, L=L, seed=int(info[1]), ms_iters=int(info[2]), degenerate=int(info[3]))
+
+
+def init_window(flows, K, params=None, stream=None) -> Window:
+    return Window(flows, K, params, stream)

@@ -1,0 +1,145 @@
+"""GPU parity: each CUDA stage against the FP64 oracle, teacher-forced (both
+sides get the same FP32-representable state and run one sub-step).
+
+Tolerances (derived in the design notes from the FP32 arithmetic):
+  - dense scores L_h: 1e-5 relative (the benchmark spec's tolerance);
+  - per-pixel log-likelihood terms and rigidness maps: absolute 2e-5 on
+    quantities in [0, 1], relative 1e-5 on sums;
+  - P3P hypotheses: identical group indices and slots, poses to 1e-9;
+  - pose after meanshift: 1e-6 rad and 1e-6 relative translation;
+  - depth candidates: identical labels on >= 99.9% of pixels.
+"""
+import numpy as np
+import pytest
+
+from tests.helpers import f32_hypotheses, f32_state, oracle_window, pose_close, small_window
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vd():
+    from paper_2104_06789_gb300 import build, voldor
+    build.build()
+    return voldor
+
+
+@pytest.fixture(scope="module")
+def scene():
+    return small_window(seed=1000)
+
+
+def _gpu_window(vd, w, S=256, flows=None, **kw):
+    flows = w.flows.astype(np.float32) if flows is None else flows
+    p = vd.default_params(hyps_per_frame=S, groups_per_frame=2 * S,
+                          inv_depth_min=w.inv_depth_range[0], inv_depth_max=w.inv_depth_range[1], **kw)
+    return vd.Window(flows, w.K, p)
+
+
+def test_bootstrap(vd, oracle_lib, scene):
+    w = scene
+    g = _gpu_window(vd, w)
+    g.bootstrap(w.poses[0])
+    P, D, Wm = g.get_pose_depth_rigidness()
+    ow = oracle_lib.OracleWindow(w.flows.astype(np.float32).astype(np.float64), w.K, S=8,
+                                 inv_depth_min=w.inv_depth_range[0], inv_depth_max=w.inv_depth_range[1])
+    ow.bootstrap(w.poses[0])
+    assert np.all(Wm == 1.0)
+    assert np.allclose(P, np.broadcast_to(w.poses[0], P.shape), rtol=0, atol=0)
+    rel = np.abs(D - ow.theta) / ow.theta
+    # FP32 triangulation: the parallax term cancels to ~1e-3 of its parts
+    assert np.quantile(rel, 0.999) < 1e-4
+    assert rel.max() < 1e-2
+
+
+@pytest.mark.parametrize("t", [1, 2, 3])
+def test_dense_scores(vd, oracle_lib, scene, t):
+    w = scene
+    rng = np.random.default_rng(10 + t)
+    depth, rig = f32_state(rng, w)
+    g = _gpu_window(vd, w)
+    g.set_state(poses=w.poses, depth=depth, rigidness=rig, iteration=0)
+    ow = oracle_window(oracle_lib, w, w.flows.astype(np.float32).astype(np.float64), 256, depth, rig, w.poses)
+    R, tv = f32_hypotheses(rng, w.poses[t - 1][:3, :3], w.poses[t - 1][:3, 3], 64)
+    L_gpu = g.score_hypotheses(t, R, tv)
+    L_ref = ow.score(t, R, tv)
+    rel = np.abs(L_gpu - L_ref) / np.abs(L_ref)
+    assert rel.max() < 1e-5, rel.max()
+
+
+@pytest.mark.parametrize("t", [1, 3])
+def test_pose_update(vd, oracle_lib, scene, t):
+    w = scene
+    rng = np.random.default_rng(20 + t)
+    depth, rig = f32_state(rng, w)
+    rig = (0.5 + 0.5 * rig).astype(np.float32)
+    g = _gpu_window(vd, w)
+    g.set_state(poses=w.poses, depth=depth, rigidness=rig, iteration=1)
+    ow = oracle_window(oracle_lib, w, w.flows.astype(np.float32).astype(np.float64), 256, depth, rig, w.poses)
+    k = 1
+    g.pose_update(k, t)
+    hg = g.hypotheses()
+    R, tv, wts, grp, slot = ow.collect_hypotheses(k, t)
+    assert len(hg["R"]) == len(R)
+    assert np.array_equal(hg["group"], grp) and np.array_equal(hg["slot"], slot)
+    assert np.array_equal(hg["weight"], wts)
+    assert np.abs(hg["R"] - R).max() < 1e-9 and np.abs(hg["t"] - tv).max() < 1e-9
+    # scores of the FP32 scoring form, scored by the oracle
+    f32 = g.get_buffer(vd.BUF_HYPS_F32, (256, 12), np.float32)[:len(R)].astype(np.float64)
+    Rf = np.eye(3) + f32[:, :9].reshape(-1, 3, 3)
+    L_ref = ow.score(t, Rf, f32[:, 9:])
+    rel = np.abs(hg["L"] - L_ref) / np.abs(L_ref)
+    assert rel.max() < 1e-5
+    # the pose: oracle's full update on the same state
+    st, n, L_o, seed_o, its = ow.pose_update(k, t)
+    P_gpu, _, _ = g.get_pose_depth_rigidness(depth=False, rigidness=False)
+    ok, ang, dt = pose_close(P_gpu[t - 1], ow.poses[t - 1])
+    assert ok, (ang, dt, hg["seed"], seed_o)
+
+
+@pytest.mark.parametrize("k", [0, 1])
+def test_smoothed_rigidness(vd, oracle_lib, scene, k):
+    w = scene
+    rng = np.random.default_rng(30 + k)
+    depth, rig = f32_state(rng, w)
+    g = _gpu_window(vd, w)
+    g.set_state(poses=w.poses, depth=depth, rigidness=rig, iteration=k)
+    ow = oracle_window(oracle_lib, w, w.flows.astype(np.float32).astype(np.float64), 256, depth, rig, w.poses)
+    g.rigidness_smooth(k)
+    q_gpu = g.get_buffer(vd.BUF_SMOOTHED, (w.T, w.H, w.W), np.float32)
+    em = ow.emissions()
+    q_ref = ow.smooth(0 if k % 2 == 0 else 1, em)
+    assert np.abs(q_gpu - q_ref).max() < 2e-5
+
+
+def test_unsmoothed_rigidness(vd, oracle_lib, scene):
+    w = scene
+    rng = np.random.default_rng(40)
+    depth, rig = f32_state(rng, w)
+    g = _gpu_window(vd, w)
+    g.set_state(poses=w.poses, depth=depth, rigidness=rig, iteration=0)
+    ow = oracle_window(oracle_lib, w, w.flows.astype(np.float32).astype(np.float64), 256, depth, rig, w.poses)
+    g.rigidness_update()
+    _, _, W_gpu = g.get_pose_depth_rigidness(poses=False, depth=False)
+    W_ref = ow.emissions()
+    assert np.abs(W_gpu - W_ref).max() < 2e-5
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
+def test_depth_sweep(vd, oracle_lib, scene, k):
+    w = scene
+    rng = np.random.default_rng(50 + k)
+    depth, rig = f32_state(rng, w)
+    q = rng.uniform(0, 1, size=(w.T, w.H, w.W)).astype(np.float32)
+    g = _gpu_window(vd, w)
+    g.set_state(poses=w.poses, depth=depth, rigidness=rig, iteration=k)
+    g.set_buffer(vd.BUF_SMOOTHED, q)
+    ow = oracle_window(oracle_lib, w, w.flows.astype(np.float32).astype(np.float64), 256, depth, rig, w.poses)
+    g.depth_update(k)
+    lab_gpu = g.get_buffer(vd.BUF_LABELS, (w.H, w.W), np.uint8)
+    _, D_gpu, _ = g.get_pose_depth_rigidness(poses=False, rigidness=False)
+    lab_ref = ow.mie_sweep(k, q.astype(np.float64))
+    same = np.mean(lab_gpu == lab_ref)
+    assert same >= 0.999, same
+    agree = np.abs(D_gpu - ow.theta) <= 1e-5 * ow.theta
+    assert np.mean(agree) >= 0.999
