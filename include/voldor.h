@@ -192,6 +192,10 @@ voldor_status voldor_get_score_times(voldor_ctx* ctx, float* ms, long long* pair
  * count every kernel node of the graph). */
 long long voldor_kernel_launches(const voldor_ctx* ctx);
 
+/* The CUDA runtime's description of the error that poisoned the context
+ * ("no CUDA error" if none). The string is static. */
+const char* voldor_last_error_string(const voldor_ctx* ctx);
+
 /* Device memory held by the context, bytes. */
 size_t voldor_device_bytes(const voldor_ctx* ctx);
 

@@ -1,26 +1,26 @@
-// Per-pixel kernels of the VOLDOR loop: bootstrap triangulation, frame pose
-// setup, pose preparation (dense-scoring records), E-step emissions and
-// forward-backward smoothing, MIE depth sweep, unsmoothed rigidness.
+// Per-pixel kernels of the VOLDOR loop: frame pose setup, bootstrap
+// triangulation, pose preparation (dense-scoring records), E-step emissions
+// and forward-backward smoothing, MIE depth sweep, unsmoothed rigidness.
 //
+// Geometry is FP64 and likelihood arithmetic FP32 (see geom_prev/ell_frame).
 // This translation unit is compiled without FMA contraction (--fmad=false):
 // the MIE sweep compares a candidate scored in one kernel with one scored in
-// another, and equal depths must give bit-identical scores. Fused
-// multiply-adds are written out with fmaf where they are wanted.
+// another, and equal depths must give bit-identical scores.
 #include "voldor_internal.cuh"
 
 namespace vd {
 
 // ---------------------------------------------------------------------------
-// Frame setup: C_{t-1} = T_{t-1} ... T_1 (FP64) and T_t in the scaled
-// cancellation-free form, cast to FP32 for per-pixel work (Eq. 1).
+// Frame setup: C_{t-1} = T_{t-1} ... T_1 for every t (FP64), the product of
+// Eq. 1 with T_t the motion from t-1 to t.
 // ---------------------------------------------------------------------------
 __global__ void k_frame_setup(DevParams p, DevState s)
 {
-    const int t = threadIdx.x + 1;
-    if (t > p.T) return;
+    if (threadIdx.x != 0) return;
     double C[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
-    for (int i = 1; i < t; ++i) {
-        const double* A = s.poses + 12 * (i - 1);
+    for (int t = 1; t <= p.T; ++t) {
+        for (int q = 0; q < 12; ++q) s.cum[12 * (t - 1) + q] = C[q];
+        const double* A = s.poses + 12 * (t - 1);
         double O[12];
         for (int r = 0; r < 3; ++r) {
             for (int c = 0; c < 3; ++c)
@@ -29,20 +29,6 @@ __global__ void k_frame_setup(DevParams p, DevState s)
         }
         for (int q = 0; q < 12; ++q) C[q] = O[q];
     }
-    for (int q = 0; q < 12; ++q) s.cum[12 * (t - 1) + q] = C[q];
-    FrameF f;
-    for (int r = 0; r < 3; ++r) {
-        for (int c = 0; c < 3; ++c) f.Rc[r * 3 + c] = (float)C[r * 4 + c];
-        f.tc[r] = (float)C[r * 4 + 3];
-    }
-    const double* Tt = s.poses + 12 * (t - 1);
-    const double q = p.fyd / p.fxd;
-    const double sc[3] = {1.0, q, 1.0};
-    for (int r = 0; r < 3; ++r) {
-        for (int c = 0; c < 3; ++c) f.E[r * 3 + c] = (float)(sc[r] * (Tt[r * 4 + c] - (r == c ? 1.0 : 0.0)) / sc[c]);
-        f.tt[r] = (float)(sc[r] * Tt[r * 4 + 3]);
-    }
-    s.frames[t - 1] = f;
 }
 
 void launch_frame_setup(const DevParams& p, const DevState& s, cudaStream_t st)
@@ -50,17 +36,30 @@ void launch_frame_setup(const DevParams& p, const DevState& s, cudaStream_t st)
     k_frame_setup<<<1, 32, 0, st>>>(p, s);
 }
 
+// Stages C_{t-1} and T_t of every frame in shared memory.
+struct FramesD {
+    double C[kMaxT][12];
+    double Tt[kMaxT][12];
+};
+
+__device__ __forceinline__ void load_frames(const DevParams& p, const DevState& s, FramesD& f)
+{
+    for (int i = threadIdx.x; i < p.T * 12; i += blockDim.x) {
+        f.C[i / 12][i % 12] = s.cum[i];
+        f.Tt[i / 12][i % 12] = s.poses[i];
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // Bootstrap (Table 1): W := 1, poses := T_1, k := 0, and per pixel the
 // least-squares depth along the ray of pixel j from x_j + X_1^j ~ pi_1(theta).
-// With d = K^-1 [x y 1], m = K^-1 [x+u y+v 1], R d = d + E d:
+// With d = K^-1 [x y 1], m = K^-1 [x+u y+v 1]:
 //   a_x = (R d)_x - m_x (R d)_z,  b_x = m_x t_z - t_x  (same for y),
-//   theta = (a.b)/(a.a), i.e. inverse depth (a.a)/(a.b), clamped.
+//   theta = (a.b)/(a.a), i.e. inverse depth (a.a)/(a.b), clamped; FP64.
 // ---------------------------------------------------------------------------
 struct BootPose {
     double T[12];
-    float E[9];
-    float t[3];
 };
 
 __global__ void k_bootstrap(DevParams p, DevState s, BootPose bp)
@@ -74,40 +73,28 @@ __global__ void k_bootstrap(DevParams p, DevState s, BootPose bp)
     if (j >= p.N) return;
     for (int t = 0; t < p.T; ++t) s.wmap[(size_t)t * p.N + j] = 1.f;
     const int x = j % p.W, y = j / p.W;
-    const float dx = ((float)x - p.cx) * p.inv_fx;
-    const float dy = ((float)y - p.cy) * p.inv_fy;
+    const double* M = bp.T;
+    const double dx = ((double)x - p.cxd) / p.fxd, dy = ((double)y - p.cyd) / p.fyd;
     const float2 f = load_flow(s.flows, p.flow_f16, (size_t)j);
-    const float Edx = fmaf(bp.E[0], dx, fmaf(bp.E[1], dy, bp.E[2]));
-    const float Edy = fmaf(bp.E[3], dx, fmaf(bp.E[4], dy, bp.E[5]));
-    const float Edz = fmaf(bp.E[6], dx, fmaf(bp.E[7], dy, bp.E[8]));
-    const float mu_x = f.x * p.inv_fx, mu_y = f.y * p.inv_fy;      // m - d
-    const float Rdz = 1.f + Edz;
-    const float ax = Edx - dx * Edz - mu_x * Rdz;
-    const float ay = Edy - dy * Edz - mu_y * Rdz;
-    const float mx = dx + mu_x, my = dy + mu_y;
-    const float bx = fmaf(mx, bp.t[2], -bp.t[0]);
-    const float by = fmaf(my, bp.t[2], -bp.t[1]);
-    const float num = fmaf(ax, ax, ay * ay);
-    const float den = fmaf(ax, bx, ay * by);
-    float inv = p.inv_depth_min;
-    if (den > 0.f) {
-        const float r = num / den;
-        if (isfinite(r)) inv = fminf(fmaxf(r, p.inv_depth_min), p.inv_depth_max);
+    const double mx = ((double)x + f.x - p.cxd) / p.fxd, my = ((double)y + f.y - p.cyd) / p.fyd;
+    const double Rdx = M[0] * dx + M[1] * dy + M[2];
+    const double Rdy = M[4] * dx + M[5] * dy + M[6];
+    const double Rdz = M[8] * dx + M[9] * dy + M[10];
+    const double ax = Rdx - mx * Rdz, bx = mx * M[11] - M[3];
+    const double ay = Rdy - my * Rdz, by = my * M[11] - M[7];
+    const double num = ax * ax + ay * ay, den = ax * bx + ay * by;
+    double inv = (double)p.inv_depth_min;
+    if (den > 0.0) {
+        const double r = num / den;
+        if (isfinite(r)) inv = fmin(fmax(r, (double)p.inv_depth_min), (double)p.inv_depth_max);
     }
-    s.theta[j] = 1.f / inv;
+    s.theta[j] = (float)(1.0 / inv);
 }
 
 void launch_bootstrap(const DevParams& p, const DevState& s, const double* T1, cudaStream_t st)
 {
     BootPose bp;
-    for (int r = 0; r < 3; ++r) {
-        for (int c = 0; c < 3; ++c) {
-            bp.T[r * 4 + c] = T1[r * 4 + c];
-            bp.E[r * 3 + c] = (float)(T1[r * 4 + c] - (r == c ? 1.0 : 0.0));
-        }
-        bp.T[r * 4 + 3] = T1[r * 4 + 3];
-        bp.t[r] = (float)T1[r * 4 + 3];
-    }
+    for (int q = 0; q < 12; ++q) bp.T[q] = T1[q];
     const int nb = (p.N + kPixThreads - 1) / kPixThreads;
     k_bootstrap<<<nb, kPixThreads, 0, st>>>(p, s, bp);
 }
@@ -118,14 +105,14 @@ void launch_bootstrap(const DevParams& p, const DevState& s, const double* T1, c
 // ---------------------------------------------------------------------------
 __global__ void k_prep_count(DevParams p, DevState s, int t)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    __shared__ FrameF fr;
-    if (threadIdx.x == 0) fr = s.frames[t - 1];
+    __shared__ double C[12];
+    if (threadIdx.x < 12) C[threadIdx.x] = s.cum[12 * (t - 1) + threadIdx.x];
     __syncthreads();
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
     bool valid = false;
     if (j < p.N) {
-        PixGeom g;
-        valid = pixel_geometry(p, fr, s.flows, t, j % p.W, j / p.W, s.theta[j], g);
+        GeomD g;
+        valid = geom_prev(p, C, s.flows, t, j % p.W, j / p.W, s.theta[j], g);
     }
     const int cnt = __syncthreads_count(valid);
     if (threadIdx.x == 0) s.pix_block_count[blockIdx.x] = cnt;
@@ -133,11 +120,10 @@ __global__ void k_prep_count(DevParams p, DevState s, int t)
 
 __global__ void k_prep_write(DevParams p, DevState s, int t)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    __shared__ FrameF fr;
+    __shared__ double C[12];
     __shared__ int warp_sum[kPixThreads / 32];
     __shared__ int base;
-    if (threadIdx.x == 0) fr = s.frames[t - 1];
+    if (threadIdx.x < 12) C[threadIdx.x] = s.cum[12 * (t - 1) + threadIdx.x];
     // offset of this block: sum of the counts of all earlier blocks
     int acc = 0;
     for (int b = threadIdx.x; b < (int)blockIdx.x; b += blockDim.x) acc += s.pix_block_count[b];
@@ -150,10 +136,10 @@ __global__ void k_prep_write(DevParams p, DevState s, int t)
         base = tot;
     }
     __syncthreads();
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
     bool valid = false;
-    PixGeom g;
-    if (j < p.N) valid = pixel_geometry(p, fr, s.flows, t, j % p.W, j / p.W, s.theta[j], g);
-    // rank within the block
+    GeomD g;
+    if (j < p.N) valid = geom_prev(p, C, s.flows, t, j % p.W, j / p.W, s.theta[j], g);
     const unsigned bal = __ballot_sync(0xffffffffu, valid);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __syncthreads();
@@ -162,10 +148,13 @@ __global__ void k_prep_write(DevParams p, DevState s, int t)
     int rank = __popc(bal & ((1u << lane) - 1u));
     for (int w = 0; w < warp; ++w) rank += warp_sum[w];
     if (valid) {
-        const FiskConst fc = fisk_const(p, g.vob);
+        const float n = (float)sqrt(g.fu * g.fu + g.fv * g.fv);
+        const FiskConst fc = fisk_const(p, n);
+        const double iz = 1.0 / g.Pz;
         PixRec r;
-        r.a = make_float4(g.xb, g.yb2, g.w, g.vob.x * p.inv_fx);
-        r.b = make_float4(g.vob.y * p.inv_fx, fc.beta, fc.beta_k, fc.Cp);
+        r.a = make_float4((float)(g.Px * iz), (float)(p.fyd / p.fxd * g.Py * iz), (float)iz, (float)(g.fu / p.fxd));
+        r.b = make_float4((float)(g.fv / p.fxd), fc.beta, fc.beta * (p.log2_fx2 - fc.log2_alpha),
+                          (float)(p.fxd * p.fxd) * fc.mu_over_beta);
         r.c = make_float4(s.wmap[(size_t)(t - 1) * p.N + j], 0.f, 0.f, 0.f);
         s.pix[base + rank] = r;
     }
@@ -183,34 +172,27 @@ void launch_pose_prep(const DevParams& p, const DevState& s, int t, cudaStream_t
     k_prep_write<<<nb, kPixThreads, 0, st>>>(p, s, t);
 }
 
-// ---------------------------------------------------------------------------
-// Per-(t, j) evaluation at a given depth: log[rho/(rho+mu)], log(1/2) where
-// the model takes rho := mu.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float frame_ell(const DevParams& p, const FrameF& fr, const void* flows, int t, int x,
-                                           int y, float depth)
+// ell_t(j) at a given depth under the current poses; log(1/2) where the model
+// takes rho := mu (pi_{t-1} invalid or behind camera t).
+__device__ __forceinline__ float depth_ell(const DevParams& p, const FramesD& f, const void* flows, int t, int x, int y,
+                                           float depth)
 {
-    PixGeom g;
-    if (!pixel_geometry(p, fr, flows, t, x, y, depth, g)) return -0.69314718055994531f;
-    const FiskConst fc = fisk_const(p, g.vob);
-    return pixel_ell(p, fr, g, fc);
+    GeomD g;
+    if (!geom_prev(p, f.C[t - 1], flows, t, x, y, depth, g)) return -0.69314718055994531f;
+    return ell_frame(p, f.Tt[t - 1], g);
 }
 
 // Emissions rho/(rho+mu) of every (t, j) at the current depth (E-step input)
 // or, written into W, the unsmoothed rigidness update.
 __global__ void k_emissions(DevParams p, DevState s, float* out)
 {
-    __shared__ FrameF frs[kMaxT];
-    if (threadIdx.x < p.T) frs[threadIdx.x] = s.frames[threadIdx.x];
-    __syncthreads();
+    __shared__ FramesD f;
+    load_frames(p, s, f);
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= p.N) return;
     const int x = j % p.W, y = j / p.W;
     const float depth = s.theta[j];
-    for (int t = 1; t <= p.T; ++t) {
-        const float ell = frame_ell(p, frs[t - 1], s.flows, t, x, y, depth);
-        out[(size_t)(t - 1) * p.N + j] = expf(ell);
-    }
+    for (int t = 1; t <= p.T; ++t) out[(size_t)(t - 1) * p.N + j] = expf(depth_ell(p, f, s.flows, t, x, y, depth));
 }
 
 void launch_emissions(const DevParams& p, const DevState& s, float* out, cudaStream_t st)
@@ -284,15 +266,15 @@ void launch_forward_backward(const DevParams& p, const DevState& s, cudaStream_t
 // MIE depth update (Eq. 10, Fig. 5).
 // Prepare: per pixel, the scores of the prev and smp candidates
 // (sum over t of q_s * ell, in order t = 1..T) and the smp depth.
-// Sweep: one warp per chain, lane t-1 evaluates frame t of the nbr candidate.
+// Sweep: one warp per chain, lane t-1 evaluates frame t of the nbr candidate;
+// lane sums are added in the same order t = 1..T.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float nan_to_ninf(float v) { return isnan(v) ? -INFINITY : v; }
 
 __global__ void k_mie_prepare(DevParams p, DevState s)
 {
-    __shared__ FrameF frs[kMaxT];
-    if (threadIdx.x < p.T) frs[threadIdx.x] = s.frames[threadIdx.x];
-    __syncthreads();
+    __shared__ FramesD f;
+    load_frames(p, s, f);
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= p.N) return;
     const int k = *s.iter;
@@ -304,8 +286,8 @@ __global__ void k_mie_prepare(DevParams p, DevState s)
     float sp = 0.f, ss = 0.f;
     for (int t = 1; t <= p.T; ++t) {
         const float q = s.qs[(size_t)(t - 1) * p.N + j];
-        sp = __fadd_rn(sp, __fmul_rn(q, frame_ell(p, frs[t - 1], s.flows, t, x, y, prev)));
-        ss = __fadd_rn(ss, __fmul_rn(q, frame_ell(p, frs[t - 1], s.flows, t, x, y, smp)));
+        sp = __fadd_rn(sp, __fmul_rn(q, depth_ell(p, f, s.flows, t, x, y, prev)));
+        ss = __fadd_rn(ss, __fmul_rn(q, depth_ell(p, f, s.flows, t, x, y, smp)));
     }
     s.mie_prev_score[j] = nan_to_ninf(sp);
     s.mie_smp[j] = smp;
@@ -314,6 +296,8 @@ __global__ void k_mie_prepare(DevParams p, DevState s)
 
 __global__ void k_mie_sweep(DevParams p, DevState s)
 {
+    __shared__ FramesD f;
+    load_frames(p, s, f);
     const int dir = (*s.iter) & 3;
     const bool rows = (dir == 0 || dir == 2);
     const int n_chains = rows ? p.H : p.W;
@@ -321,8 +305,6 @@ __global__ void k_mie_sweep(DevParams p, DevState s)
     const int lane = threadIdx.x & 31;
     const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (c >= n_chains) return;
-    FrameF fr;
-    if (lane < p.T) fr = s.frames[lane];
     const int t = lane + 1;
     float nbr = 0.f;
     for (int i = 0; i < len; ++i) {
@@ -341,7 +323,7 @@ __global__ void k_mie_sweep(DevParams p, DevState s)
             float e = 0.f;
             if (lane < p.T) {
                 const float q = s.qs[(size_t)(t - 1) * p.N + j];
-                e = __fmul_rn(q, frame_ell(p, fr, s.flows, t, x, y, nbr));
+                e = __fmul_rn(q, depth_ell(p, f, s.flows, t, x, y, nbr));
             }
             float tot = 0.f;
             for (int tt = 0; tt < p.T; ++tt) tot = __fadd_rn(tot, __shfl_sync(0xffffffffu, e, tt));

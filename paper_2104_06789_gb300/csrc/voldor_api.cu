@@ -33,6 +33,7 @@ struct voldor_ctx {
     int graph_pairs = 0;
     std::map<long long, long long> graph_kernels;   // kernel nodes per cached graph
     long long launches = 0;                          // kernels enqueued so far
+    cudaError_t first_error = cudaSuccess;           // the error that poisoned the context
 };
 
 namespace {
@@ -42,7 +43,10 @@ const voldor_status kCuda = VOLDOR_ERR_CUDA;
 bool cuda_ok(voldor_ctx* c, cudaError_t e)
 {
     if (e == cudaSuccess) return true;
-    if (c) c->poisoned = true;
+    if (c) {
+        if (c->first_error == cudaSuccess) c->first_error = e;
+        c->poisoned = true;
+    }
     return false;
 }
 
@@ -114,7 +118,6 @@ size_t layout(voldor_ctx& c, char* base)
     s.qs = (float*)take(T * N * 4);
     s.poses = (double*)take(T * 12 * 8);
     s.cum = (double*)take(T * 12 * 8);
-    s.frames = (FrameF*)take(T * sizeof(FrameF));
     s.iter = (int*)take(4);
     s.status = (int*)take(16);
     c.flag_dev = (int*)take(4);
@@ -593,6 +596,12 @@ voldor_status voldor_get_score_times(voldor_ctx* c, float* ms, long long* pairs,
 }
 
 long long voldor_kernel_launches(const voldor_ctx* c) { return c ? c->launches : 0; }
+
+const char* voldor_last_error_string(const voldor_ctx* c)
+{
+    if (!c || c->first_error == cudaSuccess) return "no CUDA error";
+    return cudaGetErrorString(c->first_error);
+}
 
 size_t voldor_device_bytes(const voldor_ctx* c) { return c ? c->arena_bytes : 0; }
 

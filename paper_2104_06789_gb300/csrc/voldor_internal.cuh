@@ -38,16 +38,6 @@ struct DevParams {
     uint64_t seed, window_id;
 };
 
-// FP32 form of the poses of frame t used by per-pixel work:
-// C_{t-1} = (Rc, tc) and T_t in the cancellation-free scaled form
-// E = S_y (R_t - I) S_y^-1, tt = S_y t_t with S_y = diag(1, fy/fx, 1).
-struct FrameF {
-    float Rc[9];
-    float tc[3];
-    float E[9];
-    float tt[3];
-};
-
 // Per-pixel record of a frame for dense scoring (three float4 = 48 B).
 //  a = {xb, yb2, w, ut}: normalised coords x/z, (fy/fx) y/z, inverse depth 1/z
 //      in camera t-1, observed flow u / fx
@@ -66,7 +56,6 @@ struct DevState {
     float* qs;                // [T][H][W] smoothed q (also emission scratch)
     double* poses;            // [T][12] row-major [R | t]
     double* cum;              // [T][12] C_{t-1} = T_{t-1} ... T_1 (FP64)
-    FrameF* frames;           // [T]
     int* iter;                // [1] iteration counter k
     int* status;              // [4] n_hyp, seed, meanshift steps, status bits
     // dense scoring scratch
@@ -155,86 +144,91 @@ __device__ __forceinline__ bool flow_bilinear(const DevParams& p, const void* fl
 }
 
 // ---------------------------------------------------------------------------
-// Per-pixel geometry of frame t (1-based) at depth `depth`: the point in
-// camera t-1 as (xb, yb2, w) and pi_{t-1}. False if P_z <= 0 or pi_{t-1}
-// leaves the image.
+// Per-pixel geometry of frame t (1-based) at depth `depth`, in FP64: the point
+// P in camera t-1 (Eq. 1 with C_{t-1}), pi_{t-1}, and the observed flow
+// X_t(pi_{t-1}) by bilinear interpolation. The per-pixel passes keep the
+// geometry in FP64 because the rigid flow (tens of px) cancels against the
+// observed flow down to residuals of a tenth of a pixel; the likelihood
+// arithmetic that follows is FP32. False if P_z <= 0 or pi_{t-1} leaves
+// [0, W-1] x [0, H-1].
 // ---------------------------------------------------------------------------
-struct PixGeom {
-    float xb, yb2, w;    // x/z, (fy/fx) y/z, 1/z in camera t-1
-    float2 vob;          // observed flow at pi_{t-1}
+struct GeomD {
+    double Px, Py, Pz;    // point in camera t-1
+    double u, v;          // pi_{t-1}
+    double fu, fv;        // observed flow X_t(pi_{t-1})
 };
 
-__device__ __forceinline__ bool pixel_geometry(const DevParams& p, const FrameF& fr, const void* flows, int t,
-                                               int x, int y, float depth, PixGeom& g)
+__device__ __forceinline__ bool geom_prev(const DevParams& p, const double* C, const void* flows, int t, int x, int y,
+                                          float depth, GeomD& g)
 {
-    const float dx = ((float)x - p.cx) * p.inv_fx;
-    const float dy = ((float)y - p.cy) * p.inv_fy;
-    float u, v;
+    const double th = (double)depth;
+    const double dx = ((double)x - p.cxd) / p.fxd, dy = ((double)y - p.cyd) / p.fyd;
     if (t == 1) {
-        if (!(depth > 0.f)) return false;
-        g.xb = dx;
-        g.yb2 = p.fy_over_fx * dy;
-        g.w = 1.f / depth;
-        u = (float)x;
-        v = (float)y;
+        g.Px = th * dx; g.Py = th * dy; g.Pz = th;
+        g.u = (double)x; g.v = (double)y;
+        if (!(th > 0.0)) return false;
     } else {
-        const float X = depth * dx, Y = depth * dy, Z = depth;
-        const float Px = fmaf(fr.Rc[0], X, fmaf(fr.Rc[1], Y, fmaf(fr.Rc[2], Z, fr.tc[0])));
-        const float Py = fmaf(fr.Rc[3], X, fmaf(fr.Rc[4], Y, fmaf(fr.Rc[5], Z, fr.tc[1])));
-        const float Pz = fmaf(fr.Rc[6], X, fmaf(fr.Rc[7], Y, fmaf(fr.Rc[8], Z, fr.tc[2])));
-        if (!(Pz > 0.f)) return false;
-        const float iz = 1.f / Pz;
-        const float xb = Px * iz, yb = Py * iz;
-        g.xb = xb;
-        g.yb2 = p.fy_over_fx * yb;
-        g.w = iz;
-        u = fmaf(p.fx, xb, p.cx);
-        v = fmaf(p.fy, yb, p.cy);
+        const double X = th * dx, Y = th * dy, Z = th;
+        g.Px = C[0] * X + C[1] * Y + C[2] * Z + C[3];
+        g.Py = C[4] * X + C[5] * Y + C[6] * Z + C[7];
+        g.Pz = C[8] * X + C[9] * Y + C[10] * Z + C[11];
+        if (!(g.Pz > 0.0)) return false;
+        const double iz = 1.0 / g.Pz;
+        g.u = p.fxd * g.Px * iz + p.cxd;
+        g.v = p.fyd * g.Py * iz + p.cyd;
     }
-    return flow_bilinear(p, flows, t - 1, u, v, g.vob);
+    if (!(g.u >= 0.0 && g.u <= (double)(p.W - 1) && g.v >= 0.0 && g.v <= (double)(p.H - 1))) return false;
+    const int x0 = min((int)floor(g.u), p.W - 2), y0 = min((int)floor(g.v), p.H - 2);
+    const double ax = g.u - x0, ay = g.v - y0;
+    const size_t base = (size_t)(t - 1) * p.N + (size_t)y0 * p.W + x0;
+    const float2 f00 = load_flow(flows, p.flow_f16, base), f10 = load_flow(flows, p.flow_f16, base + 1);
+    const float2 f01 = load_flow(flows, p.flow_f16, base + p.W), f11 = load_flow(flows, p.flow_f16, base + p.W + 1);
+    const double w00 = (1.0 - ax) * (1.0 - ay), w10 = ax * (1.0 - ay), w01 = (1.0 - ax) * ay, w11 = ax * ay;
+    g.fu = w00 * f00.x + w10 * f10.x + w01 * f01.x + w11 * f11.x;
+    g.fv = w00 * f00.y + w10 * f10.y + w01 * f01.y + w11 * f11.y;
+    return true;
 }
 
-// Fisk constants of an observed flow (Eqs. 5-7): beta, beta * log2(fx^2/alpha)
-// and Cp = fx^2 * mu / beta, with mu = F(lambda^2 |v|^2) written as
-// mu / beta = ys / (x_mu (1 + ys)^2), ys = 2^-|beta log2(x_mu / alpha)|.
+// Fisk quantities of an observed flow of magnitude n (Eqs. 5-7), FP32:
+// beta, log2(alpha), and mu / beta written as ys / (x_mu (1 + ys)^2) with
+// x_mu = lambda^2 n^2 and ys = 2^-|beta log2(x_mu / alpha)|.
 struct FiskConst {
-    float beta, beta_k, Cp;
+    float beta, log2_alpha, mu_over_beta;
 };
 
-__device__ __forceinline__ FiskConst fisk_const(const DevParams& p, float2 vob)
+__device__ __forceinline__ FiskConst fisk_const(const DevParams& p, float n)
 {
-    const float n = sqrtf(vob.x * vob.x + vob.y * vob.y);
-    const float log2_alpha = fmaf(p.a2_log2e, n, p.log2_a1);
-    const float beta = fmaxf(fmaf(p.b1, n, p.b2), p.beta_min);
+    FiskConst c;
+    c.log2_alpha = fmaf(p.a2_log2e, n, p.log2_a1);
+    c.beta = fmaxf(fmaf(p.b1, n, p.b2), p.beta_min);
     const float xmu = fminf(fmaxf(p.lambda2 * n * n, p.x_min), p.x_max);
-    const float smu = beta * (log2f(xmu) - log2_alpha);
+    const float smu = c.beta * (log2f(xmu) - c.log2_alpha);
     const float ys = exp2f(-fabsf(smu));
     const float g = 1.f + ys;
-    FiskConst c;
-    c.beta = beta;
-    c.beta_k = beta * (p.log2_fx2 - log2_alpha);
-    c.Cp = (p.fx * p.fx) * ys / (xmu * g * g);
+    c.mu_over_beta = ys / (xmu * g * g);
     return c;
 }
 
-// log[rho/(rho+mu)] (Eq. 10 term) of the residual between the rigid flow under
-// frame pose fr and the observation, accurate FP32 (library log/exp). Returns
+// log[rho/(rho+mu)] (Eq. 10 term) for frame pose T_t (FP64 [R | t]): rigid
+// flow and residual in FP64, the likelihood in FP32:
+//   r = mu / rho = (mu / beta) x (y + 2 + 1/y),  y = (x / alpha)^beta,
+//   ell = -log1p(r).
 // log(1/2) when the point is behind camera t (the model's rho := mu).
-__device__ __forceinline__ float pixel_ell(const DevParams& p, const FrameF& fr, const PixGeom& g,
-                                           const FiskConst& fc)
+__device__ __forceinline__ float ell_frame(const DevParams& p, const double* Tt, const GeomD& g)
 {
-    const float ax = fmaf(fr.E[0], g.xb, fmaf(fr.E[1], g.yb2, fmaf(fr.tt[0], g.w, fr.E[2])));
-    const float ay = fmaf(fr.E[3], g.xb, fmaf(fr.E[4], g.yb2, fmaf(fr.tt[1], g.w, fr.E[5])));
-    const float az = fmaf(fr.E[6], g.xb, fmaf(fr.E[7], g.yb2, fmaf(fr.tt[2], g.w, fr.E[8])));
-    const float den = 1.f + az;
-    if (!(den > 0.f)) return -0.69314718055994531f;
-    const float rd = 1.f / den;
-    const float ru = fmaf(fmaf(-g.xb, az, ax), rd, -g.vob.x * p.inv_fx);
-    const float rv = fmaf(fmaf(-g.yb2, az, ay), rd, -g.vob.y * p.inv_fx);
-    const float xs = fminf(fmaxf(fmaf(ru, ru, rv * rv), p.xs_min), p.xs_max);
-    const float s = fmaf(fc.beta, log2f(xs), fc.beta_k);
+    const double Qx = Tt[0] * g.Px + Tt[1] * g.Py + Tt[2] * g.Pz + Tt[3];
+    const double Qy = Tt[4] * g.Px + Tt[5] * g.Py + Tt[6] * g.Pz + Tt[7];
+    const double Qz = Tt[8] * g.Px + Tt[9] * g.Py + Tt[10] * g.Pz + Tt[11];
+    if (!(Qz > 0.0)) return -0.69314718055994531f;
+    const double iq = 1.0 / Qz;
+    const double ru = (p.fxd * Qx * iq + p.cxd - g.u) - g.fu;
+    const double rv = (p.fyd * Qy * iq + p.cyd - g.v) - g.fv;
+    const float x = (float)fmin(fmax(ru * ru + rv * rv, (double)p.x_min), (double)p.x_max);
+    const float n = (float)sqrt(g.fu * g.fu + g.fv * g.fv);
+    const FiskConst fc = fisk_const(p, n);
+    const float s = fc.beta * (log2f(x) - fc.log2_alpha);
     const float e = exp2f(fabsf(s));
-    const float r = fc.Cp * xs * (e + 2.f + 1.f / e);     // mu / rho
+    const float r = fc.mu_over_beta * x * (e + 2.f + 1.f / e);
     return -log1pf(r);
 }
 

@@ -78,6 +78,7 @@ def lib():
             "voldor_enable_timing": (i, [vp, i]),
             "voldor_get_score_times": (i, [vp, P(C.c_float), P(C.c_longlong), i, P(i)]),
             "voldor_kernel_launches": (C.c_longlong, [vp]),
+            "voldor_last_error_string": (C.c_char_p, [vp]),
             "voldor_device_bytes": (sz, [vp]),
         }
         for name, (res, args) in sig.items():
@@ -92,8 +93,10 @@ def status_string(s):
     return lib().voldor_status_string(int(s)).decode()
 
 
-def _check(st, where, allow=()):
+def _check(st, where, allow=(), handle=None):
     if st != OK and st not in allow:
+        if st == ERR_CUDA and handle:
+            where = f"{where} [{lib().voldor_last_error_string(handle).decode()}]"
         raise VoldorError(st, where)
     return st
 
@@ -168,15 +171,15 @@ class Window:
     def set_flows(self, flows):
         ptr, on_dev, dt, keep = _flow_arg(flows)
         assert dt == self.flow_dtype
-        _check(lib().voldor_set_flows(self._h, ptr, on_dev), "voldor_set_flows")
+        _check(lib().voldor_set_flows(self._h, ptr, on_dev), "voldor_set_flows", handle=self._h)
 
     def bootstrap(self, T1):
         T1, p = _f64(T1)
-        _check(lib().voldor_bootstrap(self._h, BOOT_GIVEN_POSE, p), "voldor_bootstrap")
+        _check(lib().voldor_bootstrap(self._h, BOOT_GIVEN_POSE, p), "voldor_bootstrap", handle=self._h)
 
     def em_step(self, n_iters, allow_degenerate=True):
         allow = (ERR_DEGENERATE,) if allow_degenerate else ()
-        return _check(lib().voldor_em_step(self._h, int(n_iters)), "voldor_em_step", allow)
+        return _check(lib().voldor_em_step(self._h, int(n_iters)), "voldor_em_step", allow, handle=self._h)
 
     def get_pose_depth_rigidness(self, poses=True, depth=True, rigidness=True):
         P = np.zeros((self.T, 4, 4)) if poses else None
@@ -184,7 +187,7 @@ class Window:
         Wm = np.zeros((self.T, self.H, self.W), np.float32) if rigidness else None
         nul = lambda a, t: a.ctypes.data_as(C.POINTER(t)) if a is not None else None
         _check(lib().voldor_get_pose_depth_rigidness(self._h, nul(P, C.c_double), nul(D, C.c_float),
-                                                     nul(Wm, C.c_float)), "voldor_get_pose_depth_rigidness")
+                                                     nul(Wm, C.c_float)), "voldor_get_pose_depth_rigidness", handle=self._h)
         return P, D, Wm
 
     # -- stage calls ------------------------------------------------------------
@@ -199,10 +202,10 @@ class Window:
             return p
 
         _check(lib().voldor_set_state(self._h, arg(poses, _f64), arg(depth, _f32), arg(rigidness, _f32),
-                                      int(iteration)), "voldor_set_state")
+                                      int(iteration)), "voldor_set_state", handle=self._h)
 
     def pose_update(self, k, t):
-        return _check(lib().voldor_pose_update(self._h, int(k), int(t)), "voldor_pose_update", (ERR_DEGENERATE,))
+        return _check(lib().voldor_pose_update(self._h, int(k), int(t)), "voldor_pose_update", (ERR_DEGENERATE,), handle=self._h)
 
     def score_hypotheses(self, t, R, tv):
         R, pR = _f64(R)
@@ -210,29 +213,29 @@ class Window:
         n = R.shape[0]
         L = np.zeros(n)
         _check(lib().voldor_score_hypotheses(self._h, int(t), n, pR, pt, L.ctypes.data_as(C.POINTER(C.c_double))),
-               "voldor_score_hypotheses")
+               "voldor_score_hypotheses", handle=self._h)
         return L
 
     def rigidness_smooth(self, k):
-        _check(lib().voldor_rigidness_smooth(self._h, int(k)), "voldor_rigidness_smooth")
+        _check(lib().voldor_rigidness_smooth(self._h, int(k)), "voldor_rigidness_smooth", handle=self._h)
 
     def depth_update(self, k):
-        _check(lib().voldor_depth_update(self._h, int(k)), "voldor_depth_update")
+        _check(lib().voldor_depth_update(self._h, int(k)), "voldor_depth_update", handle=self._h)
 
     def rigidness_update(self):
-        _check(lib().voldor_rigidness_update(self._h), "voldor_rigidness_update")
+        _check(lib().voldor_rigidness_update(self._h), "voldor_rigidness_update", handle=self._h)
 
     def get_buffer(self, which, shape, dtype):
         out = np.zeros(shape, dtype=dtype)
-        _check(lib().voldor_get_buffer(self._h, which, C.c_void_p(out.ctypes.data), out.nbytes), "voldor_get_buffer")
+        _check(lib().voldor_get_buffer(self._h, which, C.c_void_p(out.ctypes.data), out.nbytes), "voldor_get_buffer", handle=self._h)
         return out
 
     def set_buffer(self, which, arr):
         arr = np.ascontiguousarray(arr)
-        _check(lib().voldor_set_buffer(self._h, which, C.c_void_p(arr.ctypes.data), arr.nbytes), "voldor_set_buffer")
+        _check(lib().voldor_set_buffer(self._h, which, C.c_void_p(arr.ctypes.data), arr.nbytes), "voldor_set_buffer", handle=self._h)
 
     def enable_timing(self, on=True):
-        _check(lib().voldor_enable_timing(self._h, int(bool(on))), "voldor_enable_timing")
+        _check(lib().voldor_enable_timing(self._h, int(bool(on))), "voldor_enable_timing", handle=self._h)
 
     def get_score_times(self, max_n=1024):
         """(ms per scoring launch, pairs per launch) of the last timed em_step."""
@@ -241,7 +244,7 @@ class Window:
         n = C.c_int(0)
         _check(lib().voldor_get_score_times(self._h, ms.ctypes.data_as(C.POINTER(C.c_float)),
                                             pairs.ctypes.data_as(C.POINTER(C.c_longlong)), max_n, C.byref(n)),
-               "voldor_get_score_times")
+               "voldor_get_score_times", handle=self._h)
         m = min(n.value, max_n)
         return ms[:m], pairs[:m]
 

@@ -47,9 +47,7 @@ def test_bootstrap(vd, oracle_lib, scene):
     assert np.all(Wm == 1.0)
     assert np.allclose(P, np.broadcast_to(w.poses[0], P.shape), rtol=0, atol=0)
     rel = np.abs(D - ow.theta) / ow.theta
-    # FP32 triangulation: the parallax term cancels to ~1e-3 of its parts
-    assert np.quantile(rel, 0.999) < 1e-4
-    assert rel.max() < 1e-2
+    assert rel.max() < 1e-6          # FP64 triangulation, FP32 storage
 
 
 @pytest.mark.parametrize("t", [1, 2, 3])
@@ -122,7 +120,11 @@ def test_unsmoothed_rigidness(vd, oracle_lib, scene):
     g.rigidness_update()
     _, _, W_gpu = g.get_pose_depth_rigidness(poses=False, depth=False)
     W_ref = ow.emissions()
-    assert np.abs(W_gpu - W_ref).max() < 2e-5
+    # per-pixel log-likelihood ell = log W: 1e-5 relative, plus the FP32
+    # rounding of the stored W
+    ell_ref = np.log(W_ref)
+    err = np.abs(np.log(W_gpu.astype(np.float64)) - ell_ref)
+    assert np.all(err <= 1e-5 * np.abs(ell_ref) + 2.0 ** -23), err.max()
 
 
 @pytest.mark.parametrize("k", [0, 1, 2, 3])
