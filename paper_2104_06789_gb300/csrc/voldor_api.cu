@@ -184,9 +184,10 @@ bool enqueue_pose_update(voldor_ctx* c, int t, cudaEvent_t ev0, cudaEvent_t ev1,
     launch_pose_prep(p, s, t, st);
     launch_p3p_groups(p, s, t, st);
     launch_hyp_collect(p, s, st);
-    if (ev0 && !cuda_ok(c, cudaEventRecord(ev0, st))) return false;
+    // External records become event-record nodes when the stream is captured
+    if (ev0 && !cuda_ok(c, cudaEventRecordWithFlags(ev0, st, cudaEventRecordExternal))) return false;
     launch_score(p, s, log_idx, st);
-    if (ev1 && !cuda_ok(c, cudaEventRecord(ev1, st))) return false;
+    if (ev1 && !cuda_ok(c, cudaEventRecordWithFlags(ev1, st, cudaEventRecordExternal))) return false;
     launch_score_reduce(p, s, st);
     launch_meanshift(p, s, t, st);
     return launched(c);
