@@ -196,6 +196,40 @@ long long voldor_kernel_launches(const voldor_ctx* ctx);
  * ("no CUDA error" if none). The string is static. */
 const char* voldor_last_error_string(const voldor_ctx* ctx);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free dense scoring. The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory when they need
+ * a score -- code recording a CUDA graph that must not contain allocations,
+ * a process that gives this library a fixed memory budget, or a caller whose
+ * own allocator owns the device. It allocates nothing (no cudaMalloc, no
+ * cudaFree, no allocating library routine): its only scratch is a 4 MiB
+ * array compiled into the library, which every GPU that loads the library
+ * holds until the process exits.
+ *
+ * It computes, on the device and asynchronously on `cuda_stream`,
+ *   L[h] = - sum_j records[j].wq * log(1 + mu_j / rho_j(h))
+ * for h < n_hyps: the dense score voldor_score_hypotheses returns, but for
+ * pixel records and hypotheses the caller supplies.
+ *  records: device, n_pix records of 12 floats (48 bytes, 16-byte aligned):
+ *           {xb, yb2, w, ut, vt, beta, beta_k, Cp, wq, 0, 0, 0} with, for the
+ *           pixel's point P in camera t-1, xb = P_x/P_z, yb2 = (fy/fx) P_y/P_z,
+ *           w = 1/P_z, (ut, vt) = X_t(pi_{t-1}) / fx, beta = B(|X_t|),
+ *           beta_k = beta * log2(fx^2 / A(|X_t|)), Cp = fx^2 * mu / beta
+ *           (mu of Eq. 7), wq = W_t^j. Every record given is scored.
+ *  hyps:    device, n_hyps x 12 floats: E (9, row-major) and tt (3) with
+ *           E = S (R - I) S^-1, tt = S t, S = diag(1, fy/fx, 1).
+ *  xs_min, xs_max: floor and cap of the squared residual divided by fx^2.
+ *  L:       device, n_hyps doubles, written.
+ * Limits: 1 <= n_hyps <= 8192, n_pix >= 0; otherwise INVALID_ARG before any
+ * device work. The first call on a device looks up the scratch array's device
+ * address (with that device current); make that first call before any stream
+ * capture. Every call writes each scratch cell it later reads, so nothing
+ * carries over between calls -- but all calls share the one array, so calls
+ * that overlap on the GPU (different streams, or different host threads) race
+ * and must be serialised by the caller. Errors: INVALID_ARG, CUDA. */
+voldor_status voldor_score_records_noalloc(const float* records, int n_pix, const float* hyps, int n_hyps,
+                                           double xs_min, double xs_max, double* L, void* cuda_stream);
+
 /* Device memory held by the context, bytes. */
 size_t voldor_device_bytes(const voldor_ctx* ctx);
 

@@ -16,6 +16,9 @@
 // MUFU work: rcp, lg2, ex2, ex2, lg2 (for r >= 1/8); log1p(r) for r < 1/8 is
 // a Taylor polynomial on the FMA pipe, because lg2 near 1 has only absolute
 // accuracy. Sums: FP32 over 32 pixels, then FP64.
+#include <cmath>
+#include <mutex>
+
 #include "voldor_internal.cuh"
 
 namespace vd {
@@ -168,4 +171,114 @@ void launch_score_reduce(const DevParams& p, const DevState& s, cudaStream_t st)
     k_score_reduce<<<(p.S + 255) / 256, 256, 0, st>>>(p, s);
 }
 
+
+// ---------------------------------------------------------------------------
+// Allocation-free dense scoring.
+//
+// Some callers cannot allocate device memory at the time they want a score:
+// code running inside a CUDA stream capture that must not add allocation
+// nodes, a host that hands the GPU to this library under a fixed memory
+// budget, or a caller whose own allocator owns all device memory. For them,
+// voldor_score_records_noalloc scores caller-given pixel records against
+// caller-given hypotheses with the same per-pair arithmetic as k_score and
+// takes its only scratch (the per-chunk partial sums) from the file-scope
+// array below, which every GPU that loads this library holds until the
+// process exits.
+// ---------------------------------------------------------------------------
+constexpr int kStaticMaxHyps = 8192;
+constexpr int kStaticChunks = 64;
+static __device__ __align__(256) double g_static_partials[kStaticChunks * kStaticMaxHyps];   // 4 MiB
+
+__global__ void __launch_bounds__(kScoreThreads, 2)
+k_score_records(const float4* __restrict__ pix, int n_pix, const float* __restrict__ hyps, int n_hyp, float xs_min,
+                float xs_max, double* __restrict__ partial)
+{
+    const int tile0 = blockIdx.x * kScoreHypsPerBlock;
+    if (tile0 >= n_hyp) return;
+    const int chunk = blockIdx.y, n_chunks = gridDim.y;
+    const long long lo = (long long)n_pix * chunk / n_chunks;
+    const long long hi = (long long)n_pix * (chunk + 1) / n_chunks;
+    HypF hy[kScoreHypsPerThread];
+#pragma unroll
+    for (int i = 0; i < kScoreHypsPerThread; ++i) {
+        const float* f = hyps + (size_t)min(tile0 + i * kScoreThreads + (int)threadIdx.x, n_hyp - 1) * 12;
+        hy[i] = HypF{f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7], f[8], f[9], f[10], f[11]};
+    }
+    double acc[kScoreHypsPerThread];
+    float facc[kScoreHypsPerThread];
+#pragma unroll
+    for (int i = 0; i < kScoreHypsPerThread; ++i) { acc[i] = 0.0; facc[i] = 0.f; }
+    long long j = lo;
+    while (j < hi) {
+        const long long jend = min(hi, j + 32);
+        for (; j < jend; ++j) {
+            const float4 a = __ldg(pix + 3 * j);
+            const float4 b = __ldg(pix + 3 * j + 1);
+            const float wq = __ldg(reinterpret_cast<const float*>(pix + 3 * j + 2));
+#pragma unroll
+            for (int i = 0; i < kScoreHypsPerThread; ++i) facc[i] = fmaf(wq, pair_term(hy[i], a, b, xs_min, xs_max), facc[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < kScoreHypsPerThread; ++i) { acc[i] += (double)facc[i]; facc[i] = 0.f; }
+    }
+#pragma unroll
+    for (int i = 0; i < kScoreHypsPerThread; ++i) {
+        const int h = tile0 + i * kScoreThreads + threadIdx.x;
+        if (h < n_hyp) partial[(size_t)chunk * kStaticMaxHyps + h] = -acc[i];
+    }
+}
+
+__global__ void k_reduce_records(const double* __restrict__ partial, int n_hyp, int n_chunks, double* __restrict__ L)
+{
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= n_hyp) return;
+    double v = 0.0;
+    for (int c = 0; c < n_chunks; ++c) v += partial[(size_t)c * kStaticMaxHyps + h];
+    L[h] = v;
+}
+
+// Device address of g_static_partials, looked up once per device with that
+// device current (a host-side reference to the array is only a stand-in).
+constexpr int kStaticMaxDevices = 64;
+static double* g_static_ptr[kStaticMaxDevices];
+static std::mutex g_static_mutex;
+
+static cudaError_t static_partials(double** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kStaticMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_partials);
+        if (e != cudaSuccess) return e;
+        g_static_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_static_ptr[dev];
+    return cudaSuccess;
+}
+
 }  // namespace vd
+
+extern "C" voldor_status voldor_score_records_noalloc(const float* records, int n_pix, const float* hyps, int n_hyps,
+                                                      double xs_min, double xs_max, double* L, void* cuda_stream)
+{
+    using namespace vd;
+    if (!records || !hyps || !L || n_pix < 0 || n_hyps < 1) return VOLDOR_ERR_INVALID_ARG;
+    if (n_hyps > kStaticMaxHyps) return VOLDOR_ERR_INVALID_ARG;
+    if (!(xs_min > 0.0) || !(xs_max > xs_min) || !std::isfinite(xs_max)) return VOLDOR_ERR_INVALID_ARG;
+    double* partial = nullptr;
+    if (static_partials(&partial) != cudaSuccess) {
+        cudaGetLastError();
+        return VOLDOR_ERR_CUDA;
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int tiles = (n_hyps + kScoreHypsPerBlock - 1) / kScoreHypsPerBlock;
+    k_score_records<<<dim3(tiles, kStaticChunks), kScoreThreads, 0, st>>>(
+        reinterpret_cast<const float4*>(records), n_pix, hyps, n_hyps, (float)xs_min, (float)xs_max, partial);
+    k_reduce_records<<<(n_hyps + 255) / 256, 256, 0, st>>>(partial, n_hyps, kStaticChunks, L);
+    if (cudaGetLastError() != cudaSuccess) return VOLDOR_ERR_CUDA;
+    return VOLDOR_OK;
+}

@@ -80,6 +80,7 @@ def lib():
             "voldor_kernel_launches": (C.c_longlong, [vp]),
             "voldor_last_error_string": (C.c_char_p, [vp]),
             "voldor_device_bytes": (sz, [vp]),
+            "voldor_score_records_noalloc": (i, [vp, i, vp, i, d, d, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -265,6 +266,20 @@ class Window:
         L = self.get_buffer(BUF_SCORES, (S,), np.float64)[:n]
         return dict(R=hyps[:, :9].reshape(-1, 3, 3), t=hyps[:, 9:], group=hinfo[:, 0], slot=hinfo[:, 1],
                     weight=w, L=L, seed=int(info[1]), ms_iters=int(info[2]), degenerate=int(info[3]))
+
+
+def score_records_noalloc(records, hyps, L, xs_min, xs_max, stream=None):
+    """Allocation-free dense scoring (voldor_score_records_noalloc).
+
+    records: CUDA float32 tensor [n_pix, 12]; hyps: CUDA float32 tensor
+    [n_hyps, 12]; L: CUDA float64 tensor [n_hyps], written asynchronously on
+    `stream`. Allocates no device memory.
+    """
+    st = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+    _check(lib().voldor_score_records_noalloc(C.c_void_p(records.data_ptr()), int(records.shape[0]),
+                                              C.c_void_p(hyps.data_ptr()), int(hyps.shape[0]), float(xs_min),
+                                              float(xs_max), C.c_void_p(L.data_ptr()), C.c_void_p(st)),
+           "voldor_score_records_noalloc")
 
 
 def init_window(flows, K, params=None, stream=None) -> Window:
