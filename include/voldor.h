@@ -82,7 +82,7 @@ void voldor_default_params(voldor_params* p);
  *                   flows_on_device == 0, device memory of the current device
  *                   otherwise. Copied on `cuda_stream` (a cudaStream_t or NULL).
  *  params:          NULL = voldor_default_params().
- * Errors: INVALID_ARG (width < 2, height < 2, T < 1 or > 16, non-finite or
+ * Errors: INVALID_ARG (width or height < 2 or > 4096, T < 1 or > 16, non-finite or
  * non-positive focal lengths, invalid params), OOM, CUDA. *out is NULL on
  * error. */
 voldor_status voldor_init_window(voldor_ctx** out, int width, int height, int T,

@@ -74,9 +74,9 @@ __global__ void k_bootstrap(DevParams p, DevState s, BootPose bp)
     for (int t = 0; t < p.T; ++t) s.wmap[(size_t)t * p.N + j] = 1.f;
     const int x = j % p.W, y = j / p.W;
     const double* M = bp.T;
-    const double dx = ((double)x - p.cxd) / p.fxd, dy = ((double)y - p.cyd) / p.fyd;
+    const double dx = ((double)x - p.cxd) * p.inv_fxd, dy = ((double)y - p.cyd) * p.inv_fyd;
     const float2 f = load_flow(s.flows, p.flow_f16, (size_t)j);
-    const double mx = ((double)x + f.x - p.cxd) / p.fxd, my = ((double)y + f.y - p.cyd) / p.fyd;
+    const double mx = ((double)x + f.x - p.cxd) * p.inv_fxd, my = ((double)y + f.y - p.cyd) * p.inv_fyd;
     const double Rdx = M[0] * dx + M[1] * dy + M[2];
     const double Rdy = M[4] * dx + M[5] * dy + M[6];
     const double Rdz = M[8] * dx + M[9] * dy + M[10];
@@ -148,12 +148,12 @@ __global__ void k_prep_write(DevParams p, DevState s, int t)
     int rank = __popc(bal & ((1u << lane) - 1u));
     for (int w = 0; w < warp; ++w) rank += warp_sum[w];
     if (valid) {
-        const float n = (float)sqrt(g.fu * g.fu + g.fv * g.fv);
+        const float n = sqrtf((float)(g.fu * g.fu + g.fv * g.fv));
         const FiskConst fc = fisk_const(p, n);
-        const double iz = 1.0 / g.Pz;
+        const double iz = rcp64(g.Pz);
         PixRec r;
-        r.a = make_float4((float)(g.Px * iz), (float)(p.fyd / p.fxd * g.Py * iz), (float)iz, (float)(g.fu / p.fxd));
-        r.b = make_float4((float)(g.fv / p.fxd), fc.beta, fc.beta * (p.log2_fx2 - fc.log2_alpha),
+        r.a = make_float4((float)(g.Px * iz), (float)(p.fy_over_fx_d * g.Py * iz), (float)iz, (float)(g.fu * p.inv_fxd));
+        r.b = make_float4((float)(g.fv * p.inv_fxd), fc.beta, fc.beta * (p.log2_fx2 - fc.log2_alpha),
                           (float)(p.fxd * p.fxd) * fc.mu_over_beta);
         r.c = make_float4(s.wmap[(size_t)(t - 1) * p.N + j], 0.f, 0.f, 0.f);
         s.pix[base + rank] = r;
@@ -263,13 +263,51 @@ void launch_forward_backward(const DevParams& p, const DevState& s, cudaStream_t
 }
 
 // ---------------------------------------------------------------------------
-// MIE depth update (Eq. 10, Fig. 5).
-// Prepare: per pixel, the scores of the prev and smp candidates
-// (sum over t of q_s * ell, in order t = 1..T) and the smp depth.
-// Sweep: one warp per chain, lane t-1 evaluates frame t of the nbr candidate;
-// lane sums are added in the same order t = 1..T.
+// MIE depth update (Eq. 10, Fig. 5), chain-parallel with the exact sequential
+// semantics. Along a chain, the sequential sweep carries one value v (the
+// winner at the previous pixel) and at position i picks
+//   v           if S_i(v) > S_i(prev_i) and S_i(v) >= S_i(smp_i),
+//   own_i       otherwise, own_i = smp_i if S_i(smp_i) > S_i(prev_i) else prev_i,
+// where S_i(d) = sum_t q_s(t, i) ell_t(i; d) summed in order t = 1..T. So the
+// carried value is always own_r of the last position r where it was reset,
+// and it survives from r until the first position where it loses. Three
+// phases reproduce that bit for bit:
+//   prepare  per pixel: S(prev), smp, S(smp), own;
+//   runs     per pixel r (in parallel): test own_r at r+1, r+2, ... until it
+//            loses, at most kRunCap positions (speculation);
+//   resolve  per chain: follow r -> end of run from the chain start; a run
+//            that reached the cap is continued on the fly.
 // ---------------------------------------------------------------------------
+constexpr int kRunCap = 16;
+
 __device__ __forceinline__ float nan_to_ninf(float v) { return isnan(v) ? -INFINITY : v; }
+
+__device__ __forceinline__ float mie_score(const DevParams& p, const DevState& s, const FramesD& f, int x, int y, float d)
+{
+    const int j = y * p.W + x;
+    float acc = 0.f;
+    for (int t = 1; t <= p.T; ++t) {
+        const float q = s.qs[(size_t)(t - 1) * p.N + j];
+        acc = __fadd_rn(acc, __fmul_rn(q, depth_ell(p, f, s.flows, t, x, y, d)));
+    }
+    return nan_to_ninf(acc);
+}
+
+// Chain geometry: (x, y) of position i of chain c in direction dir.
+__device__ __forceinline__ void chain_xy(const DevParams& p, int dir, int c, int i, int& x, int& y)
+{
+    switch (dir) {
+        case 0: x = i; y = c; break;
+        case 1: x = c; y = i; break;
+        case 2: x = p.W - 1 - i; y = c; break;
+        default: x = c; y = p.H - 1 - i; break;
+    }
+}
+
+__device__ __forceinline__ bool survives(const DevState& s, int j, float sv)
+{
+    return sv > s.mie_prev_score[j] && sv >= s.mie_smp_score[j];
+}
 
 __global__ void k_mie_prepare(DevParams p, DevState s)
 {
@@ -282,61 +320,98 @@ __global__ void k_mie_prepare(DevParams p, DevState s)
     const U64x4 r = philox4x64_10((uint64_t)j, 0ull, (uint64_t)k, (uint64_t)kStreamDepth, p.seed, p.window_id);
     const float u = (float)(r.v[0] >> 40) * (1.f / 16777216.f);
     const float smp = 1.f / fmaf(u, p.inv_depth_max - p.inv_depth_min, p.inv_depth_min);
-    const float prev = s.theta[j];
-    float sp = 0.f, ss = 0.f;
-    for (int t = 1; t <= p.T; ++t) {
-        const float q = s.qs[(size_t)(t - 1) * p.N + j];
-        sp = __fadd_rn(sp, __fmul_rn(q, depth_ell(p, f, s.flows, t, x, y, prev)));
-        ss = __fadd_rn(ss, __fmul_rn(q, depth_ell(p, f, s.flows, t, x, y, smp)));
-    }
-    s.mie_prev_score[j] = nan_to_ninf(sp);
+    s.mie_prev_score[j] = mie_score(p, s, f, x, y, s.theta[j]);
     s.mie_smp[j] = smp;
-    s.mie_smp_score[j] = nan_to_ninf(ss);
+    s.mie_smp_score[j] = mie_score(p, s, f, x, y, smp);
 }
 
-__global__ void k_mie_sweep(DevParams p, DevState s)
+// own value of pixel j (before the sweep overwrites theta)
+__device__ __forceinline__ float own_value(const DevState& s, int j)
+{
+    return s.mie_smp_score[j] > s.mie_prev_score[j] ? s.mie_smp[j] : s.theta[j];
+}
+
+__global__ void k_mie_runs(DevParams p, DevState s)
 {
     __shared__ FramesD f;
     load_frames(p, s, f);
     const int dir = (*s.iter) & 3;
     const bool rows = (dir == 0 || dir == 2);
+    const int len = rows ? p.W : p.H;
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= p.N) return;
+    const int c = id / len, i = id % len;
+    int x, y;
+    chain_xy(p, dir, c, i, x, y);
+    const int j = y * p.W + x;
+    const float v = own_value(s, j);
+    int e = i + 1;
+    int steps = 0;
+    while (e < len && steps < kRunCap) {
+        int xe, ye;
+        chain_xy(p, dir, c, e, xe, ye);
+        if (!survives(s, ye * p.W + xe, mie_score(p, s, f, xe, ye, v))) break;
+        ++e;
+        ++steps;
+    }
+    s.mie_next[j] = (steps == kRunCap && e < len) ? -e : e;
+}
+
+constexpr int kResolveThreads = 128;
+constexpr int kMaxChain = kMaxImageSide;
+
+__global__ void __launch_bounds__(kResolveThreads) k_mie_resolve(DevParams p, DevState s)
+{
+    __shared__ FramesD f;
+    __shared__ short origin[kMaxChain];
+    load_frames(p, s, f);
+    const int dir = (*s.iter) & 3;
+    const bool rows = (dir == 0 || dir == 2);
     const int n_chains = rows ? p.H : p.W;
     const int len = rows ? p.W : p.H;
-    const int lane = threadIdx.x & 31;
-    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int c = blockIdx.x;
     if (c >= n_chains) return;
-    const int t = lane + 1;
-    float nbr = 0.f;
-    for (int i = 0; i < len; ++i) {
-        int x, y;
-        switch (dir) {
-            case 0: x = i; y = c; break;
-            case 1: x = c; y = i; break;
-            case 2: x = p.W - 1 - i; y = c; break;
-            default: x = c; y = p.H - 1 - i; break;
-        }
-        const int j = y * p.W + x;
-        float best = s.theta[j];
-        float best_s = s.mie_prev_score[j];
-        unsigned char label = 0;
-        if (i > 0) {
-            float e = 0.f;
-            if (lane < p.T) {
-                const float q = s.qs[(size_t)(t - 1) * p.N + j];
-                e = __fmul_rn(q, depth_ell(p, f, s.flows, t, x, y, nbr));
+    if (threadIdx.x == 0) {
+        int r = 0;
+        while (r < len) {
+            int x, y;
+            chain_xy(p, dir, c, r, x, y);
+            const int jr = y * p.W + x;
+            int e = s.mie_next[jr];
+            if (e < 0) {                       // speculation capped: continue on the fly
+                e = -e;
+                const float v = own_value(s, jr);
+                while (e < len) {
+                    int xe, ye;
+                    chain_xy(p, dir, c, e, xe, ye);
+                    if (!survives(s, ye * p.W + xe, mie_score(p, s, f, xe, ye, v))) break;
+                    ++e;
+                }
             }
-            float tot = 0.f;
-            for (int tt = 0; tt < p.T; ++tt) tot = __fadd_rn(tot, __shfl_sync(0xffffffffu, e, tt));
-            tot = nan_to_ninf(tot);
-            if (tot > best_s) { best = nbr; best_s = tot; label = 1; }
+            for (int q = r; q < e; ++q) origin[q] = (short)r;
+            r = e;
         }
-        const float ss = s.mie_smp_score[j];
-        if (ss > best_s) { best = s.mie_smp[j]; best_s = ss; label = 2; }
-        if (lane == 0) {
-            s.theta[j] = best;
-            s.labels[j] = label;
-        }
-        nbr = best;
+    }
+    __syncthreads();
+    // new depths and labels; read every own value before any theta is written
+    float vals[kMaxChain / kResolveThreads];
+    unsigned char labs[kMaxChain / kResolveThreads];
+    int n = 0;
+    for (int q = threadIdx.x; q < len; q += kResolveThreads, ++n) {
+        int x, y;
+        chain_xy(p, dir, c, origin[q], x, y);
+        const int jo = y * p.W + x;
+        vals[n] = own_value(s, jo);
+        labs[n] = (origin[q] != q) ? 1 : (s.mie_smp_score[jo] > s.mie_prev_score[jo] ? 2 : 0);
+    }
+    __syncthreads();
+    n = 0;
+    for (int q = threadIdx.x; q < len; q += kResolveThreads, ++n) {
+        int x, y;
+        chain_xy(p, dir, c, q, x, y);
+        const int j = y * p.W + x;
+        s.theta[j] = vals[n];
+        s.labels[j] = labs[n];
     }
 }
 
@@ -344,9 +419,8 @@ void launch_mie(const DevParams& p, const DevState& s, cudaStream_t st)
 {
     const int nb = (p.N + kPixThreads - 1) / kPixThreads;
     k_mie_prepare<<<nb, kPixThreads, 0, st>>>(p, s);
-    const int chains = p.H > p.W ? p.H : p.W;
-    const int warps_per_block = 4;
-    k_mie_sweep<<<(chains + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(p, s);
+    k_mie_runs<<<nb, kPixThreads, 0, st>>>(p, s);
+    k_mie_resolve<<<p.H > p.W ? p.H : p.W, kResolveThreads, 0, st>>>(p, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -83,6 +83,49 @@ __device__ __forceinline__ float pair_term(const HypF& h, const float4 a, const 
     return den > 0.f ? v : 0.69314718055994531f;
 }
 
+// Bulk-copy staging of pixel-record tiles: one thread issues
+// cp.async.bulk (global -> shared) completing on an mbarrier per ring slot;
+// every thread waits on the slot's phase with a bounded try_wait.
+constexpr int kTilePix = 256;                       // records per tile (12 KB)
+constexpr int kStages = 2;
+constexpr long long kWaitLimit = 1ll << 26;        // bounded spin on an mbarrier phase
+
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
+{
+    for (long long i = 0; i < kWaitLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
 __global__ void __launch_bounds__(kScoreThreads, 2) k_score(DevParams p, DevState s, int log_idx)
 {
     const int n_hyp = *s.n_hyp;
@@ -96,6 +139,28 @@ __global__ void __launch_bounds__(kScoreThreads, 2) k_score(DevParams p, DevStat
     const int chunk = blockIdx.y, n_chunks = gridDim.y;
     const long long lo = (long long)n_pix * chunk / n_chunks;
     const long long hi = (long long)n_pix * (chunk + 1) / n_chunks;
+    const int n_tiles = (int)((hi - lo + kTilePix - 1) / kTilePix);
+
+    __shared__ __align__(128) float4 tile[kStages][kTilePix * 3];
+    __shared__ __align__(8) uint64_t full[kStages];
+    __shared__ int timed_out;
+    const float4* gpix = reinterpret_cast<const float4*>(s.pix);
+    auto issue = [&](int it) {
+        const long long j0 = lo + (long long)it * kTilePix;
+        const int cnt = (int)min((long long)kTilePix, hi - j0);
+        const uint32_t bytes = (uint32_t)cnt * (uint32_t)sizeof(PixRec);
+        uint64_t* bar = &full[it % kStages];
+        mbar_expect_tx(bar, bytes);
+        bulk_g2s(&tile[it % kStages][0], gpix + 3 * j0, bytes, bar);
+    };
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kStages; ++i) mbar_init(&full[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        timed_out = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int i = 0; i < kStages && i < n_tiles; ++i) issue(i);
 
     HypF hy[kScoreHypsPerThread];
 #pragma unroll
@@ -105,24 +170,44 @@ __global__ void __launch_bounds__(kScoreThreads, 2) k_score(DevParams p, DevStat
         hy[i] = HypF{f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7], f[8], f[9], f[10], f[11]};
     }
     double acc[kScoreHypsPerThread];
-    float facc[kScoreHypsPerThread];
 #pragma unroll
-    for (int i = 0; i < kScoreHypsPerThread; ++i) { acc[i] = 0.0; facc[i] = 0.f; }
-
+    for (int i = 0; i < kScoreHypsPerThread; ++i) acc[i] = 0.0;
     const float xs_min = p.xs_min, xs_max = p.xs_max;
-    const float4* __restrict__ pix = reinterpret_cast<const float4*>(s.pix);
-    long long j = lo;
-    while (j < hi) {
-        const long long jend = min(hi, j + 32);
-        for (; j < jend; ++j) {
-            const float4 a = __ldg(pix + 3 * j);
-            const float4 b = __ldg(pix + 3 * j + 1);
-            const float wq = __ldg(reinterpret_cast<const float*>(pix + 3 * j + 2));
+
+    int it = 0;
+    for (; it < n_tiles; ++it) {
+        const int slot = it % kStages;
+        if (!mbar_wait_bounded(&full[slot], (uint32_t)((it / kStages) & 1))) atomicExch(&timed_out, 1);
+        __syncthreads();
+        if (timed_out) break;
+        const int cnt = (int)min((long long)kTilePix, hi - (lo + (long long)it * kTilePix));
+        const float4* t4 = &tile[slot][0];
+        float facc[kScoreHypsPerThread];
+#pragma unroll
+        for (int i = 0; i < kScoreHypsPerThread; ++i) facc[i] = 0.f;
+        for (int q = 0; q < cnt; ++q) {
+            const float4 a = t4[3 * q];
+            const float4 b = t4[3 * q + 1];
+            const float wq = reinterpret_cast<const float*>(t4 + 3 * q + 2)[0];
 #pragma unroll
             for (int i = 0; i < kScoreHypsPerThread; ++i) facc[i] = fmaf(wq, pair_term(hy[i], a, b, xs_min, xs_max), facc[i]);
         }
 #pragma unroll
-        for (int i = 0; i < kScoreHypsPerThread; ++i) { acc[i] += (double)facc[i]; facc[i] = 0.f; }
+        for (int i = 0; i < kScoreHypsPerThread; ++i) acc[i] += (double)facc[i];
+        __syncthreads();                       // every thread is done with this slot
+        if (threadIdx.x == 0 && it + kStages < n_tiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(it + kStages);
+        }
+    }
+    if (timed_out) {
+        // drain the copies this block issued (bounded) before leaving
+        if (threadIdx.x == 0) {
+            for (int j = it; j < n_tiles && j < it + kStages; ++j)
+                mbar_wait_bounded(&full[j % kStages], (uint32_t)((j / kStages) & 1));
+            atomicOr(s.status + 3, 1 << 16);
+        }
+        return;
     }
     const int S = p.S;
 #pragma unroll

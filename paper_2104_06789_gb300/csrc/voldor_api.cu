@@ -92,6 +92,7 @@ DevParams make_dev_params(const voldor_ctx& c)
     d.inv_depth_min = (float)p.inv_depth_min; d.inv_depth_max = (float)p.inv_depth_max;
     d.gamma = (float)p.gamma;
     d.fxd = c.K.fx; d.fyd = c.K.fy; d.cxd = c.K.cx; d.cyd = c.K.cy;
+    d.inv_fxd = 1.0 / c.K.fx; d.inv_fyd = 1.0 / c.K.fy; d.fy_over_fx_d = c.K.fy / c.K.fx;
     d.sigma_t = p.sigma_t; d.sigma_r = p.sigma_r; d.ms_tol = p.ms_tol;
     d.seed = p.seed; d.window_id = p.window_id;
     return d;
@@ -139,6 +140,7 @@ size_t layout(voldor_ctx& c, char* base)
     s.mie_prev_score = (float*)take(N * 4);
     s.mie_smp = (float*)take(N * 4);
     s.mie_smp_score = (float*)take(N * 4);
+    s.mie_next = (int*)take(N * 4);
     s.labels = (unsigned char*)take(N);
     s.fb_fwd = (float*)take(T * N * 8);
     s.score_log = (long long*)take((size_t)kScoreLogMax * 2 * 8);
@@ -291,6 +293,7 @@ voldor_status voldor_init_window(voldor_ctx** out, int width, int height, int T,
     if (!out) return VOLDOR_ERR_INVALID_ARG;
     *out = nullptr;
     if (!K || !flows || width < 2 || height < 2 || T < 1 || T > kMaxT) return VOLDOR_ERR_INVALID_ARG;
+    if (width > kMaxImageSide || height > kMaxImageSide) return VOLDOR_ERR_INVALID_ARG;
     if ((long long)width * height > 0x7fffffffLL) return VOLDOR_ERR_INVALID_ARG;
     if (!finite_pos(K->fx) || !finite_pos(K->fy) || !std::isfinite(K->cx) || !std::isfinite(K->cy))
         return VOLDOR_ERR_INVALID_ARG;

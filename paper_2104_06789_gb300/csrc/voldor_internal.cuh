@@ -21,6 +21,7 @@ constexpr int kMeanshiftCtas = 8;      // thread-block cluster of the meanshift
 constexpr int kMeanshiftThreads = 1024;
 constexpr int kPixThreads = 256;
 constexpr int kScoreLogMax = 1024;
+constexpr int kMaxImageSide = 4096;   // longest chain the depth sweep resolves in shared memory
 
 // Everything a kernel needs to know about the window, by value.
 struct DevParams {
@@ -34,6 +35,7 @@ struct DevParams {
     float inv_depth_min, inv_depth_max;
     float gamma;
     double fxd, fyd, cxd, cyd;
+    double inv_fxd, inv_fyd, fy_over_fx_d;
     double sigma_t, sigma_r, ms_tol;
     uint64_t seed, window_id;
 };
@@ -79,6 +81,7 @@ struct DevState {
     float* mie_prev_score;    // [N]
     float* mie_smp;           // [N]
     float* mie_smp_score;     // [N]
+    int* mie_next;            // [N] end of each pixel's speculative run (chain position), negative if capped
     unsigned char* labels;    // [N]
     float* fb_fwd;            // [T][H][W] forward messages
     long long* score_log;     // [kScoreLogMax][2] (n_hyp, n_pix) of timed scoring launches
@@ -158,11 +161,24 @@ struct GeomD {
     double fu, fv;        // observed flow X_t(pi_{t-1})
 };
 
+// 1/d in FP64 from the SFU reciprocal and two Newton steps (full double
+// precision for normal d; falls back to division outside [1e-30, 1e30]).
+__device__ __forceinline__ double rcp64(double d)
+{
+    const double ad = fabs(d);
+    if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
+    double r = (double)__frcp_rn((float)d);
+    double e = fma(-d, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-d, r, 1.0);
+    return fma(r, e, r);
+}
+
 __device__ __forceinline__ bool geom_prev(const DevParams& p, const double* C, const void* flows, int t, int x, int y,
                                           float depth, GeomD& g)
 {
     const double th = (double)depth;
-    const double dx = ((double)x - p.cxd) / p.fxd, dy = ((double)y - p.cyd) / p.fyd;
+    const double dx = ((double)x - p.cxd) * p.inv_fxd, dy = ((double)y - p.cyd) * p.inv_fyd;
     if (t == 1) {
         g.Px = th * dx; g.Py = th * dy; g.Pz = th;
         g.u = (double)x; g.v = (double)y;
@@ -173,7 +189,7 @@ __device__ __forceinline__ bool geom_prev(const DevParams& p, const double* C, c
         g.Py = C[4] * X + C[5] * Y + C[6] * Z + C[7];
         g.Pz = C[8] * X + C[9] * Y + C[10] * Z + C[11];
         if (!(g.Pz > 0.0)) return false;
-        const double iz = 1.0 / g.Pz;
+        const double iz = rcp64(g.Pz);
         g.u = p.fxd * g.Px * iz + p.cxd;
         g.v = p.fyd * g.Py * iz + p.cyd;
     }
@@ -220,11 +236,11 @@ __device__ __forceinline__ float ell_frame(const DevParams& p, const double* Tt,
     const double Qy = Tt[4] * g.Px + Tt[5] * g.Py + Tt[6] * g.Pz + Tt[7];
     const double Qz = Tt[8] * g.Px + Tt[9] * g.Py + Tt[10] * g.Pz + Tt[11];
     if (!(Qz > 0.0)) return -0.69314718055994531f;
-    const double iq = 1.0 / Qz;
+    const double iq = rcp64(Qz);
     const double ru = (p.fxd * Qx * iq + p.cxd - g.u) - g.fu;
     const double rv = (p.fyd * Qy * iq + p.cyd - g.v) - g.fv;
     const float x = (float)fmin(fmax(ru * ru + rv * rv, (double)p.x_min), (double)p.x_max);
-    const float n = (float)sqrt(g.fu * g.fu + g.fv * g.fv);
+    const float n = sqrtf((float)(g.fu * g.fu + g.fv * g.fv));
     const FiskConst fc = fisk_const(p, n);
     const float s = fc.beta * (log2f(x) - fc.log2_alpha);
     const float e = exp2f(fabsf(s));

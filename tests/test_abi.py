@@ -46,7 +46,7 @@ def test_invalid_arguments_are_rejected_on_the_host(vd):
     p = vd.default_params()
     fp = ctypes.c_void_p(flows.ctypes.data)
     assert L.voldor_init_window(None, 8, 8, 2, ctypes.byref(K), ctypes.byref(p), fp, 0, 0, None) == vd.ERR_INVALID_ARG
-    for (w, hgt, T) in [(1, 8, 2), (8, 1, 2), (8, 8, 0), (8, 8, 17)]:
+    for (w, hgt, T) in [(1, 8, 2), (8, 1, 2), (8, 8, 0), (8, 8, 17), (4097, 8, 2), (8, 4097, 2)]:
         assert L.voldor_init_window(ctypes.byref(h), w, hgt, T, ctypes.byref(K), ctypes.byref(p), fp, 0, 0,
                                     None) == vd.ERR_INVALID_ARG
         assert not h.value
