@@ -21,6 +21,15 @@ __global__ void k_frame_setup(DevParams p, DevState s)
     for (int t = 1; t <= p.T; ++t) {
         for (int q = 0; q < 12; ++q) s.cum[12 * (t - 1) + q] = C[q];
         const double* A = s.poses + 12 * (t - 1);
+        float* f = s.frames32 + 24 * (t - 1);     // E_c = R_c - I, t_c, E_t = R_t - I, t_t
+        for (int r = 0; r < 3; ++r) {
+            for (int c = 0; c < 3; ++c) {
+                f[r * 3 + c] = (float)(C[r * 4 + c] - (r == c ? 1.0 : 0.0));
+                f[12 + r * 3 + c] = (float)(A[r * 4 + c] - (r == c ? 1.0 : 0.0));
+            }
+            f[9 + r] = (float)C[r * 4 + 3];
+            f[21 + r] = (float)A[r * 4 + 3];
+        }
         double O[12];
         for (int r = 0; r < 3; ++r) {
             for (int c = 0; c < 3; ++c)
@@ -182,6 +191,81 @@ __device__ __forceinline__ float depth_ell(const DevParams& p, const FramesD& f,
     return ell_frame(p, f.Tt[t - 1], g);
 }
 
+// ell_t(j) at depth d in FP32 for the MIE candidate scores, written without
+// cancellation: with d = K^-1 [x y 1], the point in camera t-1 is
+// theta (d + a), a = E_c d + t_c / theta, so pi_{t-1} = (x, y) + delta with
+// delta = f (a_xy - d_xy a_z) / (1 + a_z) (a small quantity); the sample
+// position is split into an integer pixel and a fraction; the rigid flow is
+// xi = f (b_xy - pb_xy b_z) / (1 + b_z) with b = E_t pb + t_t / P_z. Every
+// MIE candidate is scored by this one function, so equal depths score
+// bit-identically.
+struct FramesF {
+    float v[kMaxT][24];
+};
+
+__device__ __forceinline__ void load_frames32(const DevParams& p, const DevState& s, FramesF& f)
+{
+    for (int i = threadIdx.x; i < p.T * 24; i += blockDim.x) f.v[i / 24][i % 24] = s.frames32[i];
+    __syncthreads();
+}
+
+__device__ __forceinline__ float depth_ell_fast(const DevParams& p, const float* fr, const void* flows, int t, int x,
+                                                int y, float depth)
+{
+    const float ln_half = -0.69314718055994531f;
+    if (!(depth > 0.f)) return ln_half;
+    const float dx = ((float)x - p.cx) * p.inv_fx, dy = ((float)y - p.cy) * p.inv_fy;
+    const float w0 = 1.f / depth;
+    float pbx = dx, pby = dy, w = w0;
+    int x0 = x, y0 = y;
+    float fxr = 0.f, fyr = 0.f;
+    if (t > 1) {
+        const float* E = fr;
+        const float ax = fmaf(E[0], dx, fmaf(E[1], dy, fmaf(fr[9], w0, E[2])));
+        const float ay = fmaf(E[3], dx, fmaf(E[4], dy, fmaf(fr[10], w0, E[5])));
+        const float az = fmaf(E[6], dx, fmaf(E[7], dy, fmaf(fr[11], w0, E[8])));
+        const float den = 1.f + az;
+        if (!(den > 0.f)) return ln_half;
+        const float rd = 1.f / den;
+        const float mx = fmaf(-dx, az, ax) * rd, my = fmaf(-dy, az, ay) * rd;    // pb - d
+        pbx = dx + mx;
+        pby = dy + my;
+        w = w0 * rd;
+        const float du = p.fx * mx, dv = p.fy * my;     // pi_{t-1} - (x, y)
+        if (!(fabsf(du) < 1e7f && fabsf(dv) < 1e7f)) return ln_half;
+        const float iu = floorf(du), iv = floorf(dv);
+        x0 = x + (int)iu;
+        y0 = y + (int)iv;
+        fxr = du - iu;
+        fyr = dv - iv;
+    }
+    // valid iff 0 <= u <= W-1 and 0 <= v <= H-1
+    if (x0 < 0 || y0 < 0 || x0 > p.W - 1 || y0 > p.H - 1) return ln_half;
+    if ((x0 == p.W - 1 && fxr > 0.f) || (y0 == p.H - 1 && fyr > 0.f)) return ln_half;
+    if (x0 == p.W - 1) { x0 = p.W - 2; fxr = 1.f; }
+    if (y0 == p.H - 1) { y0 = p.H - 2; fyr = 1.f; }
+    const size_t base = (size_t)(t - 1) * p.N + (size_t)y0 * p.W + x0;
+    const float2 f00 = load_flow(flows, p.flow_f16, base), f10 = load_flow(flows, p.flow_f16, base + 1);
+    const float2 f01 = load_flow(flows, p.flow_f16, base + p.W), f11 = load_flow(flows, p.flow_f16, base + p.W + 1);
+    const float w00 = (1.f - fxr) * (1.f - fyr), w10 = fxr * (1.f - fyr), w01 = (1.f - fxr) * fyr, w11 = fxr * fyr;
+    const float fu = fmaf(w00, f00.x, fmaf(w10, f10.x, fmaf(w01, f01.x, w11 * f11.x)));
+    const float fv = fmaf(w00, f00.y, fmaf(w10, f10.y, fmaf(w01, f01.y, w11 * f11.y)));
+    const float* Et = fr + 12;
+    const float bx = fmaf(Et[0], pbx, fmaf(Et[1], pby, fmaf(fr[21], w, Et[2])));
+    const float by = fmaf(Et[3], pbx, fmaf(Et[4], pby, fmaf(fr[22], w, Et[5])));
+    const float bz = fmaf(Et[6], pbx, fmaf(Et[7], pby, fmaf(fr[23], w, Et[8])));
+    const float den = 1.f + bz;
+    if (!(den > 0.f)) return ln_half;
+    const float rd = 1.f / den;
+    const float ru = fmaf(p.fx * fmaf(-pbx, bz, bx), rd, -fu);
+    const float rv = fmaf(p.fy * fmaf(-pby, bz, by), rd, -fv);
+    const float xsq = fminf(fmaxf(fmaf(ru, ru, rv * rv), p.x_min), p.x_max);
+    const FiskConst fc = fisk_const(p, sqrtf(fmaf(fu, fu, fv * fv)));
+    const float s = fc.beta * (log2f(xsq) - fc.log2_alpha);
+    const float e = exp2f(fabsf(s));
+    return -log1pf(fc.mu_over_beta * xsq * (e + 2.f + 1.f / e));
+}
+
 // Emissions rho/(rho+mu) of every (t, j) at the current depth (E-step input)
 // or, written into W, the unsmoothed rigidness update.
 __global__ void k_emissions(DevParams p, DevState s, float* out)
@@ -278,17 +362,17 @@ void launch_forward_backward(const DevParams& p, const DevState& s, cudaStream_t
 //   resolve  per chain: follow r -> end of run from the chain start; a run
 //            that reached the cap is continued on the fly.
 // ---------------------------------------------------------------------------
-constexpr int kRunCap = 16;
+constexpr int kRunCap = 32;
 
 __device__ __forceinline__ float nan_to_ninf(float v) { return isnan(v) ? -INFINITY : v; }
 
-__device__ __forceinline__ float mie_score(const DevParams& p, const DevState& s, const FramesD& f, int x, int y, float d)
+__device__ __forceinline__ float mie_score(const DevParams& p, const DevState& s, const FramesF& f, int x, int y, float d)
 {
     const int j = y * p.W + x;
     float acc = 0.f;
     for (int t = 1; t <= p.T; ++t) {
         const float q = s.qs[(size_t)(t - 1) * p.N + j];
-        acc = __fadd_rn(acc, __fmul_rn(q, depth_ell(p, f, s.flows, t, x, y, d)));
+        acc = __fadd_rn(acc, __fmul_rn(q, depth_ell_fast(p, f.v[t - 1], s.flows, t, x, y, d)));
     }
     return nan_to_ninf(acc);
 }
@@ -311,8 +395,8 @@ __device__ __forceinline__ bool survives(const DevState& s, int j, float sv)
 
 __global__ void k_mie_prepare(DevParams p, DevState s)
 {
-    __shared__ FramesD f;
-    load_frames(p, s, f);
+    __shared__ FramesF f;
+    load_frames32(p, s, f);
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= p.N) return;
     const int k = *s.iter;
@@ -333,8 +417,8 @@ __device__ __forceinline__ float own_value(const DevState& s, int j)
 
 __global__ void k_mie_runs(DevParams p, DevState s)
 {
-    __shared__ FramesD f;
-    load_frames(p, s, f);
+    __shared__ FramesF f;
+    load_frames32(p, s, f);
     const int dir = (*s.iter) & 3;
     const bool rows = (dir == 0 || dir == 2);
     const int len = rows ? p.W : p.H;
@@ -362,22 +446,29 @@ constexpr int kMaxChain = kMaxImageSide;
 
 __global__ void __launch_bounds__(kResolveThreads) k_mie_resolve(DevParams p, DevState s)
 {
-    __shared__ FramesD f;
+    __shared__ FramesF f;
     __shared__ short origin[kMaxChain];
-    load_frames(p, s, f);
+    __shared__ int next_s[kMaxChain];
+    load_frames32(p, s, f);
     const int dir = (*s.iter) & 3;
     const bool rows = (dir == 0 || dir == 2);
     const int n_chains = rows ? p.H : p.W;
     const int len = rows ? p.W : p.H;
     const int c = blockIdx.x;
     if (c >= n_chains) return;
+    for (int q = threadIdx.x; q < len; q += kResolveThreads) {
+        int x, y;
+        chain_xy(p, dir, c, q, x, y);
+        next_s[q] = s.mie_next[y * p.W + x];
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         int r = 0;
         while (r < len) {
             int x, y;
             chain_xy(p, dir, c, r, x, y);
             const int jr = y * p.W + x;
-            int e = s.mie_next[jr];
+            int e = next_s[r];
             if (e < 0) {                       // speculation capped: continue on the fly
                 e = -e;
                 const float v = own_value(s, jr);

@@ -119,6 +119,7 @@ size_t layout(voldor_ctx& c, char* base)
     s.qs = (float*)take(T * N * 4);
     s.poses = (double*)take(T * 12 * 8);
     s.cum = (double*)take(T * 12 * 8);
+    s.frames32 = (float*)take(T * 24 * 4);
     s.iter = (int*)take(4);
     s.status = (int*)take(16);
     c.flag_dev = (int*)take(4);

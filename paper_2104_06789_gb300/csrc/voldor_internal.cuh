@@ -58,6 +58,7 @@ struct DevState {
     float* qs;                // [T][H][W] smoothed q (also emission scratch)
     double* poses;            // [T][12] row-major [R | t]
     double* cum;              // [T][12] C_{t-1} = T_{t-1} ... T_1 (FP64)
+    float* frames32;          // [T][24] FP32 E_c = R_c - I, t_c, E_t = R_t - I, t_t
     int* iter;                // [1] iteration counter k
     int* status;              // [4] n_hyp, seed, meanshift steps, status bits
     // dense scoring scratch
