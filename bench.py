@@ -289,14 +289,20 @@ def run_ours(args):
 
     props = torch.cuda.get_device_properties(local_rank)
     sms = props.multi_processor_count
-    peak = sms * MUFU_PER_SM_PER_CLK * NOMINAL_MAX_MHZ * 1e6 / 1e12      # T MUFU-ops/s
+    # SFU results per SM clock, measured on this GPU (exp2, log2, reciprocal);
+    # the algorithmic mix per pair is 1 rcp + 2 lg2 + 1 ex2
+    rates = {name: voldor.probe_sfu_rate(op) for op, name in enumerate(("ex2", "lg2", "rcp"))}
+    per_clk = ALGO_MUFU_PER_PAIR / (1.0 / rates["rcp"] + 2.0 / rates["lg2"] + 1.0 / rates["ex2"])
+    peak = sms * per_clk * NOMINAL_MAX_MHZ * 1e6 / 1e12                # T SFU-ops/s
     score_ms = np.array(score_ms)
     score_pairs = np.array(score_pairs, dtype=np.float64)
     achieved = float(np.mean(ALGO_MUFU_PER_PAIR * score_pairs / (score_ms * 1e-3)) / 1e12) if len(score_ms) else None
     roofline = {"kernel": "k_score (dense hypothesis scoring)", "bound": "alu", "achieved": achieved,
-                "peak": peak, "unit": "T MUFU-op/s (4 algorithmic SFU ops per hypothesis-pixel pair)",
+                "peak": peak, "unit": "T SFU-op/s (4 algorithmic SFU ops per hypothesis-pixel pair)",
                 "frac": achieved / peak if achieved else None, "traffic": None,
-                "peak_source": f"{sms} SMs x {MUFU_PER_SM_PER_CLK} SFU ops/clk x {NOMINAL_MAX_MHZ:.0f} MHz",
+                "peak_source": (f"{sms} SMs x {per_clk:.2f} SFU results/clk/SM (measured: ex2 {rates['ex2']:.2f}, "
+                                f"lg2 {rates['lg2']:.2f}, rcp {rates['rcp']:.2f}; mix 1 rcp + 2 lg2 + 1 ex2) x "
+                                f"{NOMINAL_MAX_MHZ:.0f} MHz; nominal table value 16/clk/SM"),
                 "launches_timed": int(len(score_ms)), "mean_launch_ms": float(score_ms.mean()) if len(score_ms) else None,
                 "share_of_step": float(score_ms.sum() / total_ms) if len(score_ms) else None}
 

@@ -230,6 +230,13 @@ const char* voldor_last_error_string(const voldor_ctx* ctx);
 voldor_status voldor_score_records_noalloc(const float* records, int n_pix, const float* hyps, int n_hyps,
                                            double xs_min, double xs_max, double* L, void* cuda_stream);
 
+/* Diagnostic for rooflines (no counterpart in the paper): measures the SFU
+ * (special-function unit) throughput of the current GPU in results per SM
+ * clock for op 0 = exp2, 1 = log2, 2 = reciprocal (approximate forms), by
+ * timing independent chains with the SM cycle counter. Allocates and frees a
+ * few KB; synchronises the device. Errors: INVALID_ARG, OOM, CUDA. */
+voldor_status voldor_probe_sfu_rate(int op, double* results_per_sm_clock);
+
 /* Device memory held by the context, bytes. */
 size_t voldor_device_bytes(const voldor_ctx* ctx);
 

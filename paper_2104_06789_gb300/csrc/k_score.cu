@@ -13,11 +13,13 @@
 //   s    = beta log2(xs) + beta_k               (log2 of (x/alpha)^beta)
 //   r    = Cp xs (2^s + 2 + 2^-s)               (= mu / rho, Eqs. 3-4, 7)
 //   ell  = -log1p(r)
-// MUFU work: rcp, lg2, ex2, ex2, lg2 (for r >= 1/8); log1p(r) for r < 1/8 is
-// a Taylor polynomial on the FMA pipe, because lg2 near 1 has only absolute
-// accuracy. Sums: FP32 over 32 pixels, then FP64.
+// MUFU work: rcp, lg2, ex2, ex2, lg2 (for r >= 1/4); log1p(r) for r < 1/4 is
+// a polynomial on the FMA pipe, because lg2 near 1 has only absolute
+// accuracy. Each thread carries 8 hypotheses (instruction-level parallelism
+// over occupancy); sums are FP32 per 256-pixel tile, then FP64.
 #include <cmath>
 #include <mutex>
+#include <vector>
 
 #include "voldor_internal.cuh"
 
@@ -48,20 +50,19 @@ struct HypF {
     float e0, e1, e2, e3, e4, e5, e6, e7, e8, t0, t1, t2;
 };
 
-// log1p(r) for r >= 0: Taylor series to r^9 below 1/8, ln2 * lg2(1 + r) above.
+// log1p(r) for r >= 0: below 1/4 r * P(r) with P the degree-5 Chebyshev
+// interpolant of log1p(r)/r on [0, 1/4] (relative error 6e-8 in FP32
+// Horner form); above, ln2 * lg2(1 + r).
 __device__ __forceinline__ float log1p_pos(float r)
 {
-    float s = fmaf(r, -1.f / 9.f, 1.f / 8.f);
-    s = fmaf(r, s, -1.f / 7.f);
-    s = fmaf(r, s, 1.f / 6.f);
-    s = fmaf(r, s, -1.f / 5.f);
-    s = fmaf(r, s, 1.f / 4.f);
-    s = fmaf(r, s, -1.f / 3.f);
-    s = fmaf(r, s, 1.f / 2.f);
-    s = fmaf(r, -s, 1.f);
+    float s = fmaf(r, -9.216756374e-02f, 1.815955490e-01f);
+    s = fmaf(r, s, -2.477561533e-01f);
+    s = fmaf(r, s, 3.332059979e-01f);
+    s = fmaf(r, s, -4.999973178e-01f);
+    s = fmaf(r, s, 1.0f);
     const float small = r * s;
     const float big = 0.69314718055994531f * mufu_lg2(1.f + r);
-    return r < 0.125f ? small : big;
+    return r < 0.25f ? small : big;
 }
 
 // -ell = log1p(mu/rho) of one (hypothesis, pixel) pair; ln 2 behind camera t.
@@ -126,7 +127,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return false;
 }
 
-__global__ void __launch_bounds__(kScoreThreads, 2) k_score(DevParams p, DevState s, int log_idx)
+__global__ void __launch_bounds__(kScoreThreads, kScoreBlocksPerSM) k_score(DevParams p, DevState s, int log_idx)
 {
     const int n_hyp = *s.n_hyp;
     const int n_pix = *s.pix_count;
@@ -238,8 +239,8 @@ int score_chunks(int S, int N)
             g_num_sms = 152;
     }
     const int tiles = (S + kScoreHypsPerBlock - 1) / kScoreHypsPerBlock;
-    // two resident blocks per SM, two waves
-    int chunks = (g_num_sms * 2 * 2 + tiles - 1) / tiles;
+    // four waves of the resident blocks, for load balance
+    int chunks = (g_num_sms * kScoreBlocksPerSM * 4 + tiles - 1) / tiles;
     if (chunks > N) chunks = N;
     return chunks < 1 ? 1 : chunks;
 }
@@ -274,7 +275,7 @@ constexpr int kStaticMaxHyps = 8192;
 constexpr int kStaticChunks = 64;
 static __device__ __align__(256) double g_static_partials[kStaticChunks * kStaticMaxHyps];   // 4 MiB
 
-__global__ void __launch_bounds__(kScoreThreads, 2)
+__global__ void __launch_bounds__(kScoreThreads, kScoreBlocksPerSM)
 k_score_records(const float4* __restrict__ pix, int n_pix, const float* __restrict__ hyps, int n_hyp, float xs_min,
                 float xs_max, double* __restrict__ partial)
 {
@@ -365,5 +366,65 @@ extern "C" voldor_status voldor_score_records_noalloc(const float* records, int 
         reinterpret_cast<const float4*>(records), n_pix, hyps, n_hyps, (float)xs_min, (float)xs_max, partial);
     k_reduce_records<<<(n_hyps + 255) / 256, 256, 0, st>>>(partial, n_hyps, kStaticChunks, L);
     if (cudaGetLastError() != cudaSuccess) return VOLDOR_ERR_CUDA;
+    return VOLDOR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostic: SFU (MUFU) throughput of this GPU in results per SM clock, for
+// the roofline of the dense scoring. Every thread runs 8 independent chains of
+// one SFU op; each block times itself with clock64, so the figure does not
+// depend on the clock frequency.
+// ---------------------------------------------------------------------------
+namespace vd {
+__global__ void __launch_bounds__(256) k_sfu_probe(int op, int iters, float seed, float* sink, long long* cycles)
+{
+    float v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = seed + 0.001f * (threadIdx.x + i);
+    __syncthreads();
+    const long long t0 = clock64();
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (op == 0) v[i] = mufu_ex2(v[i]);
+            else if (op == 1) v[i] = mufu_lg2(v[i]);
+            else v[i] = mufu_rcp(v[i]);
+        }
+    }
+    __syncthreads();
+    const long long t1 = clock64();
+    float acc = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc += v[i];
+    if (acc == 1234.5f) sink[threadIdx.x] = acc;     // keeps the chains alive
+    if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+}  // namespace vd
+
+extern "C" voldor_status voldor_probe_sfu_rate(int op, double* results_per_sm_clock)
+{
+    using namespace vd;
+    if (!results_per_sm_clock || op < 0 || op > 2) return VOLDOR_ERR_INVALID_ARG;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return VOLDOR_ERR_CUDA;
+    const int blocks = sms * 4, threads = 256, iters = 4096;
+    float* sink = nullptr;
+    long long* cyc = nullptr;
+    if (cudaMalloc(&sink, threads * sizeof(float)) != cudaSuccess) return VOLDOR_ERR_OOM;
+    if (cudaMalloc(&cyc, blocks * sizeof(long long)) != cudaSuccess) { cudaFree(sink); return VOLDOR_ERR_OOM; }
+    // ex2 and rcp chains stay bounded from these seeds; lg2 of values in (0, 1)
+    const float seed = op == 1 ? 0.5f : 0.75f;
+    k_sfu_probe<<<blocks, threads>>>(op, 64, seed, sink, cyc);          // warm-up
+    k_sfu_probe<<<blocks, threads>>>(op, iters, seed, sink, cyc);
+    std::vector<long long> h(blocks);
+    cudaError_t e = cudaMemcpy(h.data(), cyc, blocks * sizeof(long long), cudaMemcpyDeviceToHost);
+    cudaFree(sink);
+    cudaFree(cyc);
+    if (e != cudaSuccess) return VOLDOR_ERR_CUDA;
+    // 4 resident blocks per SM share it: results per SM clock = 4 * per-block ops / cycles
+    double sum = 0.0;
+    for (int b = 0; b < blocks; ++b) sum += 4.0 * (double)threads * 8.0 * iters / (double)h[b];
+    *results_per_sm_clock = sum / blocks;
     return VOLDOR_OK;
 }

@@ -15,7 +15,8 @@ namespace vd {
 constexpr int kMaxT = 16;
 constexpr int kMaxSols = 4;            // P3P has at most four solutions
 constexpr int kScoreThreads = 256;     // dense scoring block
-constexpr int kScoreHypsPerThread = 4;
+constexpr int kScoreHypsPerThread = 8;   // independent hypotheses per thread (ILP)
+constexpr int kScoreBlocksPerSM = 1;
 constexpr int kScoreHypsPerBlock = kScoreThreads * kScoreHypsPerThread;
 constexpr int kMeanshiftCtas = 8;      // thread-block cluster of the meanshift
 constexpr int kMeanshiftThreads = 1024;

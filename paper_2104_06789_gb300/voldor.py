@@ -81,6 +81,7 @@ def lib():
             "voldor_last_error_string": (C.c_char_p, [vp]),
             "voldor_device_bytes": (sz, [vp]),
             "voldor_score_records_noalloc": (i, [vp, i, vp, i, d, d, vp, vp]),
+            "voldor_probe_sfu_rate": (i, [i, P(d)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -280,6 +281,13 @@ def score_records_noalloc(records, hyps, L, xs_min, xs_max, stream=None):
                                               C.c_void_p(hyps.data_ptr()), int(hyps.shape[0]), float(xs_min),
                                               float(xs_max), C.c_void_p(L.data_ptr()), C.c_void_p(st)),
            "voldor_score_records_noalloc")
+
+
+def probe_sfu_rate(op):
+    """SFU results per SM clock of the current GPU: op 0 exp2, 1 log2, 2 rcp."""
+    v = C.c_double(0.0)
+    _check(lib().voldor_probe_sfu_rate(int(op), C.byref(v)), "voldor_probe_sfu_rate")
+    return v.value
 
 
 def init_window(flows, K, params=None, stream=None) -> Window:
