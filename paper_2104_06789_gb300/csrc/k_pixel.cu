@@ -125,6 +125,7 @@ __global__ void k_prep_count(DevParams p, DevState s, int t)
     }
     const int cnt = __syncthreads_count(valid);
     if (threadIdx.x == 0) s.pix_block_count[blockIdx.x] = cnt;
+    if (blockIdx.x == 0 && threadIdx.x < 8) s.pix_bounds[threadIdx.x] = 0.f;
 }
 
 __global__ void k_prep_write(DevParams p, DevState s, int t)
@@ -166,6 +167,14 @@ __global__ void k_prep_write(DevParams p, DevState s, int t)
                           (float)(p.fxd * p.fxd) * fc.mu_over_beta);
         r.c = make_float4(s.wmap[(size_t)(t - 1) * p.N + j], 0.f, 0.f, 0.f);
         s.pix[base + rank] = r;
+        // frame bounds for the dense scoring's fast path (non-negative floats
+        // order like their bit patterns)
+        int* b = reinterpret_cast<int*>(s.pix_bounds);
+        atomicMax(b + 0, __float_as_int(fabsf(r.a.x)));
+        atomicMax(b + 1, __float_as_int(fabsf(r.a.y)));
+        atomicMax(b + 2, __float_as_int(fabsf(r.a.z)));
+        atomicMax(b + 3, __float_as_int(fabsf(r.a.w)));
+        atomicMax(b + 4, __float_as_int(fabsf(r.b.x)));
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
         int tot = base;
@@ -444,11 +453,17 @@ __global__ void k_mie_runs(DevParams p, DevState s)
 constexpr int kResolveThreads = 128;
 constexpr int kMaxChain = kMaxImageSide;
 
+// Resolution of one chain per block. All threads walk the run ends in
+// lockstep from the chain start (uniform control flow); a run whose
+// speculation reached the cap is continued kResolveThreads positions at a
+// time, each thread testing one position; the run's positions are filled in
+// parallel.
 __global__ void __launch_bounds__(kResolveThreads) k_mie_resolve(DevParams p, DevState s)
 {
     __shared__ FramesF f;
     __shared__ short origin[kMaxChain];
     __shared__ int next_s[kMaxChain];
+    __shared__ int first_fail;
     load_frames32(p, s, f);
     const int dir = (*s.iter) & 3;
     const bool rows = (dir == 0 || dir == 2);
@@ -462,26 +477,32 @@ __global__ void __launch_bounds__(kResolveThreads) k_mie_resolve(DevParams p, De
         next_s[q] = s.mie_next[y * p.W + x];
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int r = 0;
-        while (r < len) {
-            int x, y;
-            chain_xy(p, dir, c, r, x, y);
-            const int jr = y * p.W + x;
-            int e = next_s[r];
-            if (e < 0) {                       // speculation capped: continue on the fly
-                e = -e;
-                const float v = own_value(s, jr);
-                while (e < len) {
+    int r = 0;
+    while (r < len) {
+        int e = next_s[r];
+        if (e < 0) {                           // speculation capped: continue block-parallel
+            int xr, yr;
+            chain_xy(p, dir, c, r, xr, yr);
+            const float v = own_value(s, yr * p.W + xr);
+            int pos = -e;
+            while (true) {
+                if (threadIdx.x == 0) first_fail = len;
+                __syncthreads();
+                const int q = pos + (int)threadIdx.x;
+                if (q < len) {
                     int xe, ye;
-                    chain_xy(p, dir, c, e, xe, ye);
-                    if (!survives(s, ye * p.W + xe, mie_score(p, s, f, xe, ye, v))) break;
-                    ++e;
+                    chain_xy(p, dir, c, q, xe, ye);
+                    if (!survives(s, ye * p.W + xe, mie_score(p, s, f, xe, ye, v))) atomicMin(&first_fail, q);
                 }
+                __syncthreads();
+                const int ff = first_fail;
+                __syncthreads();
+                if (ff < len || pos + kResolveThreads >= len) { e = ff < len ? ff : len; break; }
+                pos += kResolveThreads;
             }
-            for (int q = r; q < e; ++q) origin[q] = (short)r;
-            r = e;
         }
+        for (int q = r + (int)threadIdx.x; q < e; q += kResolveThreads) origin[q] = (short)r;
+        r = e;
     }
     __syncthreads();
     // new depths and labels; read every own value before any theta is written

@@ -284,10 +284,15 @@ __device__ bool group_point(const DevParams& p, const DevState& s, const double*
     return d3unit(bear);
 }
 
-__global__ void k_p3p_groups(DevParams p, DevState s, int t)
+__global__ void k_p3p_groups(DevParams p, DevState s, int t, int g_begin, int g_end, int skip_if_found)
 {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= p.G) return;
+    const int g = g_begin + blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= g_end) return;
+    if (skip_if_found && *s.grp_found >= p.S) {   // the first groups already give S hypotheses
+        s.grp_count[g] = 0;
+        s.grp_weight[g] = 0.0;
+        return;
+    }
     const int k = *s.iter;
     const U64x4 r = philox4x64_10((uint64_t)g, (uint64_t)t, (uint64_t)k, (uint64_t)kStreamPose, p.seed, p.window_id);
     long long j[3];
@@ -314,9 +319,33 @@ __global__ void k_p3p_groups(DevParams p, DevState s, int t)
         for (int q = 0; q < 12; ++q) o[i * 12 + q] = sols[i].Rt[q];
 }
 
+// Solutions found by groups [0, n): one block.
+__global__ void k_count_found(DevState s, int n)
+{
+    int acc = 0;
+    for (int g = threadIdx.x; g < n; g += blockDim.x) acc += s.grp_count[g];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ int ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += ws[w];
+        *s.grp_found = tot;
+    }
+}
+
+// Groups are solved in two halves: the second half only if the first gave
+// fewer than S solutions (the collection keeps the first S in group order,
+// so later groups cannot contribute otherwise).
 void launch_p3p_groups(const DevParams& p, const DevState& s, int t, cudaStream_t st)
 {
-    k_p3p_groups<<<(p.G + 127) / 128, 128, 0, st>>>(p, s, t);
+    const int g1 = p.G < p.S ? p.G : p.S;
+    k_p3p_groups<<<(g1 + 127) / 128, 128, 0, st>>>(p, s, t, 0, g1, 0);
+    if (g1 < p.G) {
+        k_count_found<<<1, 1024, 0, st>>>(s, g1);
+        k_p3p_groups<<<(p.G - g1 + 127) / 128, 128, 0, st>>>(p, s, t, g1, p.G, 1);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -489,10 +518,14 @@ void score_hyps_from_host(const DevParams& p, const DevState& s, int n, cudaStre
 // ---------------------------------------------------------------------------
 // Meanshift (Eqs. 18-19): x <- sum_h w_h K(x - p_h) p_h / sum_h w_h K(x - p_h),
 // K(d) = exp(-d^T Sigma^-1 d / 2), seeded at argmax_h L_h (lowest index on
-// ties), on a cluster of kMeanshiftCtas CTAs. Distances and sums in FP64; the
-// Gaussian itself in FP32. Every CTA reduces the cluster's partial sums in the
-// same order, so all take the same steps; partial buffers alternate by
-// iteration parity so one cluster barrier per step suffices.
+// ties), on a cluster of kMeanshiftCtas CTAs. The state x and all sums across
+// threads are FP64; each hypothesis is held as its FP32 offset from the seed,
+// so the Gaussian and the per-thread partial sums are FP32 on small numbers.
+// Every CTA reduces the cluster's partial sums in the same order, so all take
+// the same steps; partial buffers alternate by iteration parity so one
+// cluster barrier per step suffices. The iteration stops when the step is
+// below ms_tol, when a step below 1e-7 no longer contracts (the FP32 noise
+// floor of the kernel weights), or after ms_max_iter steps.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double warp_sum_d(double v)
 {
@@ -509,6 +542,7 @@ k_meanshift(DevParams p, DevState s, int t)
     __shared__ double wred[32][8];
     __shared__ double part[2][8];
     __shared__ double xs[8];
+    __shared__ double seedp[6];
     __shared__ double bval[32];
     __shared__ int bidx[32];
     __shared__ int flag;
@@ -539,34 +573,46 @@ k_meanshift(DevParams p, DevState s, int t)
         for (int w = 1; w < nwarp; ++w)
             if (bval[w] > v || (bval[w] == v && bidx[w] < i)) { v = bval[w]; i = bidx[w]; }
         if (i == 0x7fffffff) i = 0;
-        for (int c = 0; c < 6; ++c) xs[c] = s.hyp_p[(size_t)i * 6 + c];
+        for (int c = 0; c < 6; ++c) { seedp[c] = s.hyp_p[(size_t)i * 6 + c]; xs[c] = seedp[c]; }
         bidx[0] = i;
         flag = 0;
     }
     __syncthreads();
     const int seed = bidx[0];
-    const double ivt = 1.0 / p.sigma_t, ivr = 1.0 / p.sigma_r;
+    // FP32 offsets of this CTA's hypotheses from the seed
+    const int stride = kMeanshiftCtas * blockDim.x;
+    for (int h = rank * blockDim.x + tid; h < n; h += stride) {
+        float4* o = reinterpret_cast<float4*>(s.hyp_dp + (size_t)h * 8);
+        const double* ph = s.hyp_p + (size_t)h * 6;
+        o[0] = make_float4((float)(ph[0] - seedp[0]), (float)(ph[1] - seedp[1]), (float)(ph[2] - seedp[2]),
+                           (float)(ph[3] - seedp[3]));
+        o[1] = make_float4((float)(ph[4] - seedp[4]), (float)(ph[5] - seedp[5]), (float)s.hyp_w[h], 0.f);
+    }
+    const float ivt = (float)(1.0 / p.sigma_t), ivr = (float)(1.0 / p.sigma_r);
+    const float mlog2e = -0.5f * 1.4426950408889634f;
     int it = 0;
     bool degenerate = false;
+    double prev_step = INFINITY;
     for (; it < p.ms_max_iter; ++it) {
-        double x[6];
-        for (int c = 0; c < 6; ++c) x[c] = xs[c];
-        double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-        for (int h = rank * blockDim.x + tid; h < n; h += kMeanshiftCtas * blockDim.x) {
-            const double* ph = s.hyp_p + (size_t)h * 6;
-            double m = 0.0;
-            for (int c = 0; c < 6; ++c) {
-                const double d = x[c] - ph[c];
-                m += d * d * (c < 3 ? ivt : ivr);
-            }
-            const double kw = s.hyp_w[h] * (double)expf(-0.5f * (float)m);
-            if (!(kw > 0.0)) continue;     // zero weight (or a non-finite hypothesis) adds nothing
+        float dx[6];
+        for (int c = 0; c < 6; ++c) dx[c] = (float)(xs[c] - seedp[c]);
+        float acc[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int h = rank * blockDim.x + tid; h < n; h += stride) {
+            const float4* o = reinterpret_cast<const float4*>(s.hyp_dp + (size_t)h * 8);
+            const float4 q0 = o[0], q1 = o[1];
+            const float d0 = dx[0] - q0.x, d1 = dx[1] - q0.y, d2 = dx[2] - q0.z;
+            const float d3 = dx[3] - q0.w, d4 = dx[4] - q1.x, d5 = dx[5] - q1.y;
+            const float m = fmaf(d0 * d0 + d1 * d1 + d2 * d2, ivt, (d3 * d3 + d4 * d4 + d5 * d5) * ivr);
+            const float kw = q1.z * exp2f(mlog2e * m);
+            if (!(kw > 0.f)) continue;     // zero weight (or a non-finite hypothesis) adds nothing
             acc[0] += kw;
-            for (int c = 0; c < 6; ++c) acc[1 + c] += kw * ph[c];
+            acc[1] = fmaf(kw, q0.x, acc[1]); acc[2] = fmaf(kw, q0.y, acc[2]); acc[3] = fmaf(kw, q0.z, acc[3]);
+            acc[4] = fmaf(kw, q0.w, acc[4]); acc[5] = fmaf(kw, q1.x, acc[5]); acc[6] = fmaf(kw, q1.y, acc[6]);
         }
-        for (int c = 0; c < 7; ++c) acc[c] = warp_sum_d(acc[c]);
+        double accd[7];
+        for (int c = 0; c < 7; ++c) accd[c] = warp_sum_d((double)acc[c]);
         if (lane == 0)
-            for (int c = 0; c < 7; ++c) wred[warp][c] = acc[c];
+            for (int c = 0; c < 7; ++c) wred[warp][c] = accd[c];
         __syncthreads();
         const int buf = it & 1;
         if (tid < 7) {
@@ -586,11 +632,13 @@ k_meanshift(DevParams p, DevState s, int t)
             } else {
                 double step = 0.0;
                 for (int c = 0; c < 6; ++c) {
-                    const double xn = tot[1 + c] / tot[0];
+                    const double xn = seedp[c] + tot[1 + c] / tot[0];
                     step += (xn - xs[c]) * (xn - xs[c]);
                     xs[c] = xn;
                 }
-                flag = (sqrt(step) < p.ms_tol) ? 1 : 0;
+                step = sqrt(step);
+                flag = (step < p.ms_tol || (step >= prev_step && step < 1e-7)) ? 1 : 0;
+                prev_step = step;
             }
         }
         __syncthreads();

@@ -50,23 +50,27 @@ struct HypF {
     float e0, e1, e2, e3, e4, e5, e6, e7, e8, t0, t1, t2;
 };
 
-// log1p(r) for r >= 0: below 1/4 r * P(r) with P the degree-5 Chebyshev
-// interpolant of log1p(r)/r on [0, 1/4] (relative error 6e-8 in FP32
-// Horner form); above, ln2 * lg2(1 + r).
-__device__ __forceinline__ float log1p_pos(float r)
+// log2(1 + r) for r >= 0: below 1/4 r * P(r) with P the degree-5 Chebyshev
+// interpolant of log2(1 + r)/r on [0, 1/4] (relative error 7e-8 in FP32
+// Horner form); above, lg2(1 + r).
+__device__ __forceinline__ float log2_1p_pos(float r)
 {
-    float s = fmaf(r, -9.216756374e-02f, 1.815955490e-01f);
-    s = fmaf(r, s, -2.477561533e-01f);
-    s = fmaf(r, s, 3.332059979e-01f);
-    s = fmaf(r, s, -4.999973178e-01f);
-    s = fmaf(r, s, 1.0f);
+    float s = fmaf(r, -1.329696774e-01f, 2.619870007e-01f);
+    s = fmaf(r, s, -3.574365675e-01f);
+    s = fmaf(r, s, 4.807146490e-01f);
+    s = fmaf(r, s, -7.213436365e-01f);
+    s = fmaf(r, s, 1.442695022e+00f);
     const float small = r * s;
-    const float big = 0.69314718055994531f * mufu_lg2(1.f + r);
+    const float big = mufu_lg2(1.f + r);
     return r < 0.25f ? small : big;
 }
 
-// -ell = log1p(mu/rho) of one (hypothesis, pixel) pair; ln 2 behind camera t.
-__device__ __forceinline__ float pair_term(const HypF& h, const float4 a, const float4 b, float xs_min, float xs_max)
+// -ell / ln2 = log2(1 + mu/rho) of one (hypothesis, pixel) pair; 1 (log2 of
+// 2) behind camera t. The checked form tests 1 + a_z > 0 and caps the squared
+// residual at xs_max; the fast form is used only for hypotheses whose frame
+// bounds prove both unnecessary (hyp_is_safe).
+template <bool kChecked>
+__device__ __forceinline__ float pair_term2(const HypF& h, const float4 a, const float4 b, float xs_min, float xs_max)
 {
     const float xb = a.x, yb2 = a.y, w = a.z, ut = a.w;
     const float vt = b.x, beta = b.y, beta_k = b.z, Cp = b.w;
@@ -77,11 +81,29 @@ __device__ __forceinline__ float pair_term(const HypF& h, const float4 a, const 
     const float rd = mufu_rcp(den);
     const float ru = fmaf(fmaf(-xb, az, ax), rd, -ut);
     const float rv = fmaf(fmaf(-yb2, az, ay), rd, -vt);
-    const float xs = fminf(fmaxf(fmaf(ru, ru, rv * rv), xs_min), xs_max);
+    float xs = fmaxf(fmaf(ru, ru, rv * rv), xs_min);
+    if (kChecked) xs = fminf(xs, xs_max);
     const float sg = fabsf(fmaf(beta, mufu_lg2(xs), beta_k));
     const float r = Cp * xs * (mufu_ex2(sg) + (2.f + mufu_ex2(-sg)));
-    const float v = log1p_pos(r);
-    return den > 0.f ? v : 0.69314718055994531f;
+    const float v = log2_1p_pos(r);
+    if (kChecked) return den > 0.f ? v : 1.f;
+    return v;
+}
+
+// A hypothesis is safe for a frame if, for every record within the frame
+// bounds (|xb| <= bx, |yb2| <= by, 0 < w <= bw, |ut| <= bu, |vt| <= bv),
+// 1 + a_z >= 1/4 and the squared residual stays below xs_max; then the checks
+// of the pair term cannot change its value.
+__device__ __forceinline__ bool hyp_is_safe(const HypF& h, const float* bd, float xs_max)
+{
+    const float bx = bd[0], by = bd[1], bw = bd[2], bu = bd[3], bv = bd[4];
+    const float az_max = fabsf(h.e6) * bx + fabsf(h.e7) * by + fabsf(h.e8) + fabsf(h.t2) * bw;
+    const float ax_max = fabsf(h.e0) * bx + fabsf(h.e1) * by + fabsf(h.e2) + fabsf(h.t0) * bw;
+    const float ay_max = fabsf(h.e3) * bx + fabsf(h.e4) * by + fabsf(h.e5) + fabsf(h.t1) * bw;
+    if (!(az_max <= 0.75f)) return false;               // 1 + a_z >= 1/4, so 1/(1 + a_z) <= 4
+    const float ru = 4.f * (ax_max + bx * az_max) + bu;
+    const float rv = 4.f * (ay_max + by * az_max) + bv;
+    return ru * ru + rv * rv < 0.5f * xs_max;
 }
 
 // Bulk-copy staging of pixel-record tiles: one thread issues
@@ -174,6 +196,14 @@ __global__ void __launch_bounds__(kScoreThreads, kScoreBlocksPerSM) k_score(DevP
 #pragma unroll
     for (int i = 0; i < kScoreHypsPerThread; ++i) acc[i] = 0.0;
     const float xs_min = p.xs_min, xs_max = p.xs_max;
+    bool safe = true;
+    {
+        float bd[5];
+        for (int q = 0; q < 5; ++q) bd[q] = s.pix_bounds[q];
+#pragma unroll
+        for (int i = 0; i < kScoreHypsPerThread; ++i) safe = safe && hyp_is_safe(hy[i], bd, xs_max);
+    }
+    const bool warp_safe = __all_sync(0xffffffffu, safe);
 
     int it = 0;
     for (; it < n_tiles; ++it) {
@@ -186,12 +216,24 @@ __global__ void __launch_bounds__(kScoreThreads, kScoreBlocksPerSM) k_score(DevP
         float facc[kScoreHypsPerThread];
 #pragma unroll
         for (int i = 0; i < kScoreHypsPerThread; ++i) facc[i] = 0.f;
-        for (int q = 0; q < cnt; ++q) {
-            const float4 a = t4[3 * q];
-            const float4 b = t4[3 * q + 1];
-            const float wq = reinterpret_cast<const float*>(t4 + 3 * q + 2)[0];
+        if (warp_safe) {
+            for (int q = 0; q < cnt; ++q) {
+                const float4 a = t4[3 * q];
+                const float4 b = t4[3 * q + 1];
+                const float wq = reinterpret_cast<const float*>(t4 + 3 * q + 2)[0];
 #pragma unroll
-            for (int i = 0; i < kScoreHypsPerThread; ++i) facc[i] = fmaf(wq, pair_term(hy[i], a, b, xs_min, xs_max), facc[i]);
+                for (int i = 0; i < kScoreHypsPerThread; ++i)
+                    facc[i] = fmaf(wq, pair_term2<false>(hy[i], a, b, xs_min, xs_max), facc[i]);
+            }
+        } else {
+            for (int q = 0; q < cnt; ++q) {
+                const float4 a = t4[3 * q];
+                const float4 b = t4[3 * q + 1];
+                const float wq = reinterpret_cast<const float*>(t4 + 3 * q + 2)[0];
+#pragma unroll
+                for (int i = 0; i < kScoreHypsPerThread; ++i)
+                    facc[i] = fmaf(wq, pair_term2<true>(hy[i], a, b, xs_min, xs_max), facc[i]);
+            }
         }
 #pragma unroll
         for (int i = 0; i < kScoreHypsPerThread; ++i) acc[i] += (double)facc[i];
@@ -214,11 +256,11 @@ __global__ void __launch_bounds__(kScoreThreads, kScoreBlocksPerSM) k_score(DevP
 #pragma unroll
     for (int i = 0; i < kScoreHypsPerThread; ++i) {
         const int h = tile0 + i * kScoreThreads + threadIdx.x;
-        if (h < n_hyp) s.partial[(size_t)chunk * S + h] = -acc[i];
+        if (h < n_hyp) s.partial[(size_t)chunk * S + h] = -acc[i] * 0.69314718055994531;
     }
 }
 
-// L_h = sum over chunks, in chunk order.
+// L_h = sum over chunks, in chunk order (partials are in natural-log units).
 __global__ void k_score_reduce(DevParams p, DevState s)
 {
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
@@ -302,7 +344,8 @@ k_score_records(const float4* __restrict__ pix, int n_pix, const float* __restri
             const float4 b = __ldg(pix + 3 * j + 1);
             const float wq = __ldg(reinterpret_cast<const float*>(pix + 3 * j + 2));
 #pragma unroll
-            for (int i = 0; i < kScoreHypsPerThread; ++i) facc[i] = fmaf(wq, pair_term(hy[i], a, b, xs_min, xs_max), facc[i]);
+            for (int i = 0; i < kScoreHypsPerThread; ++i)
+                facc[i] = fmaf(wq, pair_term2<true>(hy[i], a, b, xs_min, xs_max), facc[i]);
         }
 #pragma unroll
         for (int i = 0; i < kScoreHypsPerThread; ++i) { acc[i] += (double)facc[i]; facc[i] = 0.f; }
@@ -310,7 +353,7 @@ k_score_records(const float4* __restrict__ pix, int n_pix, const float* __restri
 #pragma unroll
     for (int i = 0; i < kScoreHypsPerThread; ++i) {
         const int h = tile0 + i * kScoreThreads + threadIdx.x;
-        if (h < n_hyp) partial[(size_t)chunk * kStaticMaxHyps + h] = -acc[i];
+        if (h < n_hyp) partial[(size_t)chunk * kStaticMaxHyps + h] = -acc[i] * 0.69314718055994531;
     }
 }
 
@@ -376,20 +419,30 @@ extern "C" voldor_status voldor_score_records_noalloc(const float* records, int 
 // depend on the clock frequency.
 // ---------------------------------------------------------------------------
 namespace vd {
+__device__ __forceinline__ float sfu_step(int op, float v)
+{
+    float y;
+    if (op == 0) {          // exp2(-|v|): stays in [0.5, 1)
+        asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-fabsf(v)));
+    } else if (op == 1) {   // log2(v) + 1.5: converges to ~3.2, stays normal
+        asm volatile("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(v));
+        y += 1.5f;
+    } else {                // 1 / (-v): alternates between two normal values
+        asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-v));
+    }
+    return y;
+}
+
 __global__ void __launch_bounds__(256) k_sfu_probe(int op, int iters, float seed, float* sink, long long* cycles)
 {
     float v[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = seed + 0.001f * (threadIdx.x + i);
+    for (int i = 0; i < 8; ++i) v[i] = seed + 0.001f * (float)((threadIdx.x + i) & 63);
     __syncthreads();
     const long long t0 = clock64();
     for (int it = 0; it < iters; ++it) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            if (op == 0) v[i] = mufu_ex2(v[i]);
-            else if (op == 1) v[i] = mufu_lg2(v[i]);
-            else v[i] = mufu_rcp(v[i]);
-        }
+        for (int i = 0; i < 8; ++i) v[i] = sfu_step(op, v[i]);
     }
     __syncthreads();
     const long long t1 = clock64();
@@ -413,8 +466,7 @@ extern "C" voldor_status voldor_probe_sfu_rate(int op, double* results_per_sm_cl
     long long* cyc = nullptr;
     if (cudaMalloc(&sink, threads * sizeof(float)) != cudaSuccess) return VOLDOR_ERR_OOM;
     if (cudaMalloc(&cyc, blocks * sizeof(long long)) != cudaSuccess) { cudaFree(sink); return VOLDOR_ERR_OOM; }
-    // ex2 and rcp chains stay bounded from these seeds; lg2 of values in (0, 1)
-    const float seed = op == 1 ? 0.5f : 0.75f;
+    const float seed = op == 1 ? 1.5f : 0.75f;
     k_sfu_probe<<<blocks, threads>>>(op, 64, seed, sink, cyc);          // warm-up
     k_sfu_probe<<<blocks, threads>>>(op, iters, seed, sink, cyc);
     std::vector<long long> h(blocks);

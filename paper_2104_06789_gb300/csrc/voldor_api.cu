@@ -126,6 +126,7 @@ size_t layout(voldor_ctx& c, char* base)
     s.pix = (PixRec*)take(N * sizeof(PixRec));
     s.pix_block_count = (int*)take(((N + kPixThreads - 1) / kPixThreads) * 4);
     s.pix_count = (int*)take(4);
+    s.pix_bounds = (float*)take(8 * 4);
     s.grp_sols = (double*)take(G * kMaxSols * 12 * 8);
     s.grp_weight = (double*)take(G * 8);
     s.grp_count = (int*)take(G * 4);
@@ -135,6 +136,8 @@ size_t layout(voldor_ctx& c, char* base)
     s.hyp_f32 = (float*)take(S * 12 * 4);
     s.hyp_p = (double*)take(S * 6 * 8);
     s.hyp_w = (double*)take(S * 8);
+    s.hyp_dp = (float*)take(S * 8 * 4);
+    s.grp_found = (int*)take(4);
     s.hyp_info = (long long*)take(S * 2 * 8);
     s.partial = (double*)take((size_t)chunks * S * 8);
     s.scores = (double*)take(S * 8);

@@ -19,7 +19,7 @@ constexpr int kScoreHypsPerThread = 8;   // independent hypotheses per thread (I
 constexpr int kScoreBlocksPerSM = 1;
 constexpr int kScoreHypsPerBlock = kScoreThreads * kScoreHypsPerThread;
 constexpr int kMeanshiftCtas = 8;      // thread-block cluster of the meanshift
-constexpr int kMeanshiftThreads = 1024;
+constexpr int kMeanshiftThreads = 256;
 constexpr int kPixThreads = 256;
 constexpr int kScoreLogMax = 1024;
 constexpr int kMaxImageSide = 4096;   // longest chain the depth sweep resolves in shared memory
@@ -66,6 +66,7 @@ struct DevState {
     PixRec* pix;              // [N] compacted valid pixels of the current frame
     int* pix_block_count;     // [ceil(N / kPixThreads)]
     int* pix_count;           // [1]
+    float* pix_bounds;        // [8] max |xb|, |yb2|, w, |ut|, |vt| over the current frame's records
     // P3P
     double* grp_sols;         // [G][4][12]
     double* grp_weight;       // [G]
@@ -76,6 +77,8 @@ struct DevState {
     float* hyp_f32;           // [S][12] scoring form
     double* hyp_p;            // [S][6] se(3) log
     double* hyp_w;            // [S]
+    float* hyp_dp;            // [S][8] meanshift scratch: p_h - p_seed (6), w_h, 0
+    int* grp_found;           // [1] solutions of the first group half
     long long* hyp_info;      // [S][2]
     double* partial;          // [n_chunks][S]
     double* scores;           // [S]
