@@ -340,11 +340,13 @@ __global__ void k_count_found(DevState s, int n)
 // so later groups cannot contribute otherwise).
 void launch_p3p_groups(const DevParams& p, const DevState& s, int t, cudaStream_t st)
 {
+    // one warp per block: the solve is FP64-bound per SM, so the groups are
+    // spread over every SM
     const int g1 = p.G < p.S ? p.G : p.S;
-    k_p3p_groups<<<(g1 + 127) / 128, 128, 0, st>>>(p, s, t, 0, g1, 0);
+    k_p3p_groups<<<(g1 + 31) / 32, 32, 0, st>>>(p, s, t, 0, g1, 0);
     if (g1 < p.G) {
         k_count_found<<<1, 1024, 0, st>>>(s, g1);
-        k_p3p_groups<<<(p.G - g1 + 127) / 128, 128, 0, st>>>(p, s, t, g1, p.G, 1);
+        k_p3p_groups<<<(p.G - g1 + 31) / 32, 32, 0, st>>>(p, s, t, g1, p.G, 1);
     }
 }
 

@@ -34,6 +34,8 @@ struct voldor_ctx {
     std::map<long long, long long> graph_kernels;   // kernel nodes per cached graph
     long long launches = 0;                          // kernels enqueued so far
     cudaError_t first_error = cudaSuccess;           // the error that poisoned the context
+    cudaStream_t aux = nullptr;                      // second stream: P3P beside the pose preparation
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -187,8 +189,13 @@ bool enqueue_pose_update(voldor_ctx* c, int t, cudaEvent_t ev0, cudaEvent_t ev1,
     const DevState& s = c->ds;
     cudaStream_t st = c->stream;
     launch_frame_setup(p, s, st);
+    // the minimal groups and P3P (FP64) run beside the pixel records
+    if (!cuda_ok(c, cudaEventRecord(c->ev_fork, st))) return false;
+    if (!cuda_ok(c, cudaStreamWaitEvent(c->aux, c->ev_fork, 0))) return false;
+    launch_p3p_groups(p, s, t, c->aux);
+    if (!cuda_ok(c, cudaEventRecord(c->ev_join, c->aux))) return false;
     launch_pose_prep(p, s, t, st);
-    launch_p3p_groups(p, s, t, st);
+    if (!cuda_ok(c, cudaStreamWaitEvent(st, c->ev_join, 0))) return false;
     launch_hyp_collect(p, s, st);
     // External records become event-record nodes when the stream is captured
     if (ev0 && !cuda_ok(c, cudaEventRecordWithFlags(ev0, st, cudaEventRecordExternal))) return false;
@@ -321,6 +328,12 @@ voldor_status voldor_init_window(voldor_ctx** out, int width, int height, int T,
     }
     c->arena_bytes = bytes;
     layout(*c, (char*)c->arena);
+    if (!cuda_ok(c, cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking)) ||
+        !cuda_ok(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) ||
+        !cuda_ok(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming))) {
+        voldor_destroy(c);
+        return kCuda;
+    }
     if (!cuda_ok(c, cudaMemsetAsync(c->arena, 0, bytes, c->stream))) { voldor_destroy(c); return kCuda; }
     voldor_status st = upload_flows(c, flows, flows_on_device);
     if (st != VOLDOR_OK) { voldor_destroy(c); return st; }
@@ -437,6 +450,9 @@ void voldor_destroy(voldor_ctx* c)
     else cudaDeviceSynchronize();
     for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    if (c->aux) { cudaStreamSynchronize(c->aux); cudaStreamDestroy(c->aux); }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->arena) cudaFree(c->arena);
     cudaGetLastError();
     delete c;
