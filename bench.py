@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--hyps", type=int, default=8192)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="run the batched workload instead: this many windows of mixed size and T in one graph")
     return ap.parse_args()
 
 
@@ -322,9 +324,106 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# batched workload: many windows of mixed resolution and T in one CUDA graph
+# ---------------------------------------------------------------------------
+def batch_workload(n, seed=4000):
+    """n windows, resolutions uniform over {320x240, 640x480, 1242x375} and T
+    uniform in [3, 8]; two rendered scenes per resolution (planar-patch scenes
+    at 320x240, handheld scenes otherwise, focal scaled with the width), each
+    window taking the first T flows of one of them and its own Philox key."""
+    from paper_2104_06789_gb300 import synthetic
+    rng = np.random.default_rng(seed)
+    bases = {}
+    for r, (W, H) in enumerate([(320, 240), (640, 480), (1242, 375)]):
+        for v in range(2):
+            sd = seed + 10 * r + v
+            if W == 320:
+                bases[(r, v)] = synthetic.small_planes(seed=sd, W=W, H=H, f=0.75 * W, T=8)
+            else:
+                bases[(r, v)] = synthetic.handheld(seed=sd, W=W, H=H, f=0.82 * W, T=8)
+    out = []
+    for i in range(n):
+        r = int(rng.integers(0, 3))
+        T = int(rng.integers(3, 9))
+        b = bases[(r, int(rng.integers(0, 2)))]
+        out.append((b, T))
+    return out
+
+
+def run_batch(args):
+    import torch
+
+    from paper_2104_06789_gb300 import build, voldor
+    torch.cuda.set_device(0)
+    build.build()
+    wl = batch_workload(args.batch)
+    S = 4096
+    wins, tune = [], []
+    for i, (b, T) in enumerate(wl):
+        p = voldor.default_params(hyps_per_frame=S, groups_per_frame=2 * S, inv_depth_min=b.inv_depth_range[0],
+                                  inv_depth_max=b.inv_depth_range[1], window_id=i)
+        g = voldor.Window(np.ascontiguousarray(b.flows[:T].astype(np.float16)), b.K, p)
+        g.bootstrap(b.poses[0])
+        tune.append(g.autotune())
+        wins.append((g, b, T))
+    stream = torch.cuda.Stream()
+
+    def boot_all():
+        for g, b, T in wins:
+            g.bootstrap(b.poses[0])
+
+    batch = voldor.Batch([g for g, _, _ in wins], args.iters)
+    for _ in range(args.warmup):
+        boot_all()
+        batch.run(stream)
+    lat, walls = [], []
+    for _ in range(args.steps):
+        boot_all()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.extend(batch.run(stream).tolist())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        walls.append(e0.elapsed_time(e1))
+    # the same windows one after another (em_step each), for comparison
+    seq = []
+    for _ in range(max(1, args.steps // 2)):
+        boot_all()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for g, _, _ in wins:
+            g.em_step(args.iters)
+        torch.cuda.synchronize()
+        seq.append((time.perf_counter() - t0) * 1e3)
+    n = len(wins)
+    wall = float(np.median(walls))
+    units = sum(b.H * b.W * T * args.iters for _, b, T in wins)
+    shapes = {}
+    for hpt, ch, _ in tune:
+        shapes[f"{hpt}x{ch}"] = shapes.get(f"{hpt}x{ch}", 0) + 1
+    line = {"metric": "windows/s, mixed 320x240/640x480/1242x375 windows, T in [3,8], one CUDA graph",
+            "value": n / (wall / 1e3), "unit": "windows/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": wall, "higher_is_better": True, "data": "synthetic", "dtype": "f32",
+            "config": {"workload": "batch_mixed", "windows": n, "em_iters": args.iters, "hyps_per_frame": S,
+                       "flows": "fp16", "resolutions": sorted({f"{b.W}x{b.H}" for _, b, _ in wins})},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(np.max(lat))},
+            "mpixel_frame_per_s": units / (wall / 1e3) / 1e6,
+            "sequential_em_step_ms": float(np.median(seq)), "batch_speedup_vs_sequential": float(np.median(seq)) / wall,
+            "autotuned_shapes": shapes}
+    print(json.dumps(line), flush=True)
+    batch.destroy()
+    for g, _, _ in wins:
+        g.destroy()
+
+
 def main():
     args = parse_args()
-    if args.impl == "reference":
+    if args.batch:
+        run_batch(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

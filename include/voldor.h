@@ -237,6 +237,40 @@ voldor_status voldor_score_records_noalloc(const float* records, int n_pix, cons
  * few KB; synchronises the device. Errors: INVALID_ARG, OOM, CUDA. */
 voldor_status voldor_probe_sfu_rate(int op, double* results_per_sm_clock);
 
+/* ---------------------------------------------------------------------------
+ * Batching and tuning (SURVEY config 4; no counterpart in the paper).
+ * ------------------------------------------------------------------------- */
+
+/* Autotunes the dense-scoring tile shape of one window: hypotheses per thread
+ * (4 or 8, i.e. 1024 or 2048 hypotheses per block) and pixel chunks (1, 2, 4
+ * or 8 waves of resident blocks), timing each candidate with CUDA events on
+ * the window's own frame-1 hypotheses and records. Keeps the fastest;
+ * discards captured graphs that used another shape. Overwrites the stage
+ * buffers (hypotheses, records), not the state (poses, depth, W, k).
+ * Synchronises. Outputs may be NULL. */
+voldor_status voldor_autotune(voldor_ctx* ctx, int* hyps_per_thread, int* chunks, float* best_ms);
+
+/* Sets the dense-scoring tile shape directly (hyps_per_thread 4 or 8). */
+voldor_status voldor_set_score_shape(voldor_ctx* ctx, int hyps_per_thread, int chunks);
+
+/* A batch of windows run as one CUDA graph: every window's n_iters
+ * iterations (the graph voldor_em_step would replay) become independent
+ * branches of a single graph launch, so windows of different sizes and T run
+ * concurrently. Each window must be bootstrapped and appear once; windows
+ * must outlive the batch. */
+typedef struct voldor_batch voldor_batch;
+voldor_status voldor_batch_create(voldor_ctx* const* ctxs, int n, int n_iters, voldor_batch** out);
+
+/* Launches the batch on `cuda_stream` and synchronises. latency_ms (n floats,
+ * or NULL) receives, per window, the time from the batch start to the end of
+ * that window's last kernel (CUDA events). Returns DEGENERATE if any window
+ * had a frame without weighted hypotheses. */
+voldor_status voldor_batch_run(voldor_batch* batch, void* cuda_stream, float* latency_ms);
+void voldor_batch_destroy(voldor_batch* batch);
+
+/* One-shot form: create, run on the legacy stream, destroy. */
+voldor_status voldor_em_batch(voldor_ctx* const* ctxs, int n, int n_iters);
+
 /* Device memory held by the context, bytes. */
 size_t voldor_device_bytes(const voldor_ctx* ctx);
 

@@ -149,7 +149,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return false;
 }
 
-__global__ void __launch_bounds__(kScoreThreads, kScoreBlocksPerSM) k_score(DevParams p, DevState s, int log_idx)
+// HPT hypotheses per thread (the hypothesis side of the tile, HPT * 256 per
+// block); MINB resident blocks per SM. The autotuner picks among the instances.
+template <int HPT, int MINB>
+__global__ void __launch_bounds__(kScoreThreads, MINB) k_score(DevParams p, DevState s, int log_idx)
 {
     const int n_hyp = *s.n_hyp;
     const int n_pix = *s.pix_count;
@@ -157,7 +160,7 @@ __global__ void __launch_bounds__(kScoreThreads, kScoreBlocksPerSM) k_score(DevP
         s.score_log[2 * log_idx] = n_hyp;
         s.score_log[2 * log_idx + 1] = n_pix;
     }
-    const int tile0 = blockIdx.x * kScoreHypsPerBlock;
+    const int tile0 = blockIdx.x * (kScoreThreads * HPT);
     if (tile0 >= n_hyp) return;
     const int chunk = blockIdx.y, n_chunks = gridDim.y;
     const long long lo = (long long)n_pix * chunk / n_chunks;
@@ -185,23 +188,23 @@ __global__ void __launch_bounds__(kScoreThreads, kScoreBlocksPerSM) k_score(DevP
     if (threadIdx.x == 0)
         for (int i = 0; i < kStages && i < n_tiles; ++i) issue(i);
 
-    HypF hy[kScoreHypsPerThread];
+    HypF hy[HPT];
 #pragma unroll
-    for (int i = 0; i < kScoreHypsPerThread; ++i) {
+    for (int i = 0; i < HPT; ++i) {
         const int h = tile0 + i * kScoreThreads + threadIdx.x;
         const float* f = s.hyp_f32 + (size_t)min(h, n_hyp - 1) * 12;
         hy[i] = HypF{f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7], f[8], f[9], f[10], f[11]};
     }
-    double acc[kScoreHypsPerThread];
+    double acc[HPT];
 #pragma unroll
-    for (int i = 0; i < kScoreHypsPerThread; ++i) acc[i] = 0.0;
+    for (int i = 0; i < HPT; ++i) acc[i] = 0.0;
     const float xs_min = p.xs_min, xs_max = p.xs_max;
     bool safe = true;
     {
         float bd[5];
         for (int q = 0; q < 5; ++q) bd[q] = s.pix_bounds[q];
 #pragma unroll
-        for (int i = 0; i < kScoreHypsPerThread; ++i) safe = safe && hyp_is_safe(hy[i], bd, xs_max);
+        for (int i = 0; i < HPT; ++i) safe = safe && hyp_is_safe(hy[i], bd, xs_max);
     }
     const bool warp_safe = __all_sync(0xffffffffu, safe);
 
@@ -213,16 +216,16 @@ __global__ void __launch_bounds__(kScoreThreads, kScoreBlocksPerSM) k_score(DevP
         if (timed_out) break;
         const int cnt = (int)min((long long)kTilePix, hi - (lo + (long long)it * kTilePix));
         const float4* t4 = &tile[slot][0];
-        float facc[kScoreHypsPerThread];
+        float facc[HPT];
 #pragma unroll
-        for (int i = 0; i < kScoreHypsPerThread; ++i) facc[i] = 0.f;
+        for (int i = 0; i < HPT; ++i) facc[i] = 0.f;
         if (warp_safe) {
             for (int q = 0; q < cnt; ++q) {
                 const float4 a = t4[3 * q];
                 const float4 b = t4[3 * q + 1];
                 const float wq = reinterpret_cast<const float*>(t4 + 3 * q + 2)[0];
 #pragma unroll
-                for (int i = 0; i < kScoreHypsPerThread; ++i)
+                for (int i = 0; i < HPT; ++i)
                     facc[i] = fmaf(wq, pair_term2<false>(hy[i], a, b, xs_min, xs_max), facc[i]);
             }
         } else {
@@ -231,12 +234,12 @@ __global__ void __launch_bounds__(kScoreThreads, kScoreBlocksPerSM) k_score(DevP
                 const float4 b = t4[3 * q + 1];
                 const float wq = reinterpret_cast<const float*>(t4 + 3 * q + 2)[0];
 #pragma unroll
-                for (int i = 0; i < kScoreHypsPerThread; ++i)
+                for (int i = 0; i < HPT; ++i)
                     facc[i] = fmaf(wq, pair_term2<true>(hy[i], a, b, xs_min, xs_max), facc[i]);
             }
         }
 #pragma unroll
-        for (int i = 0; i < kScoreHypsPerThread; ++i) acc[i] += (double)facc[i];
+        for (int i = 0; i < HPT; ++i) acc[i] += (double)facc[i];
         __syncthreads();                       // every thread is done with this slot
         if (threadIdx.x == 0 && it + kStages < n_tiles) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -254,7 +257,7 @@ __global__ void __launch_bounds__(kScoreThreads, kScoreBlocksPerSM) k_score(DevP
     }
     const int S = p.S;
 #pragma unroll
-    for (int i = 0; i < kScoreHypsPerThread; ++i) {
+    for (int i = 0; i < HPT; ++i) {
         const int h = tile0 + i * kScoreThreads + threadIdx.x;
         if (h < n_hyp) s.partial[(size_t)chunk * S + h] = -acc[i] * 0.69314718055994531;
     }
@@ -272,7 +275,7 @@ __global__ void k_score_reduce(DevParams p, DevState s)
 
 static int g_num_sms = 0;
 
-int score_chunks(int S, int N)
+static int num_sms()
 {
     if (g_num_sms == 0) {
         int dev = 0;
@@ -280,18 +283,38 @@ int score_chunks(int S, int N)
         if (cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || g_num_sms <= 0)
             g_num_sms = 152;
     }
-    const int tiles = (S + kScoreHypsPerBlock - 1) / kScoreHypsPerBlock;
-    // four waves of the resident blocks, for load balance
-    int chunks = (g_num_sms * kScoreBlocksPerSM * 4 + tiles - 1) / tiles;
+    return g_num_sms;
+}
+
+// Pixel chunks so that (hypothesis tiles x chunks) blocks fill `waves` waves
+// of the resident blocks of a tile shape.
+int score_chunks_for(int S, int N, int hpt, int waves)
+{
+    const int minb = hpt == 8 ? 1 : 2;
+    const int tiles = (S + kScoreThreads * hpt - 1) / (kScoreThreads * hpt);
+    int chunks = (num_sms() * minb * waves + tiles - 1) / tiles;
     if (chunks > N) chunks = N;
     return chunks < 1 ? 1 : chunks;
 }
 
+int score_chunks(int S, int N) { return score_chunks_for(S, N, kScoreHypsPerThread, 4); }
+
+int score_chunks_max(int S, int N)
+{
+    const int a = score_chunks_for(S, N, 8, kTuneMaxWaves), b = score_chunks_for(S, N, 4, kTuneMaxWaves);
+    return a > b ? a : b;
+}
+
 void launch_score(const DevParams& p, const DevState& s, int log_idx, cudaStream_t st)
 {
-    const int tiles = (p.S + kScoreHypsPerBlock - 1) / kScoreHypsPerBlock;
-    dim3 grid(tiles, s.n_chunks);
-    k_score<<<grid, kScoreThreads, 0, st>>>(p, s, log_idx < kScoreLogMax ? log_idx : -1);
+    const int li = log_idx < kScoreLogMax ? log_idx : -1;
+    if (s.score_hpt == 4) {
+        dim3 grid((p.S + kScoreThreads * 4 - 1) / (kScoreThreads * 4), s.n_chunks);
+        k_score<4, 2><<<grid, kScoreThreads, 0, st>>>(p, s, li);
+    } else {
+        dim3 grid((p.S + kScoreThreads * 8 - 1) / (kScoreThreads * 8), s.n_chunks);
+        k_score<8, 1><<<grid, kScoreThreads, 0, st>>>(p, s, li);
+    }
 }
 
 void launch_score_reduce(const DevParams& p, const DevState& s, cudaStream_t st)

@@ -28,6 +28,7 @@ struct voldor_ctx {
     bool poisoned = false;
     bool timing = false;
     std::map<long long, cudaGraphExec_t> graphs;
+    std::map<long long, cudaGraph_t> raw_graphs;   // the captured graphs, for embedding in batches
     std::vector<cudaEvent_t> events;  // start/stop pairs of the timed graph
     int last_pairs = 0;
     int graph_pairs = 0;
@@ -107,6 +108,7 @@ size_t layout(voldor_ctx& c, char* base)
     const size_t N = (size_t)c.N, T = (size_t)c.T;
     const size_t S = (size_t)c.params.hyps_per_frame, G = (size_t)c.params.groups_per_frame;
     const int chunks = score_chunks((int)S, c.N);
+    const int chunks_max = score_chunks_max((int)S, c.N);
     size_t off = 0;
     auto take = [&](size_t bytes) -> char* {
         char* p = base ? base + off : nullptr;
@@ -141,7 +143,7 @@ size_t layout(voldor_ctx& c, char* base)
     s.hyp_dp = (float*)take(S * 8 * 4);
     s.grp_found = (int*)take(4);
     s.hyp_info = (long long*)take(S * 2 * 8);
-    s.partial = (double*)take((size_t)chunks * S * 8);
+    s.partial = (double*)take((size_t)chunks_max * S * 8);
     s.scores = (double*)take(S * 8);
     s.mie_prev_score = (float*)take(N * 4);
     s.mie_smp = (float*)take(N * 4);
@@ -151,6 +153,7 @@ size_t layout(voldor_ctx& c, char* base)
     s.fb_fwd = (float*)take(T * N * 8);
     s.score_log = (long long*)take((size_t)kScoreLogMax * 2 * 8);
     s.n_chunks = chunks;
+    s.score_hpt = kScoreHypsPerThread;
     return off;
 }
 
@@ -255,6 +258,62 @@ bool ensure_events(voldor_ctx* c, int pairs)
         c->events.push_back(e);
     }
     return true;
+}
+
+// Captures n iterations of the VOLDOR loop (with timing events if asked) as a
+// CUDA graph, instantiates it and keeps both forms on the context.
+bool ensure_graph(voldor_ctx* c, int n_iters, bool timing)
+{
+    const long long key = (long long)n_iters * 2 + (timing ? 1 : 0);
+    if (c->graphs.count(key)) return true;
+    const bool saved_timing = c->timing;
+    c->timing = timing;
+    if (timing && !ensure_events(c, n_iters * c->T)) { c->timing = saved_timing; return false; }
+    cudaStream_t cap = c->stream;
+    bool own = false;
+    if (cap == nullptr) {   // the legacy stream cannot be captured
+        if (!cuda_ok(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking))) { c->timing = saved_timing; return false; }
+        own = true;
+    }
+    cudaStream_t saved = c->stream;
+    c->stream = cap;
+    cudaGraph_t g = nullptr;
+    bool ok = cuda_ok(c, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    if (ok) {
+        for (int i = 0; i < n_iters && ok; ++i) ok = enqueue_iteration(c, i * c->T);
+        cudaError_t ee = cudaStreamEndCapture(cap, &g);
+        ok = ok && cuda_ok(c, ee);
+    }
+    c->stream = saved;
+    c->timing = saved_timing;
+    if (own) cudaStreamDestroy(cap);
+    if (!ok) { if (g) cudaGraphDestroy(g); c->poisoned = true; return false; }
+    size_t n_nodes = 0;
+    long long n_kernels = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n_nodes) == cudaSuccess && n_nodes > 0) {
+        std::vector<cudaGraphNode_t> nodes(n_nodes);
+        if (cudaGraphGetNodes(g, nodes.data(), &n_nodes) == cudaSuccess)
+            for (size_t q = 0; q < n_nodes; ++q) {
+                cudaGraphNodeType ty;
+                if (cudaGraphNodeGetType(nodes[q], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++n_kernels;
+            }
+    }
+    cudaGraphExec_t ge = nullptr;
+    if (!cuda_ok(c, cudaGraphInstantiate(&ge, g, 0))) { cudaGraphDestroy(g); return false; }
+    c->graphs[key] = ge;
+    c->raw_graphs[key] = g;
+    c->graph_kernels[key] = n_kernels;
+    if (timing) c->graph_pairs = n_iters * c->T;
+    return true;
+}
+
+void drop_graphs(voldor_ctx* c)
+{
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : c->raw_graphs) cudaGraphDestroy(kv.second);
+    c->graphs.clear();
+    c->raw_graphs.clear();
+    c->graph_kernels.clear();
 }
 
 voldor_status read_status_word(voldor_ctx* c, int* host4)
@@ -370,46 +429,8 @@ voldor_status voldor_em_step(voldor_ctx* c, int n_iters)
     if (!c->bootstrapped) return VOLDOR_ERR_NOT_BOOTSTRAPPED;
     if (n_iters == 0) return VOLDOR_OK;
     const long long key = (long long)n_iters * 2 + (c->timing ? 1 : 0);
+    if (!ensure_graph(c, n_iters, c->timing)) return kCuda;
     auto it = c->graphs.find(key);
-    if (it == c->graphs.end()) {
-        if (c->timing && !ensure_events(c, n_iters * c->T)) return kCuda;
-        cudaStream_t cap = c->stream;
-        bool own = false;
-        if (cap == nullptr) {   // the legacy stream cannot be captured
-            if (!cuda_ok(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking))) return kCuda;
-            own = true;
-        }
-        cudaStream_t saved = c->stream;
-        c->stream = cap;
-        cudaGraph_t g = nullptr;
-        bool ok = cuda_ok(c, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-        if (ok) {
-            for (int i = 0; i < n_iters && ok; ++i) ok = enqueue_iteration(c, i * c->T);
-            cudaError_t ee = cudaStreamEndCapture(cap, &g);
-            ok = ok && cuda_ok(c, ee);
-        }
-        c->stream = saved;
-        if (own) cudaStreamDestroy(cap);
-        if (!ok) { if (g) cudaGraphDestroy(g); c->poisoned = true; return kCuda; }
-        size_t n_nodes = 0;
-        long long n_kernels = 0;
-        if (cudaGraphGetNodes(g, nullptr, &n_nodes) == cudaSuccess && n_nodes > 0) {
-            std::vector<cudaGraphNode_t> nodes(n_nodes);
-            if (cudaGraphGetNodes(g, nodes.data(), &n_nodes) == cudaSuccess)
-                for (size_t q = 0; q < n_nodes; ++q) {
-                    cudaGraphNodeType ty;
-                    if (cudaGraphNodeGetType(nodes[q], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++n_kernels;
-                }
-        }
-        cudaGraphExec_t ge = nullptr;
-        if (!cuda_ok(c, cudaGraphInstantiate(&ge, g, 0))) { cudaGraphDestroy(g); return kCuda; }
-        cudaGraphDestroy(g);
-        it = c->graphs.emplace(key, ge).first;
-        c->graph_kernels[key] = n_kernels;
-        if (c->timing) c->graph_pairs = n_iters * c->T;
-    }
-    int zero = 0;
-    (void)zero;
     if (!cuda_ok(c, cudaMemsetAsync(c->ds.status + 3, 0, 4, c->stream))) return kCuda;
     if (c->timing && !cuda_ok(c, cudaMemsetAsync(c->ds.score_log, 0, (size_t)kScoreLogMax * 16, c->stream))) return kCuda;
     if (!cuda_ok(c, cudaGraphLaunch(it->second, c->stream))) return kCuda;
@@ -448,7 +469,7 @@ void voldor_destroy(voldor_ctx* c)
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
-    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    drop_graphs(c);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     if (c->aux) { cudaStreamSynchronize(c->aux); cudaStreamDestroy(c->aux); }
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -628,5 +649,172 @@ const char* voldor_last_error_string(const voldor_ctx* c)
 }
 
 size_t voldor_device_bytes(const voldor_ctx* c) { return c ? c->arena_bytes : 0; }
+
+voldor_status voldor_autotune(voldor_ctx* c, int* hpt_out, int* chunks_out, float* best_ms_out)
+{
+    if (!c) return VOLDOR_ERR_INVALID_ARG;
+    if (c->poisoned) return kCuda;
+    if (!c->bootstrapped) return VOLDOR_ERR_NOT_BOOTSTRAPPED;
+    // hypotheses and pixel records of frame 1 on the current state
+    int k_saved = 0;
+    if (!cuda_ok(c, cudaMemcpyAsync(&k_saved, c->ds.iter, 4, cudaMemcpyDeviceToHost, c->stream))) return kCuda;
+    if (!cuda_ok(c, cudaStreamSynchronize(c->stream))) return kCuda;
+    launch_frame_setup(c->dp, c->ds, c->stream);
+    launch_p3p_groups(c->dp, c->ds, 1, c->stream);
+    launch_pose_prep(c->dp, c->ds, 1, c->stream);
+    launch_hyp_collect(c->dp, c->ds, c->stream);
+    if (!launched(c)) return kCuda;
+    cudaEvent_t e0, e1;
+    if (!cuda_ok(c, cudaEventCreate(&e0)) || !cuda_ok(c, cudaEventCreate(&e1))) return kCuda;
+    const int saved_hpt = c->ds.score_hpt, saved_chunks = c->ds.n_chunks;
+    int best_hpt = saved_hpt, best_chunks = saved_chunks;
+    float best = 1e30f;
+    bool ok = true;
+    const int hpts[2] = {8, 4};
+    const int waves[4] = {1, 2, 4, kTuneMaxWaves};
+    for (int hi = 0; hi < 2 && ok; ++hi) {
+        for (int wi = 0; wi < 4 && ok; ++wi) {
+            c->ds.score_hpt = hpts[hi];
+            c->ds.n_chunks = score_chunks_for(c->params.hyps_per_frame, c->N, hpts[hi], waves[wi]);
+            launch_score(c->dp, c->ds, -1, c->stream);            // warm-up
+            float ms[3];
+            for (int r = 0; r < 3 && ok; ++r) {
+                ok = cuda_ok(c, cudaEventRecord(e0, c->stream));
+                launch_score(c->dp, c->ds, -1, c->stream);
+                ok = ok && cuda_ok(c, cudaEventRecord(e1, c->stream)) && cuda_ok(c, cudaEventSynchronize(e1)) &&
+                     cuda_ok(c, cudaEventElapsedTime(&ms[r], e0, e1)) && launched(c);
+            }
+            if (!ok) break;
+            std::sort(ms, ms + 3);
+            if (ms[1] < best) { best = ms[1]; best_hpt = hpts[hi]; best_chunks = c->ds.n_chunks; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!ok) return kCuda;
+    c->ds.score_hpt = best_hpt;
+    c->ds.n_chunks = best_chunks;
+    if (best_hpt != saved_hpt || best_chunks != saved_chunks) drop_graphs(c);   // they captured the old shape
+    launch_set_iteration(c->ds, k_saved, c->stream);
+    if (!launched(c)) return kCuda;
+    if (hpt_out) *hpt_out = best_hpt;
+    if (chunks_out) *chunks_out = best_chunks;
+    if (best_ms_out) *best_ms_out = best;
+    return VOLDOR_OK;
+}
+
+voldor_status voldor_set_score_shape(voldor_ctx* c, int hpt, int chunks)
+{
+    if (!c || (hpt != 4 && hpt != 8) || chunks < 1) return VOLDOR_ERR_INVALID_ARG;
+    if (chunks > score_chunks_max(c->params.hyps_per_frame, c->N)) return VOLDOR_ERR_INVALID_ARG;
+    if (c->poisoned) return kCuda;
+    if (hpt != c->ds.score_hpt || chunks != c->ds.n_chunks) {
+        c->ds.score_hpt = hpt;
+        c->ds.n_chunks = chunks;
+        drop_graphs(c);
+    }
+    return VOLDOR_OK;
+}
+
+struct voldor_batch {
+    std::vector<voldor_ctx*> ctxs;
+    int n_iters = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t start = nullptr;
+    std::vector<cudaEvent_t> done;
+};
+
+void voldor_batch_destroy(voldor_batch* b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->start) cudaEventDestroy(b->start);
+    for (cudaEvent_t e : b->done) cudaEventDestroy(e);
+    cudaGetLastError();
+    delete b;
+}
+
+voldor_status voldor_batch_create(voldor_ctx* const* ctxs, int n, int n_iters, voldor_batch** out)
+{
+    if (!out) return VOLDOR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!ctxs || n < 1 || n_iters < 1) return VOLDOR_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) return VOLDOR_ERR_INVALID_ARG;
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return VOLDOR_ERR_INVALID_ARG;     // a window may appear once
+        if (ctxs[i]->poisoned) return kCuda;
+        if (!ctxs[i]->bootstrapped) return VOLDOR_ERR_NOT_BOOTSTRAPPED;
+    }
+    voldor_batch* b = new (std::nothrow) voldor_batch();
+    if (!b) return VOLDOR_ERR_OOM;
+    b->ctxs.assign(ctxs, ctxs + n);
+    b->n_iters = n_iters;
+    auto fail = [&](voldor_status st) { voldor_batch_destroy(b); return st; };
+    for (int i = 0; i < n; ++i)
+        if (!ensure_graph(ctxs[i], n_iters, false)) return fail(kCuda);
+    if (cudaEventCreate(&b->start) != cudaSuccess) return fail(kCuda);
+    b->done.resize(n, nullptr);
+    for (int i = 0; i < n; ++i)
+        if (cudaEventCreate(&b->done[i]) != cudaSuccess) return fail(kCuda);
+    if (cudaGraphCreate(&b->graph, 0) != cudaSuccess) return fail(kCuda);
+    cudaGraphNode_t start_node;
+    if (cudaGraphAddEventRecordNode(&start_node, b->graph, nullptr, 0, b->start) != cudaSuccess) return fail(kCuda);
+    const long long key = (long long)n_iters * 2;
+    for (int i = 0; i < n; ++i) {
+        voldor_ctx* c = ctxs[i];
+        cudaGraphNode_t reset, child, fin;
+        cudaMemsetParams mp{};
+        mp.dst = c->ds.status + 3;
+        mp.value = 0;
+        mp.elementSize = 4;
+        mp.width = 1;
+        mp.height = 1;
+        if (cudaGraphAddMemsetNode(&reset, b->graph, &start_node, 1, &mp) != cudaSuccess) return fail(kCuda);
+        if (cudaGraphAddChildGraphNode(&child, b->graph, &reset, 1, c->raw_graphs[key]) != cudaSuccess) return fail(kCuda);
+        if (cudaGraphAddEventRecordNode(&fin, b->graph, &child, 1, b->done[i]) != cudaSuccess) return fail(kCuda);
+    }
+    if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) return fail(kCuda);
+    *out = b;
+    return VOLDOR_OK;
+}
+
+voldor_status voldor_batch_run(voldor_batch* b, void* cuda_stream, float* latency_ms)
+{
+    if (!b) return VOLDOR_ERR_INVALID_ARG;
+    for (voldor_ctx* c : b->ctxs)
+        if (c->poisoned) return kCuda;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (cudaGraphLaunch(b->exec, st) != cudaSuccess) {
+        for (voldor_ctx* c : b->ctxs) c->poisoned = true;
+        return kCuda;
+    }
+    for (voldor_ctx* c : b->ctxs) c->launches += c->graph_kernels[(long long)b->n_iters * 2];
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        for (voldor_ctx* c : b->ctxs) c->poisoned = true;
+        return kCuda;
+    }
+    voldor_status result = VOLDOR_OK;
+    for (size_t i = 0; i < b->ctxs.size(); ++i) {
+        voldor_ctx* c = b->ctxs[i];
+        if (latency_ms && cudaEventElapsedTime(&latency_ms[i], b->start, b->done[i]) != cudaSuccess) return kCuda;
+        int deg = 0;
+        if (cudaMemcpy(&deg, c->ds.status + 3, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return kCuda;
+        if (deg) result = VOLDOR_ERR_DEGENERATE;
+    }
+    return result;
+}
+
+voldor_status voldor_em_batch(voldor_ctx* const* ctxs, int n, int n_iters)
+{
+    voldor_batch* b = nullptr;
+    voldor_status st = voldor_batch_create(ctxs, n, n_iters, &b);
+    if (st != VOLDOR_OK) return st;
+    st = voldor_batch_run(b, nullptr, nullptr);
+    voldor_batch_destroy(b);
+    return st;
+}
 
 }  // extern "C"

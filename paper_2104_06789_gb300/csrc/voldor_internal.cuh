@@ -22,6 +22,7 @@ constexpr int kMeanshiftCtas = 8;      // thread-block cluster of the meanshift
 constexpr int kMeanshiftThreads = 256;
 constexpr int kPixThreads = 256;
 constexpr int kScoreLogMax = 1024;
+constexpr int kTuneMaxWaves = 8;       // largest dense-scoring grid the autotuner tries, in waves
 constexpr int kMaxImageSide = 4096;   // longest chain the depth sweep resolves in shared memory
 
 // Everything a kernel needs to know about the window, by value.
@@ -91,6 +92,7 @@ struct DevState {
     float* fb_fwd;            // [T][H][W] forward messages
     long long* score_log;     // [kScoreLogMax][2] (n_hyp, n_pix) of timed scoring launches
     int n_chunks;             // dense scoring pixel chunks
+    int score_hpt;            // dense scoring hypotheses per thread (4 or 8)
 };
 
 // ---------------------------------------------------------------------------
@@ -270,6 +272,8 @@ void launch_mie(const DevParams& p, const DevState& s, cudaStream_t st);
 void launch_set_iteration(const DevState& s, int k, cudaStream_t st);
 void launch_advance_iteration(const DevState& s, cudaStream_t st);
 int score_chunks(int S, int N);
+int score_chunks_for(int S, int N, int hpt, int waves);
+int score_chunks_max(int S, int N);
 void score_hyps_from_host(const DevParams& p, const DevState& s, int n, cudaStream_t st);
 
 }  // namespace vd

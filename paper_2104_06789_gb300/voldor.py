@@ -82,6 +82,12 @@ def lib():
             "voldor_device_bytes": (sz, [vp]),
             "voldor_score_records_noalloc": (i, [vp, i, vp, i, d, d, vp, vp]),
             "voldor_probe_sfu_rate": (i, [i, P(d)]),
+            "voldor_autotune": (i, [vp, P(i), P(i), P(C.c_float)]),
+            "voldor_set_score_shape": (i, [vp, i, i]),
+            "voldor_batch_create": (i, [P(vp), i, i, P(vp)]),
+            "voldor_batch_run": (i, [vp, vp, P(C.c_float)]),
+            "voldor_batch_destroy": (None, [vp]),
+            "voldor_em_batch": (i, [P(vp), i, i]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -256,6 +262,17 @@ class Window:
     def device_bytes(self):
         return lib().voldor_device_bytes(self._h)
 
+    def autotune(self):
+        """(hypotheses per thread, pixel chunks, best ms) chosen for this window."""
+        hpt, ch, ms = C.c_int(0), C.c_int(0), C.c_float(0)
+        _check(lib().voldor_autotune(self._h, C.byref(hpt), C.byref(ch), C.byref(ms)), "voldor_autotune",
+               handle=self._h)
+        return hpt.value, ch.value, ms.value
+
+    def set_score_shape(self, hyps_per_thread, chunks):
+        _check(lib().voldor_set_score_shape(self._h, int(hyps_per_thread), int(chunks)), "voldor_set_score_shape",
+               handle=self._h)
+
     # -- convenience readers of the stage buffers -----------------------------------
     def hypotheses(self):
         S = self.params.hyps_per_frame
@@ -288,6 +305,40 @@ def probe_sfu_rate(op):
     v = C.c_double(0.0)
     _check(lib().voldor_probe_sfu_rate(int(op), C.byref(v)), "voldor_probe_sfu_rate")
     return v.value
+
+
+class Batch:
+    """Windows run together as one CUDA graph (voldor_batch_*)."""
+
+    def __init__(self, windows, n_iters):
+        self.windows = list(windows)
+        arr = (C.c_void_p * len(self.windows))(*[w._h for w in self.windows])
+        h = C.c_void_p()
+        _check(lib().voldor_batch_create(arr, len(self.windows), int(n_iters), C.byref(h)), "voldor_batch_create")
+        self._h = h
+
+    def run(self, stream=None, latency=True):
+        st = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+        lat = np.zeros(len(self.windows), np.float32)
+        _check(lib().voldor_batch_run(self._h, C.c_void_p(st), lat.ctypes.data_as(C.POINTER(C.c_float)) if latency
+                                      else None), "voldor_batch_run", (ERR_DEGENERATE,))
+        return lat
+
+    def destroy(self):
+        if getattr(self, "_h", None):
+            lib().voldor_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def em_batch(windows, n_iters):
+    arr = (C.c_void_p * len(windows))(*[w._h for w in windows])
+    return _check(lib().voldor_em_batch(arr, len(windows), int(n_iters)), "voldor_em_batch", (ERR_DEGENERATE,))
 
 
 def init_window(flows, K, params=None, stream=None) -> Window:
