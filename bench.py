@@ -51,6 +51,12 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch", type=int, default=0,
                     help="run the batched workload instead: this many windows of mixed size and T in one graph")
+    ap.add_argument("--learned", type=int, default=0,
+                    help="run the learned-proposal comparison instead: train on this many windows")
+    ap.add_argument("--heldout", type=int, default=64)
+    ap.add_argument("--train-steps", type=int, default=20000)
+    ap.add_argument("--workers", type=int, default=0, help="scene-generator processes (0: cpu count - 1)")
+    ap.add_argument("--save-weights", default="")
     return ap.parse_args()
 
 
@@ -419,9 +425,55 @@ def run_batch(args):
         g.destroy()
 
 
+def run_learned(args):
+    """Plain vs learned initialisation: generate and label the training
+    windows, train the proposal network with the library's kernels, compare
+    the pose error per EM iteration and the time to the plain EM's error on
+    held-out windows."""
+    import torch
+
+    from paper_2104_06789_gb300 import build, learned, voldor
+    workers = args.workers or max(1, (os.cpu_count() or 2) - 1)
+    log = lambda m: print(f"[learned] {m}", file=sys.stderr, flush=True)
+    S = 4096
+    torch.cuda.set_device(0)
+    build.build()
+    t0 = time.time()
+    train_seeds = [learned.TRAIN_SEED0 + i for i in range(args.learned)]
+    held_seeds = [learned.HELDOUT_SEED0 + i for i in range(args.heldout)]
+    ds = learned.build_dataset(train_seeds, S=S, label_iters=8, workers=workers, log=log)
+    t_data = time.time() - t0
+    log(f"training set: {ds.n} windows in {t_data:.0f} s")
+    held = learned.build_dataset(held_seeds, S=S, label_iters=0, workers=workers, log=log)
+    T = ds.flows.shape[1]
+    net = voldor.Net(T, learned.init_weights(T, seed=0))
+    t1 = time.time()
+    losses = learned.train(net, ds, args.train_steps, batch=2, lr=1e-3, log=log)
+    torch.cuda.synchronize()
+    t_train = time.time() - t1
+    pix_per_step = 2 * ds.flows.shape[2] * ds.flows.shape[3]
+    if args.save_weights:
+        np.save(args.save_weights, net.get_weights())
+    del ds
+    res = learned.compare(net, held, S=S, max_iters=8, plain_iters=args.iters)
+    line = {"metric": "EM iterations and wall time to the plain EM's pose error, learned vs triangulation init",
+            "value": res["learned_ms"], "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+            "data": "synthetic", "dtype": "bf16 net, f32/f64 EM",
+            "config": {"workload": "handheld scenes at 1242x375 f=718 T=8", "train_windows": len(train_seeds),
+                       "heldout_windows": len(held_seeds), "hyps_per_frame": S, "train_steps": args.train_steps,
+                       "batch": 2, "label_iters": 8},
+            "train_s": t_train, "train_mpix_per_s": pix_per_step * args.train_steps / t_train / 1e6,
+            "loss_first_last": [float(losses[:50].mean()), float(losses[-50:].mean())],
+            "data_s": t_data, **res}
+    print(json.dumps(line), flush=True)
+    net.destroy()
+
+
 def main():
     args = parse_args()
-    if args.batch:
+    if args.learned:
+        run_learned(args)
+    elif args.batch:
         run_batch(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -36,6 +36,7 @@ extern "C" {
 #endif
 
 typedef struct voldor_ctx voldor_ctx;
+typedef struct voldor_net voldor_net;
 
 typedef enum {
     VOLDOR_OK = 0,
@@ -238,7 +239,7 @@ voldor_status voldor_score_records_noalloc(const float* records, int n_pix, cons
 voldor_status voldor_probe_sfu_rate(int op, double* results_per_sm_clock);
 
 /* ---------------------------------------------------------------------------
- * Batching and tuning (SURVEY config 4; no counterpart in the paper).
+ * Batching and tuning of many windows (no counterpart in the paper).
  * ------------------------------------------------------------------------- */
 
 /* Autotunes the dense-scoring tile shape of one window: hypotheses per thread
@@ -270,6 +271,44 @@ void voldor_batch_destroy(voldor_batch* batch);
 
 /* One-shot form: create, run on the legacy stream, destroy. */
 voldor_status voldor_em_batch(voldor_ctx* const* ctxs, int n, int n_iters);
+
+/* ---------------------------------------------------------------------------
+ * Learned proposal (no counterpart in the paper): a 6-layer
+ * 3x3 convolutional network, 2T -> 32 -> 32 -> 32 -> 32 -> 32 -> 2 channels
+ * with ReLU between layers, reads the flows (divided by 32 px, 2 channels per
+ * frame, T <= 8) and predicts per pixel a log-depth and a rigidness logit. BF16
+ * weights and activations, FP32 accumulation on tensor cores, FP32 Adam on
+ * master weights. Parameters: per layer W[Cout][3][3][Cin] then bias[Cout],
+ * FP32, layers in order.
+ * ------------------------------------------------------------------------- */
+size_t voldor_net_num_params(int T);                 /* 0 if T is not in [1, 8] */
+voldor_status voldor_net_create(int T, voldor_net** out);   /* parameters start at zero */
+void voldor_net_destroy(voldor_net* net);
+voldor_status voldor_net_set_weights(voldor_net* net, const float* host, size_t count);   /* resets Adam */
+voldor_status voldor_net_get_weights(voldor_net* net, float* host, size_t count);
+/* Gradient of the last voldor_net_train_step's loss (before its update). */
+voldor_status voldor_net_get_grads(voldor_net* net, float* host, size_t count);
+/* Forward pass on B images of H x W: flows device [B][T][H][W][2], pred device
+ * [B][H][W][8] floats (channel 0 log-depth, 1 rigidness logit, rest zero). */
+voldor_status voldor_net_forward(voldor_net* net, const void* flows, int flow_dtype, int B, int H, int W, float* pred,
+                                 void* cuda_stream);
+/* One training step: forward, loss = mean over pixels of Huber(delta 0.1) on
+ * log-depth + lam_r * BCE on the rigidness logit (target device
+ * [B][H][W][2]: log-depth, rigidness in [0, 1]; a non-finite log-depth skips
+ * the pixel), backward, Adam (lr; lr = 0 computes gradients only). *loss
+ * (host, may be NULL) gets the loss before the update. Synchronises. */
+voldor_status voldor_net_train_step(voldor_net* net, const void* flows, int flow_dtype, const float* target, int B,
+                                    int H, int W, float lr, float lam_r, float* loss, void* cuda_stream);
+/* Learned bootstrap: poses, depth and W as in voldor_bootstrap (T_1 given,
+ * triangulated depth), then the network's prediction replaces
+ *   - with VOLDOR_LEARNED_DEPTH: the depth, exp(log-depth + s) clamped to the
+ *     depth range, where s = median over pixels of log(theta_tri) - log-depth
+ *     (pixels whose triangulated depth is strictly inside the range) puts the
+ *     prediction on the metric scale that T_1 fixes;
+ *   - with VOLDOR_LEARNED_RIGIDNESS: every W_t, by sigmoid(logit).
+ * flags = 0 is the plain bootstrap. The network's T must equal the window's. */
+enum { VOLDOR_LEARNED_DEPTH = 1, VOLDOR_LEARNED_RIGIDNESS = 2 };
+voldor_status voldor_bootstrap_learned(voldor_ctx* ctx, const double* T1_rowmajor_4x4, voldor_net* net, int flags);
 
 /* Device memory held by the context, bytes. */
 size_t voldor_device_bytes(const voldor_ctx* ctx);

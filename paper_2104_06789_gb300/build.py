@@ -25,6 +25,7 @@ UNITS = {
     "k_pose.cu": [],
     "k_score.cu": [],
     "voldor_api.cu": [],
+    "k_net.cu": [],
 }
 
 

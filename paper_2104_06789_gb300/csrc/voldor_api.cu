@@ -422,6 +422,26 @@ voldor_status voldor_bootstrap(voldor_ctx* c, int mode, const double* T1)
     return VOLDOR_OK;
 }
 
+voldor_status voldor_bootstrap_learned(voldor_ctx* c, const double* T1, voldor_net* net, int flags)
+{
+    if (!c || !net || !T1 || (flags & ~(VOLDOR_LEARNED_DEPTH | VOLDOR_LEARNED_RIGIDNESS))) return VOLDOR_ERR_INVALID_ARG;
+    if (c->poisoned) return kCuda;
+    for (int i = 0; i < 12; ++i)
+        if (!std::isfinite(T1[i])) return VOLDOR_ERR_INVALID_ARG;
+    launch_bootstrap(c->dp, c->ds, T1, c->stream);          // poses, k, W, and a triangulated depth
+    c->launches += 1;
+    if (!launched(c)) return kCuda;
+    int kernels = 0;
+    voldor_status s = net_bootstrap(net, c->ds.flows, c->flow_dtype == VOLDOR_FLOW_F16, c->W, c->H, c->T,
+                                    (float)(1.0 / c->params.inv_depth_max), (float)(1.0 / c->params.inv_depth_min),
+                                    flags, c->ds.theta, c->ds.wmap, c->stream, &kernels);
+    c->launches += kernels;
+    if (s != VOLDOR_OK) return s == VOLDOR_ERR_CUDA ? (c->poisoned = true, kCuda) : s;
+    if (!cuda_ok(c, cudaMemsetAsync(c->ds.status, 0, 16, c->stream))) return kCuda;
+    c->bootstrapped = true;
+    return VOLDOR_OK;
+}
+
 voldor_status voldor_em_step(voldor_ctx* c, int n_iters)
 {
     if (!c || n_iters < 0) return VOLDOR_ERR_INVALID_ARG;

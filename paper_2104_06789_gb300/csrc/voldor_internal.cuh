@@ -272,6 +272,10 @@ void launch_mie(const DevParams& p, const DevState& s, cudaStream_t st);
 void launch_set_iteration(const DevState& s, int k, cudaStream_t st);
 void launch_advance_iteration(const DevState& s, cudaStream_t st);
 int score_chunks(int S, int N);
+// Learned proposal over a triangulated bootstrap state (flags: VOLDOR_LEARNED_*);
+// *kernels gets the number of kernels launched.
+voldor_status net_bootstrap(voldor_net* n, const void* flows, int f16, int W, int H, int T, float d_min, float d_max, int flags,
+                            float* theta, float* wmap, cudaStream_t st, int* kernels);
 int score_chunks_for(int S, int N, int hpt, int waves);
 int score_chunks_max(int S, int N);
 void score_hyps_from_host(const DevParams& p, const DevState& s, int n, cudaStream_t st);

@@ -65,9 +65,10 @@ class _Plane:
             t = ((self.c - o) @ self.n) / den
         t = np.where(np.abs(den) > 1e-12, t, np.inf)
         if self.bounded:
-            p = o[None, :] + t[:, None] * d
-            q = p - self.c
-            ok = (np.abs(q @ self.u) <= self.hu) & (np.abs(q @ self.v) <= self.hv)
+            # in-plane coordinates of o + t d relative to the centre, per axis
+            qu = (o - self.c) @ self.u + t * (d @ self.u)
+            qv = (o - self.c) @ self.v + t * (d @ self.v)
+            ok = (np.abs(qu) <= self.hu) & (np.abs(qv) <= self.hv)
             t = np.where(ok, t, np.inf)
         return np.where(t > 1e-6, t, np.inf)
 
@@ -90,12 +91,15 @@ class _Box:
     def hit(self, o, d, frame):
         off = self.offset(frame)
         lo, hi = self.lo + off, self.hi + off
+        tmin = tmax = None
         with np.errstate(divide="ignore", invalid="ignore"):
-            inv = 1.0 / d
-            t1 = (lo - o) * inv
-            t2 = (hi - o) * inv
-        tmin = np.nanmax(np.minimum(t1, t2), axis=1)
-        tmax = np.nanmin(np.maximum(t1, t2), axis=1)
+            for k in range(3):            # slab test per axis; fmax / fmin ignore NaN
+                inv = 1.0 / d[:, k]
+                t1 = (lo[k] - o[k]) * inv
+                t2 = (hi[k] - o[k]) * inv
+                a, b = np.minimum(t1, t2), np.maximum(t1, t2)
+                tmin = a if tmin is None else np.fmax(tmin, a)
+                tmax = b if tmax is None else np.fmin(tmax, b)
         ok = (tmax >= tmin) & (tmax > 1e-6)
         t = np.where(tmin > 1e-6, tmin, tmax)
         return np.where(ok, t, np.inf)

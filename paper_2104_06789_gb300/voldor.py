@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libvoldor.so")
 
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_BOOTSTRAPPED, ERR_DEGENERATE, ERR_TIMEOUT, ERR_INTERNAL = range(8)
 FLOW_F32, FLOW_F16 = 0, 1
+LEARNED_DEPTH, LEARNED_RIGIDNESS = 1, 2
 BOOT_GIVEN_POSE = 0
 (BUF_SMOOTHED, BUF_LABELS, BUF_HYPS, BUF_HYP_INFO, BUF_HYP_WEIGHT, BUF_SCORES, BUF_POSE_INFO,
  BUF_DEPTH_SAMPLES, BUF_HYPS_F32) = range(9)
@@ -88,6 +89,15 @@ def lib():
             "voldor_batch_run": (i, [vp, vp, P(C.c_float)]),
             "voldor_batch_destroy": (None, [vp]),
             "voldor_em_batch": (i, [P(vp), i, i]),
+            "voldor_net_num_params": (sz, [i]),
+            "voldor_net_create": (i, [i, P(vp)]),
+            "voldor_net_destroy": (None, [vp]),
+            "voldor_net_set_weights": (i, [vp, P(C.c_float), sz]),
+            "voldor_net_get_weights": (i, [vp, P(C.c_float), sz]),
+            "voldor_net_get_grads": (i, [vp, P(C.c_float), sz]),
+            "voldor_net_forward": (i, [vp, vp, i, i, i, i, vp, vp]),
+            "voldor_net_train_step": (i, [vp, vp, i, vp, i, i, i, C.c_float, C.c_float, P(C.c_float), vp]),
+            "voldor_bootstrap_learned": (i, [vp, P(d), vp, i]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -339,6 +349,78 @@ class Batch:
 def em_batch(windows, n_iters):
     arr = (C.c_void_p * len(windows))(*[w._h for w in windows])
     return _check(lib().voldor_em_batch(arr, len(windows), int(n_iters)), "voldor_em_batch", (ERR_DEGENERATE,))
+
+
+class Net:
+    """The learned proposal network (voldor_net_*). Device arrays are torch
+    CUDA tensors: flows [B][T][H][W][2] (float16 or float32), targets
+    [B][H][W][2] float32, predictions [B][H][W][8] float32."""
+
+    def __init__(self, T, weights=None):
+        self.T = int(T)
+        self.n_params = int(lib().voldor_net_num_params(self.T))
+        h = C.c_void_p()
+        _check(lib().voldor_net_create(self.T, C.byref(h)), "voldor_net_create")
+        self._h = h
+        if weights is not None:
+            self.set_weights(weights)
+
+    def set_weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        _check(lib().voldor_net_set_weights(self._h, w.ctypes.data_as(C.POINTER(C.c_float)), w.size),
+               "voldor_net_set_weights")
+
+    def get_weights(self):
+        w = np.zeros(self.n_params, np.float32)
+        _check(lib().voldor_net_get_weights(self._h, w.ctypes.data_as(C.POINTER(C.c_float)), w.size),
+               "voldor_net_get_weights")
+        return w
+
+    def get_grads(self):
+        g = np.zeros(self.n_params, np.float32)
+        _check(lib().voldor_net_get_grads(self._h, g.ctypes.data_as(C.POINTER(C.c_float)), g.size),
+               "voldor_net_get_grads")
+        return g
+
+    @staticmethod
+    def _flow_dtype(t):
+        import torch
+        return {torch.float16: FLOW_F16, torch.float32: FLOW_F32}[t.dtype]
+
+    def forward(self, flows, stream=None):
+        import torch
+        B, T, H, W = flows.shape[:4]
+        out = torch.empty((B, H, W, 8), dtype=torch.float32, device=flows.device)
+        st = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+        _check(lib().voldor_net_forward(self._h, C.c_void_p(flows.data_ptr()), self._flow_dtype(flows), B, H, W,
+                                        C.c_void_p(out.data_ptr()), C.c_void_p(st)), "voldor_net_forward")
+        return out
+
+    def train_step(self, flows, target, lr, lam_r=1.0, stream=None):
+        B, T, H, W = flows.shape[:4]
+        loss = C.c_float(0)
+        st = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+        _check(lib().voldor_net_train_step(self._h, C.c_void_p(flows.data_ptr()), self._flow_dtype(flows),
+                                           C.c_void_p(target.data_ptr()), B, H, W, float(lr), float(lam_r),
+                                           C.byref(loss), C.c_void_p(st)), "voldor_net_train_step")
+        return loss.value
+
+    def bootstrap(self, window, T1, depth=True, rigidness=True):
+        T1, p = _f64(T1)
+        flags = (LEARNED_DEPTH if depth else 0) | (LEARNED_RIGIDNESS if rigidness else 0)
+        _check(lib().voldor_bootstrap_learned(window._h, p, self._h, flags), "voldor_bootstrap_learned",
+               handle=window._h)
+
+    def destroy(self):
+        if getattr(self, "_h", None):
+            lib().voldor_net_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def init_window(flows, K, params=None, stream=None) -> Window:

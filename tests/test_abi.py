@@ -75,3 +75,18 @@ def test_product_path_does_not_reference_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "or_window" not in txt and "liboracle" not in txt, f
+
+
+def test_net_arguments_are_checked_on_the_host(vd):
+    from oracle import conv_net
+    L = vd.lib()
+    for T in (1, 2, 5, 8):
+        assert L.voldor_net_num_params(T) == conv_net.num_params(T)
+    assert L.voldor_net_num_params(0) == 0 and L.voldor_net_num_params(9) == 0
+    h = ctypes.c_void_p()
+    assert L.voldor_net_create(0, ctypes.byref(h)) == vd.ERR_INVALID_ARG
+    assert L.voldor_net_create(9, ctypes.byref(h)) == vd.ERR_INVALID_ARG
+    assert L.voldor_net_create(2, None) == vd.ERR_INVALID_ARG
+    assert L.voldor_net_forward(None, None, 0, 1, 1, 1, None, None) == vd.ERR_INVALID_ARG
+    assert L.voldor_bootstrap_learned(None, None, None, 3) == vd.ERR_INVALID_ARG
+    L.voldor_net_destroy(None)
