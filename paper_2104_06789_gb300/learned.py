@@ -28,6 +28,7 @@ from __future__ import annotations
 
 import math
 import multiprocessing as mp
+import os
 import time
 
 import numpy as np
@@ -58,7 +59,19 @@ def scenes(seeds, workers=0, **size):
         for j in jobs:
             yield _scene_args(j)
         return
-    with mp.get_context("spawn").Pool(workers) as pool:
+    # one BLAS thread per worker: the workers already fill the cores
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    os.environ.update({k: "1" for k in keys})
+    try:
+        pool = mp.get_context("spawn").Pool(workers)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    with pool:
         yield from pool.imap(_scene_args, jobs, chunksize=1)
 
 

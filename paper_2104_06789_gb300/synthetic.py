@@ -75,6 +75,12 @@ class _Plane:
     def offset(self, frame):
         return np.zeros(3)
 
+    def corners(self, frame):
+        if not self.bounded:
+            return None
+        return np.array([self.c + su * self.hu * self.u + sv * self.hv * self.v
+                         for su in (-1, 1) for sv in (-1, 1)])
+
 
 class _Box:
     """Axis-aligned box; a moving box translates by `vel` per frame."""
@@ -87,6 +93,12 @@ class _Box:
 
     def offset(self, frame):
         return self.vel * frame
+
+    def corners(self, frame):
+        off = self.offset(frame)
+        lo, hi = self.lo + off, self.hi + off
+        return np.array([[(lo, hi)[i][0], (lo, hi)[j][1], (lo, hi)[k][2]]
+                         for i in (0, 1) for j in (0, 1) for k in (0, 1)])
 
     def hit(self, o, d, frame):
         off = self.offset(frame)
@@ -129,21 +141,63 @@ def _fisk_noise(rng, n_true):
     return np.stack([epe * np.cos(ang), epe * np.sin(ang)], axis=-1)
 
 
+_RAYS = {}
+
+
+def _camera_rays(K, W, H):
+    """Ray directions (x/z, y/z, 1) of the pixel centres, cached per camera."""
+    key = (K, W, H)
+    if key not in _RAYS:
+        fx, fy, cx, cy = K
+        xs, ys = np.meshgrid(np.arange(W, dtype=float), np.arange(H, dtype=float))
+        if len(_RAYS) > 8:
+            _RAYS.clear()
+        _RAYS[key] = np.stack([(xs - cx) / fx, (ys - cy) / fy, np.ones_like(xs)], -1).reshape(-1, 3)
+    return _RAYS[key]
+
+
+def _footprint(prim, K, R, t, W, H, frame):
+    """Indices of the rays that can hit a bounded convex primitive (all rays:
+    None). A ray's hit point has camera depth > 0, so a primitive entirely at
+    depth <= 0 is hit by none; one entirely at depth > 0 projects inside the
+    bounding box of its projected corners; otherwise every ray is tested."""
+    C = prim.corners(frame)
+    if C is None:
+        return None
+    Xc = C @ R.T + t
+    z = Xc[:, 2]
+    if np.all(z <= 0):
+        return np.zeros(0, np.int64)
+    if np.any(z <= 1e-6):
+        return None
+    fx, fy, cx, cy = K
+    u = fx * Xc[:, 0] / z + cx
+    v = fy * Xc[:, 1] / z + cy
+    x0, x1 = max(int(np.floor(u.min())) - 1, 0), min(int(np.ceil(u.max())) + 1, W - 1)
+    y0, y1 = max(int(np.floor(v.min())) - 1, 0), min(int(np.ceil(v.max())) + 1, H - 1)
+    if x0 > x1 or y0 > y1:
+        return np.zeros(0, np.int64)
+    ys, xs = np.arange(y0, y1 + 1), np.arange(x0, x1 + 1)
+    return (ys[:, None] * W + xs[None, :]).ravel()
+
+
 def _render(prims, K, M, W, H, frame):
     """Cast the rays of a camera with world->camera transform M."""
-    fx, fy, cx, cy = K
-    xs, ys = np.meshgrid(np.arange(W, dtype=float), np.arange(H, dtype=float))
-    dc = np.stack([(xs - cx) / fx, (ys - cy) / fy, np.ones_like(xs)], -1).reshape(-1, 3)
+    dc = _camera_rays(tuple(K), W, H)
     R, t = M[:3, :3], M[:3, 3]
     o = -R.T @ t
     d = dc @ R                       # rows: R^T dc
     best = np.full(dc.shape[0], np.inf)
     oid = np.full(dc.shape[0], -1)
     for i, p in enumerate(prims):
-        ti = p.hit(o, d, frame)
-        better = ti < best
-        best = np.where(better, ti, best)
-        oid = np.where(better, i, oid)
+        idx = _footprint(p, K, R, t, W, H, frame)
+        if idx is not None and idx.size == 0:
+            continue
+        sub = slice(None) if idx is None else idx
+        ti = p.hit(o, d[sub], frame)
+        better = ti < best[sub]
+        best[sub] = np.where(better, ti, best[sub])
+        oid[sub] = np.where(better, i, oid[sub])
     X = o[None, :] + best[:, None] * d
     return X, best.reshape(H, W), oid
 
