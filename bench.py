@@ -70,6 +70,22 @@ def workload(rank):
     return synthetic.driving(seed=3000 + rank)
 
 
+def max_over_ranks(x, dist, device):
+    """The maximum of a per-rank float over all ranks (x itself on one rank)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, max_seconds):
+    """Units of all ranks over the slowest rank's time, in millions per second
+    (replicas: every rank processes the same number of units)."""
+    return world * units_per_rank / max_seconds / 1e6
+
+
 def config_dict(w, args, world):
     return {"workload": w.name, "width": w.W, "height": w.H, "T": w.T, "em_iters": args.iters,
             "hyps_per_frame": args.hyps, "groups_per_frame": 2 * args.hyps, "flows": "fp16",
@@ -255,15 +271,12 @@ def run_ours(args):
             score_pairs.extend(pairs.tolist())
         torch.cuda.synchronize()
     launches = win.kernel_launches() - launches0
-    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), dist, f"cuda:{local_rank}")
     if dist is not None:
-        tt = torch.tensor([total_ms], device=f"cuda:{local_rank}", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
         dist.barrier()
     torch.cuda.synchronize()
     units_per_step = w.H * w.W * w.T * args.iters
-    value = world * units_per_step * args.steps / (total_ms / 1e3) / 1e6
+    value = whole_job_rate(world, units_per_step * args.steps, total_ms / 1e3)
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -279,14 +292,9 @@ def run_ours(args):
             host_win.bootstrap(T1)
             host_win.em_step(args.iters)
             P, D, Wm = host_win.get_pose_depth_rigidness()
-        e2e_s = time.perf_counter() - t0
-        e2e_s_max = e2e_s
-        if dist is not None:
-            tt = torch.tensor([e2e_s], device=f"cuda:{local_rank}", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s_max = float(tt.item())
+        e2e_s_max = max_over_ranks(time.perf_counter() - t0, dist, f"cuda:{local_rank}")
         host_win.destroy()
-        e2e = {"value": world * units_per_step * args.steps / e2e_s_max / 1e6, "unit": UNIT,
+        e2e = {"value": whole_job_rate(world, units_per_step * args.steps, e2e_s_max), "unit": UNIT,
                "h2d_bytes_per_step": int(flows16.nbytes),
                "d2h_bytes_per_step": int(w.T * 16 * 8 + w.H * w.W * 4 + w.T * w.H * w.W * 4)}
 
