@@ -7,7 +7,9 @@ image-space non-rigid patches) and projects them into camera t, which gives
 the flow X_t on the grid of I_{t-1} (Sec. 3 of the paper). Residual noise is
 drawn from the Fisk model of Sec. 4: a squared end-point error with
 alpha = a1 exp(a2 n), beta = b1 n + b2 at the true flow magnitude n (capped at
-40 px for drawing), in a uniformly random direction.
+40 px for drawing), in a uniformly random direction; the drawn end-point error
+is capped at 1e4 px (the Fisk tail is unbounded, and a flow must stay finite in
+FP16).
 
 This module is an input generator only: it feeds the oracle and the CUDA path
 alike and implements none of the inference.
@@ -20,6 +22,7 @@ import numpy as np
 
 FISK_A1, FISK_A2, FISK_B1, FISK_B2 = 0.01, 0.09, -0.0022, 1.0
 NOISE_N_CAP = 40.0
+EPE_CAP = 1.0e4
 
 
 @dataclass
@@ -136,7 +139,7 @@ def _fisk_noise(rng, n_true):
     beta = np.maximum(FISK_B1 * n + FISK_B2, 0.05)
     u = rng.uniform(1e-12, 1 - 1e-12, size=n.shape)
     xsq = alpha * (u / (1 - u)) ** (1.0 / beta)
-    epe = np.sqrt(xsq)
+    epe = np.minimum(np.sqrt(xsq), EPE_CAP)
     ang = rng.uniform(0, 2 * np.pi, size=n.shape)
     return np.stack([epe * np.cos(ang), epe * np.sin(ang)], axis=-1)
 
