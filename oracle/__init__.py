@@ -90,6 +90,15 @@ def lib():
             "or_rigidness": (None, [W]),
             "or_em_iteration": (i, [W, i]),
             "or_run": (i, [W, i, i]),
+            "or_essential_8pt": (i, [P(d), P(d), P(d)]),
+            "or_essential_project": (i, [P(d), P(d), P(d), P(d)]),
+            "or_sampson": (d, [P(d), P(d), P(d)]),
+            "or_essential_candidates": (None, [P(d), P(d), P(d), P(d)]),
+            "or_epi_sample": (i, [W, i, P(d), P(C.c_int64)]),
+            "or_epi_score": (d, [W, P(d)]),
+            "or_epi_cheirality": (C.c_int64, [W, P(d), P(d)]),
+            "or_epipolar_bootstrap": (i, [W, i, d, P(d), P(d), P(i), P(i)]),
+            "or_epi_refine": (C.c_int64, [W, P(d), d, P(d), P(d)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -146,6 +155,37 @@ class OracleWindow:
     def bootstrap(self, T1):
         T1 = np.ascontiguousarray(T1, dtype=np.float64)
         lib().or_bootstrap(self.ref, _dp(T1))
+
+    def epipolar_bootstrap(self, n_samples, baseline=1.0):
+        """(status, T1, per-sample scores, chosen sample, chosen candidate)."""
+        T1 = np.zeros(16)
+        scores = np.zeros(n_samples)
+        m, c = C.c_int(-1), C.c_int(-1)
+        st = lib().or_epipolar_bootstrap(self.ref, n_samples, float(baseline), _dp(T1), _dp(scores),
+                                         C.byref(m), C.byref(c))
+        return st, T1.reshape(4, 4), scores, m.value, c.value
+
+    def epi_sample(self, m):
+        E = np.zeros(9)
+        j = np.zeros(8, dtype=np.int64)
+        ok = lib().or_epi_sample(self.ref, m, _dp(E), ptr(j, C.c_int64))
+        return ok, E.reshape(3, 3), j
+
+    def epi_score(self, E):
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        return lib().or_epi_score(self.ref, _dp(E))
+
+    def epi_refine(self, E, median):
+        """(inlier count, refined E, inlier threshold)."""
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        out, thr = np.zeros(9), C.c_double(0.0)
+        n = lib().or_epi_refine(self.ref, _dp(E), float(median), _dp(out), C.byref(thr))
+        return n, out.reshape(3, 3), thr.value
+
+    def epi_cheirality(self, R, t):
+        R = np.ascontiguousarray(R, dtype=np.float64)
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        return lib().or_epi_cheirality(self.ref, _dp(R), _dp(t))
 
     def frame_eval(self, t, j, depth):
         out = np.zeros(12)
@@ -207,6 +247,34 @@ class OracleWindow:
 
     def run(self, k0, n):
         return lib().or_run(self.ref, k0, n)
+
+
+def essential_8pt(m0, m1):
+    m0 = np.ascontiguousarray(m0, dtype=np.float64)
+    m1 = np.ascontiguousarray(m1, dtype=np.float64)
+    E = np.zeros(9)
+    ok = lib().or_essential_8pt(_dp(m0), _dp(m1), _dp(E))
+    return ok, E.reshape(3, 3)
+
+
+def essential_project(E):
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    out, U, V = np.zeros(9), np.zeros(9), np.zeros(9)
+    ok = lib().or_essential_project(_dp(E), _dp(out), _dp(U), _dp(V))
+    return ok, out.reshape(3, 3), U.reshape(3, 3), V.reshape(3, 3)
+
+
+def sampson(E, m0, m1):
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    return lib().or_sampson(_dp(E), _dp(np.ascontiguousarray(m0, dtype=np.float64)),
+                            _dp(np.ascontiguousarray(m1, dtype=np.float64)))
+
+
+def essential_candidates(U, V):
+    R, t = np.zeros(36), np.zeros(12)
+    lib().or_essential_candidates(_dp(np.ascontiguousarray(U, dtype=np.float64)),
+                                  _dp(np.ascontiguousarray(V, dtype=np.float64)), _dp(R), _dp(t))
+    return R.reshape(4, 3, 3), t.reshape(4, 3)
 
 
 def philox4x64_10(ctr, key):

@@ -59,7 +59,7 @@ typedef struct {
 } or_window;
 
 enum { OR_OK = 0, OR_DEGENERATE = 5 };
-enum { STREAM_POSE = 1, STREAM_DEPTH = 2 };
+enum { STREAM_POSE = 1, STREAM_DEPTH = 2, STREAM_EPI = 3 };
 
 // ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
@@ -1043,6 +1043,335 @@ int or_run(or_window* w, int k0, int n_iters)
         if (s != OR_OK) status = s;
     }
     return status;
+}
+
+
+// ---------------------------------------------------------------------------
+// Epipolar bootstrap of T_1 (Sec. 5.3 and Table 1: T_1 from the epipolar
+// geometry of X_1 by least median of squares, Rousseeuw 1984). Readings:
+//  - correspondences m0 = K^-1 [x, y, 1], m1 = K^-1 [x + u, y + v, 1] of every
+//    pixel whose flow target lies inside I_1 (0 <= x + u <= W - 1, same for y);
+//  - sample m takes 8 pixels j_i = hi64(r_i * N), r_0..3 from the Philox counter
+//    (m, 0, 0, EPI) and r_4..7 from (m, 1, 0, EPI); a sample with a repeated or
+//    invalid pixel, or whose 8 x 9 system has no one-dimensional null space,
+//    scores +inf;
+//  - E spans the null space of the 8 x 9 matrix with rows m1 (x) m0 (so that
+//    m1^T E m0 = 0; the eigenvector of A^T A of the smallest eigenvalue), then
+//    projected onto the essential matrices, E = U diag(1, 1, 0) V^T;
+//  - the error of pixel j is Sampson's first-order distance
+//    (m1^T E m0)^2 / ((E m0)_1^2 + (E m0)_2^2 + (E^T m1)_1^2 + (E^T m1)_2^2)
+//    in calibrated coordinates;
+//  - a sample's score is the lower median (rank floor((n - 1) / 2) in ascending
+//    order) of the errors of the n valid pixels; the smallest score wins, the
+//    lowest sample index on ties;
+//  - reweighted least squares after the LMedS fit (Rousseeuw and Leroy 1987):
+//    robust scale s = 1.4826 (1 + 5 / (n - 8)) sqrt(median); the pixels whose
+//    error under the winning sample is at most (2.5 s)^2 are inliers, and E is
+//    re-estimated as the null vector (smallest right singular vector) of the
+//    matrix of their rows m1 (x) m0, then projected again (if there are fewer
+//    than 8 inliers the sample's E is kept);
+//  - (R, t) is the candidate among (U W V^T, +u3), (U W V^T, -u3),
+//    (U W^T V^T, +u3), (U W^T V^T, -u3) (det U = det V = +1,
+//    W = [[0,-1,0],[1,0,0],[0,0,1]]) with the most valid pixels whose depth,
+//    triangulated as in the bootstrap, is positive in both cameras (the first
+//    in that order on ties); |t| is set to the caller's baseline (the scale of
+//    a monocular window is free).
+// ---------------------------------------------------------------------------
+
+// One-sided Jacobi SVD (Hestenes 1958; Golub and Van Loan, Sec. 8.6.4) of an
+// m x n matrix A (row-major, overwritten): rotations of column pairs until all
+// columns are orthogonal; then A = (A V) V^T with the columns of A V
+// orthogonal, their norms the singular values sv[n], V (n x n, row-major) the
+// right singular vectors as columns. Works on A itself, so the accuracy of the
+// small singular vectors is not squared away as in A^T A.
+static void jacobi_svd(double* A, int m, int n, double* sv, double* V)
+{
+    for (int i = 0; i < n * n; ++i) V[i] = 0.0;
+    for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        bool rotated = false;
+        for (int p = 0; p < n - 1; ++p) {
+            for (int q = p + 1; q < n; ++q) {
+                double alpha = 0.0, beta = 0.0, gamma = 0.0;
+                for (int k = 0; k < m; ++k) {
+                    alpha += A[k * n + p] * A[k * n + p];
+                    beta += A[k * n + q] * A[k * n + q];
+                    gamma += A[k * n + p] * A[k * n + q];
+                }
+                if (!(std::fabs(gamma) > 1e-17 * std::sqrt(alpha * beta))) continue;
+                rotated = true;
+                const double zeta = (beta - alpha) / (2.0 * gamma);
+                const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / std::sqrt(1.0 + t * t), s = c * t;
+                for (int k = 0; k < m; ++k) {
+                    const double ap = A[k * n + p], aq = A[k * n + q];
+                    A[k * n + p] = c * ap - s * aq;
+                    A[k * n + q] = s * ap + c * aq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double vp = V[k * n + p], vq = V[k * n + q];
+                    V[k * n + p] = c * vp - s * vq;
+                    V[k * n + q] = s * vp + c * vq;
+                }
+            }
+        }
+        if (!rotated) break;
+    }
+    for (int j = 0; j < n; ++j) {
+        double s = 0.0;
+        for (int k = 0; k < m; ++k) s += A[k * n + j] * A[k * n + j];
+        sv[j] = std::sqrt(s);
+    }
+}
+
+// The 8-point estimate: E (row-major) spans the null space of the 8 x 9 matrix
+// with rows m1 (x) m0. Returns 0 if the null space is not one-dimensional.
+int or_essential_8pt(const double* m0, const double* m1, double E[9])
+{
+    // A padded with a zero row to 9 x 9 (the null space is unchanged)
+    double A[9 * 9] = {0};
+    for (int i = 0; i < 8; ++i)
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) A[i * 9 + r * 3 + c] = m1[i * 3 + r] * m0[i * 3 + c];
+    double sv[9], V[81];
+    jacobi_svd(A, 9, 9, sv, V);
+    int order[9];
+    for (int i = 0; i < 9; ++i) order[i] = i;
+    std::sort(order, order + 9, [&](int a, int b) { return sv[a] < sv[b]; });
+    const double smax = sv[order[8]];
+    if (!(smax > 0.0) || !(sv[order[1]] > 1e-10 * smax)) return 0;
+    for (int k = 0; k < 9; ++k) E[k] = V[k * 9 + order[0]];
+    return 1;
+}
+
+// SVD of a 3 x 3 matrix: M = U diag(s) V^T with s descending and
+// det U = det V = +1 (the third singular pair is fixed by the cross products,
+// which the essential projection does not use). Returns 0 if rank(M) < 2.
+static int svd3_rank2(const double M[9], double U[9], double s[3], double V[9])
+{
+    double A[9], sv[3], Q[9];
+    std::memcpy(A, M, sizeof(A));
+    jacobi_svd(A, 3, 3, sv, Q);
+    int o[3] = {0, 1, 2};
+    std::sort(o, o + 3, [&](int a, int b) { return sv[a] > sv[b]; });
+    double v[3][3], u[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k) v[i][k] = Q[k * 3 + o[i]];
+    cross3(v[0], v[1], v[2]);                     // right-handed V
+    for (int i = 0; i < 2; ++i) {
+        s[i] = sv[o[i]];
+        if (!(s[i] > 0.0)) return 0;
+        for (int r = 0; r < 3; ++r) u[i][r] = A[r * 3 + o[i]] / s[i];   // columns of M V
+    }
+    s[2] = sv[o[2]];
+    cross3(u[0], u[1], u[2]);
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) { U[r * 3 + c] = u[c][r]; V[r * 3 + c] = v[c][r]; }
+    return 1;
+}
+
+// Closest essential matrix: U diag(1, 1, 0) V^T. Returns 0 if rank(E) < 2.
+int or_essential_project(const double Ein[9], double E[9], double U[9], double V[9])
+{
+    double s[3];
+    if (!svd3_rank2(Ein, U, s, V)) return 0;
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) E[r * 3 + c] = U[r * 3 + 0] * V[c * 3 + 0] + U[r * 3 + 1] * V[c * 3 + 1];
+    return 1;
+}
+
+double or_sampson(const double E[9], const double m0[3], const double m1[3])
+{
+    double Em0[3], Etm1[3];
+    for (int r = 0; r < 3; ++r) Em0[r] = E[r * 3 + 0] * m0[0] + E[r * 3 + 1] * m0[1] + E[r * 3 + 2] * m0[2];
+    for (int c = 0; c < 3; ++c) Etm1[c] = E[0 * 3 + c] * m1[0] + E[1 * 3 + c] * m1[1] + E[2 * 3 + c] * m1[2];
+    const double e = m1[0] * Em0[0] + m1[1] * Em0[1] + m1[2] * Em0[2];
+    const double den = Em0[0] * Em0[0] + Em0[1] * Em0[1] + Etm1[0] * Etm1[0] + Etm1[1] * Etm1[1];
+    if (!(den > 0.0)) return INFINITY;
+    return e * e / den;
+}
+
+// The four (R, t) of an essential matrix with SVD factors U, V (det +1), in the
+// candidate order of the readings; R row-major [4][9], t [4][3] (unit).
+void or_essential_candidates(const double U[9], const double V[9], double* R, double* t)
+{
+    const double Wm[9] = {0, -1, 0, 1, 0, 0, 0, 0, 1};
+    for (int a = 0; a < 2; ++a) {
+        double UW[9];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                double s = 0.0;
+                for (int k = 0; k < 3; ++k) s += U[r * 3 + k] * (a == 0 ? Wm[k * 3 + c] : Wm[c * 3 + k]);
+                UW[r * 3 + c] = s;
+            }
+        double Ra[9];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c)
+                Ra[r * 3 + c] = UW[r * 3 + 0] * V[c * 3 + 0] + UW[r * 3 + 1] * V[c * 3 + 1] + UW[r * 3 + 2] * V[c * 3 + 2];
+        for (int sgn = 0; sgn < 2; ++sgn) {
+            const int i = 2 * a + sgn;
+            std::memcpy(R + 9 * i, Ra, sizeof(Ra));
+            for (int r = 0; r < 3; ++r) t[3 * i + r] = (sgn == 0 ? 1.0 : -1.0) * U[r * 3 + 2];
+        }
+    }
+}
+
+// Correspondence of pixel j: false if the flow target leaves I_1.
+static bool epi_corr(const or_window* w, size_t j, double m0[3], double m1[3])
+{
+    const int x = (int)(j % w->width), y = (int)(j / w->width);
+    const double* f = w->flows + j * 2;
+    const double u = x + f[0], v = y + f[1];
+    if (!(u >= 0.0 && u <= w->width - 1 && v >= 0.0 && v <= w->height - 1)) return false;
+    m0[0] = (x - w->cx) / w->fx; m0[1] = (y - w->cy) / w->fy; m0[2] = 1.0;
+    m1[0] = (u - w->cx) / w->fx; m1[1] = (v - w->cy) / w->fy; m1[2] = 1.0;
+    return true;
+}
+
+// Essential matrix of sample m (0 if the sample is invalid).
+int or_epi_sample(const or_window* w, int m, double E[9], int64_t j_out[8])
+{
+    const uint64_t N = (uint64_t)w->width * w->height;
+    uint64_t r[8];
+    draw(w, (uint64_t)m, 0, 0, STREAM_EPI, r);
+    draw(w, (uint64_t)m, 1, 0, STREAM_EPI, r + 4);
+    int64_t j[8];
+    for (int i = 0; i < 8; ++i) j[i] = (int64_t)scale_index(r[i], N);
+    if (j_out) std::memcpy(j_out, j, sizeof(j));
+    for (int a = 0; a < 8; ++a)
+        for (int b = a + 1; b < 8; ++b)
+            if (j[a] == j[b]) return 0;
+    double m0[24], m1[24];
+    for (int i = 0; i < 8; ++i)
+        if (!epi_corr(w, (size_t)j[i], m0 + 3 * i, m1 + 3 * i)) return 0;
+    double E8[9], U[9], V[9];
+    if (!or_essential_8pt(m0, m1, E8)) return 0;
+    return or_essential_project(E8, E, U, V);
+}
+
+// Lower median of the Sampson errors of every valid pixel under E.
+double or_epi_score(const or_window* w, const double E[9])
+{
+    std::vector<double> d;
+    const size_t N = (size_t)w->width * w->height;
+    for (size_t j = 0; j < N; ++j) {
+        double m0[3], m1[3];
+        if (!epi_corr(w, j, m0, m1)) continue;
+        d.push_back(or_sampson(E, m0, m1));
+    }
+    if (d.empty()) return INFINITY;
+    const size_t k = (d.size() - 1) / 2;
+    std::nth_element(d.begin(), d.begin() + k, d.end());
+    return d[k];
+}
+
+// Valid pixels in front of both cameras under (R, t).
+int64_t or_epi_cheirality(const or_window* w, const double R[9], const double t[3])
+{
+    int64_t count = 0;
+    const size_t N = (size_t)w->width * w->height;
+    for (size_t j = 0; j < N; ++j) {
+        double m0[3], m1[3];
+        if (!epi_corr(w, j, m0, m1)) continue;
+        double Rd[3];
+        for (int r = 0; r < 3; ++r) Rd[r] = R[r * 3 + 0] * m0[0] + R[r * 3 + 1] * m0[1] + R[r * 3 + 2] * m0[2];
+        // the bootstrap's least-squares depth: z0 = (a.b)/(a.a)
+        const double ax = Rd[0] - m1[0] * Rd[2], bx = m1[0] * t[2] - t[0];
+        const double ay = Rd[1] - m1[1] * Rd[2], by = m1[1] * t[2] - t[1];
+        const double aa = ax * ax + ay * ay, ab = ax * bx + ay * by;
+        if (!(aa > 0.0) || !(ab > 0.0)) continue;
+        const double z0 = ab / aa;
+        const double z1 = z0 * Rd[2] + t[2];
+        if (z1 > 0.0) ++count;
+    }
+    return count;
+}
+
+// Number of valid pixels (targets inside I_1).
+static int64_t epi_valid_count(const or_window* w)
+{
+    int64_t n = 0;
+    const size_t N = (size_t)w->width * w->height;
+    for (size_t j = 0; j < N; ++j) {
+        double m0[3], m1[3];
+        n += epi_corr(w, j, m0, m1) ? 1 : 0;
+    }
+    return n;
+}
+
+// Reweighted least squares after LMedS: E_out from the inliers of E at the
+// given median; returns the inlier count (E_out = E if it is below 8).
+int64_t or_epi_refine(const or_window* w, const double E[9], double median, double E_out[9], double* thresh_out)
+{
+    const int64_t n = epi_valid_count(w);
+    std::memcpy(E_out, E, 9 * sizeof(double));
+    if (n <= 8) return 0;
+    const double s = 1.4826 * (1.0 + 5.0 / (double)(n - 8)) * std::sqrt(median);
+    const double thr = (2.5 * s) * (2.5 * s);
+    if (thresh_out) *thresh_out = thr;
+    std::vector<double> A;
+    const size_t N = (size_t)w->width * w->height;
+    for (size_t j = 0; j < N; ++j) {
+        double m0[3], m1[3];
+        if (!epi_corr(w, j, m0, m1) || !(or_sampson(E, m0, m1) <= thr)) continue;
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) A.push_back(m1[r] * m0[c]);
+    }
+    const int64_t n_in = (int64_t)(A.size() / 9);
+    if (n_in < 8) return n_in;
+    double sv[9], V[81];
+    jacobi_svd(A.data(), (int)n_in, 9, sv, V);
+    int k0 = 0;
+    for (int k = 1; k < 9; ++k)
+        if (sv[k] < sv[k0]) k0 = k;
+    double En[9], U[9], Vv[9];
+    for (int k = 0; k < 9; ++k) En[k] = V[k * 9 + k0];
+    if (or_essential_project(En, E_out, U, Vv)) return n_in;
+    std::memcpy(E_out, E, 9 * sizeof(double));
+    return n_in;
+}
+
+// The whole epipolar bootstrap: T_1 (row-major 4 x 4) into T1_out and the
+// window state as or_bootstrap leaves it. scores[n_samples] (may be null) gets
+// every sample's score. Returns OR_DEGENERATE (state untouched) if no sample is
+// valid.
+int or_epipolar_bootstrap(or_window* w, int n_samples, double baseline, double T1_out[16], double* scores,
+                          int* chosen_out, int* candidate_out)
+{
+    int best = -1;
+    double best_score = INFINITY, bestE[9] = {0};
+    for (int m = 0; m < n_samples; ++m) {
+        double E[9];
+        double s = INFINITY;
+        if (or_epi_sample(w, m, E, nullptr)) s = or_epi_score(w, E);
+        if (scores) scores[m] = s;
+        if (s < best_score) { best_score = s; best = m; std::memcpy(bestE, E, sizeof(E)); }
+    }
+    if (chosen_out) *chosen_out = best;
+    if (best < 0) return OR_DEGENERATE;
+    double Eref[9];
+    std::memcpy(Eref, bestE, sizeof(Eref));
+    or_epi_refine(w, bestE, best_score, Eref, nullptr);
+    double U[9], V[9], E2[9];
+    or_essential_project(Eref, E2, U, V);
+    double R[36], t[12];
+    or_essential_candidates(U, V, R, t);
+    int cand = 0;
+    int64_t cmax = -1;
+    for (int i = 0; i < 4; ++i) {
+        const int64_t c = or_epi_cheirality(w, R + 9 * i, t + 3 * i);
+        if (c > cmax) { cmax = c; cand = i; }
+    }
+    if (candidate_out) *candidate_out = cand;
+    double T1[16] = {0};
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) T1[r * 4 + c] = R[9 * cand + r * 3 + c];
+        T1[r * 4 + 3] = baseline * t[3 * cand + r];
+    }
+    T1[15] = 1.0;
+    std::memcpy(T1_out, T1, sizeof(T1));
+    or_bootstrap(w, T1);
+    return OR_OK;
 }
 
 }  // extern "C"
