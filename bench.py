@@ -57,6 +57,7 @@ def parse_args():
     ap.add_argument("--train-steps", type=int, default=20000)
     ap.add_argument("--workers", type=int, default=0, help="scene-generator processes (0: cpu count - 1)")
     ap.add_argument("--save-weights", default="")
+    ap.add_argument("--weights", default="", help="with --learned: evaluate these weights instead of training")
     return ap.parse_args()
 
 
@@ -449,28 +450,40 @@ def run_learned(args):
     t0 = time.time()
     train_seeds = [learned.TRAIN_SEED0 + i for i in range(args.learned)]
     held_seeds = [learned.HELDOUT_SEED0 + i for i in range(args.heldout)]
-    ds = learned.build_dataset(train_seeds, S=S, label_iters=8, workers=workers, log=log)
-    t_data = time.time() - t0
-    log(f"training set: {ds.n} windows in {t_data:.0f} s")
+    T = learned.SCENE["T"]
+    t_data = t_train = 0.0
+    losses = np.zeros(1)
+    pix_per_step = 2 * learned.SCENE["W"] * learned.SCENE["H"]
+    if args.weights:
+        net = voldor.Net(T, np.load(args.weights))
+        log(f"weights from {args.weights}: no training")
+    else:
+        ds = learned.build_dataset(train_seeds, S=S, label_iters=8, workers=workers, log=log)
+        t_data = time.time() - t0
+        log(f"training set: {ds.n} windows in {t_data:.0f} s")
+        net = voldor.Net(T, learned.init_weights(T, seed=0))
+        t1 = time.time()
+        losses = learned.train(net, ds, args.train_steps, batch=2, lr=1e-3, log=log)
+        torch.cuda.synchronize()
+        t_train = time.time() - t1
+        if args.save_weights:
+            np.save(args.save_weights, net.get_weights())
+        del ds
     held = learned.build_dataset(held_seeds, S=S, label_iters=0, workers=workers, log=log)
-    T = ds.flows.shape[1]
-    net = voldor.Net(T, learned.init_weights(T, seed=0))
-    t1 = time.time()
-    losses = learned.train(net, ds, args.train_steps, batch=2, lr=1e-3, log=log)
-    torch.cuda.synchronize()
-    t_train = time.time() - t1
-    pix_per_step = 2 * ds.flows.shape[2] * ds.flows.shape[3]
-    if args.save_weights:
-        np.save(args.save_weights, net.get_weights())
-    del ds
     res = learned.compare(net, held, S=S, max_iters=8, plain_iters=args.iters)
-    line = {"metric": "EM iterations and wall time to the plain EM's pose error, learned vs triangulation init",
-            "value": res["learned_ms"], "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+    # value: the faster learned initialisation's time to the plain EM's median error after
+    # args.iters iterations (null if neither reaches it within 8 iterations)
+    cands = [(res[f"{m}_median_ms"], m) for m in ("learned", "learned_w") if res[f"{m}_median_ms"] is not None]
+    best = min(cands) if cands else (None, None)
+    line = {"metric": "wall time to the plain EM's median pose error (bootstrap + EM iterations), learned init",
+            "value": best[0], "value_variant": best[1], "plain_ms_same_metric": res["plain_ms"],
+            "unit": "ms", "higher_is_better": False, "n_gpus": 1,
             "data": "synthetic", "dtype": "bf16 net, f32/f64 EM",
             "config": {"workload": "handheld scenes at 1242x375 f=718 T=8", "train_windows": len(train_seeds),
                        "heldout_windows": len(held_seeds), "hyps_per_frame": S, "train_steps": args.train_steps,
                        "batch": 2, "label_iters": 8},
-            "train_s": t_train, "train_mpix_per_s": pix_per_step * args.train_steps / t_train / 1e6,
+            "train_s": t_train,
+            "train_mpix_per_s": pix_per_step * args.train_steps / t_train / 1e6 if t_train else None,
             "loss_first_last": [float(losses[:50].mean()), float(losses[-50:].mean())],
             "data_s": t_data, **res}
     print(json.dumps(line), flush=True)

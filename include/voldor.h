@@ -104,6 +104,23 @@ voldor_status voldor_set_flows(voldor_ctx* ctx, const void* flows, int flows_on_
  * Resets the iteration counter k to 0. T1_rowmajor_4x4: host, 16 doubles. */
 voldor_status voldor_bootstrap(voldor_ctx* ctx, int mode, const double* T1_rowmajor_4x4);
 
+/* Epipolar bootstrap (Sec. 5.3 and Table 1, second line: T_1 from the
+ * epipolar geometry of X_1 by least median of squares), then the bootstrap of
+ * voldor_bootstrap with that T_1. Correspondences: every pixel of I_0 whose
+ * flow target lies inside I_1, in calibrated coordinates. n_samples minimal
+ * samples of 8 pixels (Philox counters (m, 0, 0, 3) and (m, 1, 0, 3) under the
+ * window key) give 8-point essential matrices, each scored by the lower median
+ * of its Sampson errors over all valid pixels; the best is refined by least
+ * squares over its inliers (error <= (2.5 s)^2, s = 1.4826 (1 + 5/(n - 8))
+ * sqrt(median)); (R, t) is the decomposition with the most pixels in front of
+ * both cameras, and |t| = baseline (a monocular window's scale is free).
+ * T1_out (host, 16 doubles, may be NULL) receives T_1. Synchronises the
+ * context's stream. VOLDOR_ERR_DEGENERATE if no sample is valid (the state is
+ * then unchanged). n_samples in [1, VOLDOR_EPI_MAX_SAMPLES]; scratch of about
+ * 25 KB per sample is allocated on first use and kept by the context. */
+#define VOLDOR_EPI_MAX_SAMPLES 4096
+voldor_status voldor_bootstrap_epipolar(voldor_ctx* ctx, int n_samples, double baseline, double* T1_out);
+
 /* Runs n_iters iterations of the VOLDOR loop (Table 1): for t = 1..T the pose
  * update of Eq. 19 (Philox-drawn minimal groups, P3P, dense scoring of every
  * hypothesis against every pixel, weighted meanshift on se(3)); the E-step
@@ -175,7 +192,15 @@ enum {
     VOLDOR_BUF_SCORES = 5,    /* double [S] dense scores L_h */
     VOLDOR_BUF_POSE_INFO = 6, /* int32 [4] n_hyp, seed index, meanshift steps, status */
     VOLDOR_BUF_DEPTH_SAMPLES = 7, /* float [H][W] last sweep's smp candidates */
-    VOLDOR_BUF_HYPS_F32 = 8   /* float [S][12] scoring form of the hypotheses */
+    VOLDOR_BUF_HYPS_F32 = 8,  /* float [S][12] scoring form of the hypotheses */
+    /* after voldor_bootstrap_epipolar with M samples: */
+    VOLDOR_BUF_EPI_E = 9,       /* double [M][9] each sample's essential matrix (row-major; 0 if invalid) */
+    VOLDOR_BUF_EPI_MEDIANS = 10,/* float [M] each sample's median Sampson error (+inf if invalid) */
+    VOLDOR_BUF_EPI_VALID = 11,  /* int32 [M] 1 valid; rejected: -1 repeated pixel, -2 a flow target outside
+                                   I_1, -3 the 8 x 9 system has rank < 8, -4 its null vector has rank < 2 */
+    VOLDOR_BUF_EPI_INFO = 12,   /* int64 [8] chosen sample, chosen candidate, valid pixels, inliers,
+                                   candidates' cheirality counts [4] */
+    VOLDOR_BUF_EPI_REFINED = 13 /* double [27] refined E, then its U and V (row-major) */
 };
 voldor_status voldor_get_buffer(voldor_ctx* ctx, int which, void* host, size_t bytes);
 voldor_status voldor_set_buffer(voldor_ctx* ctx, int which, const void* host, size_t bytes);

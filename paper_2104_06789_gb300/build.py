@@ -26,6 +26,7 @@ UNITS = {
     "k_score.cu": [],
     "voldor_api.cu": [],
     "k_net.cu": [],
+    "k_epi.cu": [],
 }
 
 

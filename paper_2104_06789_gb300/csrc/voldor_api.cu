@@ -37,6 +37,9 @@ struct voldor_ctx {
     cudaError_t first_error = cudaSuccess;           // the error that poisoned the context
     cudaStream_t aux = nullptr;                      // second stream: P3P beside the pose preparation
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    void* epi_base = nullptr;                        // epipolar bootstrap scratch
+    int epi_cap = 0;                                 // samples it holds
+    int epi_M = 0;                                   // samples of the last epipolar bootstrap
 };
 
 namespace {
@@ -422,6 +425,47 @@ voldor_status voldor_bootstrap(voldor_ctx* c, int mode, const double* T1)
     return VOLDOR_OK;
 }
 
+voldor_status voldor_bootstrap_epipolar(voldor_ctx* c, int n_samples, double baseline, double* T1_out)
+{
+    if (!c || n_samples < 1 || n_samples > VOLDOR_EPI_MAX_SAMPLES || !finite_pos(baseline)) return VOLDOR_ERR_INVALID_ARG;
+    if (c->poisoned) return kCuda;
+    if (n_samples > c->epi_cap) {
+        if (c->epi_base && !cuda_ok(c, cudaFree(c->epi_base))) return kCuda;
+        c->epi_base = nullptr;
+        c->epi_cap = 0;
+        if (cudaMalloc(&c->epi_base, epi_scratch_bytes(n_samples)) != cudaSuccess) {
+            cudaGetLastError();
+            c->epi_base = nullptr;
+            return VOLDOR_ERR_OOM;
+        }
+        c->epi_cap = n_samples;
+    }
+    EpiState e;
+    epi_layout(c->epi_base, n_samples, reinterpret_cast<float4*>(c->ds.pix), &e);
+    c->launches += launch_epipolar(c->dp, c->ds, e, baseline, c->stream);
+    if (!launched(c)) return kCuda;
+    c->epi_M = n_samples;
+    double T1d[12];
+    long long info[8];
+    if (!cuda_ok(c, cudaMemcpyAsync(T1d, e.T1, sizeof(T1d), cudaMemcpyDeviceToHost, c->stream)) ||
+        !cuda_ok(c, cudaMemcpyAsync(info, e.info, sizeof(info), cudaMemcpyDeviceToHost, c->stream)) ||
+        !cuda_ok(c, cudaStreamSynchronize(c->stream)))
+        return kCuda;
+    if (info[0] < 0) return VOLDOR_ERR_DEGENERATE;
+    double T1[16] = {0};
+    for (int q = 0; q < 12; ++q) T1[q] = T1d[q];
+    T1[15] = 1.0;
+    for (int q = 0; q < 12; ++q)
+        if (!std::isfinite(T1[q])) return VOLDOR_ERR_DEGENERATE;
+    launch_bootstrap(c->dp, c->ds, T1, c->stream);
+    c->launches += 1;
+    if (!cuda_ok(c, cudaMemsetAsync(c->ds.status, 0, 16, c->stream))) return kCuda;
+    if (!launched(c)) return kCuda;
+    c->bootstrapped = true;
+    if (T1_out) std::memcpy(T1_out, T1, sizeof(T1));
+    return VOLDOR_OK;
+}
+
 voldor_status voldor_bootstrap_learned(voldor_ctx* c, const double* T1, voldor_net* net, int flags)
 {
     if (!c || !net || !T1 || (flags & ~(VOLDOR_LEARNED_DEPTH | VOLDOR_LEARNED_RIGIDNESS))) return VOLDOR_ERR_INVALID_ARG;
@@ -495,6 +539,7 @@ void voldor_destroy(voldor_ctx* c)
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->arena) cudaFree(c->arena);
+    if (c->epi_base) cudaFree(c->epi_base);
     cudaGetLastError();
     delete c;
 }
@@ -604,6 +649,22 @@ static bool buffer_of(voldor_ctx* c, int which, void** dev, size_t* bytes, bool*
         case VOLDOR_BUF_POSE_INFO: *dev = c->ds.status; *bytes = 16; return true;
         case VOLDOR_BUF_DEPTH_SAMPLES: *dev = c->ds.mie_smp; *bytes = N * 4; return true;
         case VOLDOR_BUF_HYPS_F32: *dev = c->ds.hyp_f32; *bytes = S * 12 * 4; return true;
+        case VOLDOR_BUF_EPI_E:
+        case VOLDOR_BUF_EPI_MEDIANS:
+        case VOLDOR_BUF_EPI_VALID:
+        case VOLDOR_BUF_EPI_INFO:
+        case VOLDOR_BUF_EPI_REFINED: {
+            if (!c->epi_base || c->epi_M < 1) return false;
+            EpiState e;
+            epi_layout(c->epi_base, c->epi_M, reinterpret_cast<float4*>(c->ds.pix), &e);
+            const size_t M = (size_t)c->epi_M;
+            if (which == VOLDOR_BUF_EPI_E) { *dev = e.E; *bytes = M * 9 * 8; }
+            else if (which == VOLDOR_BUF_EPI_MEDIANS) { *dev = e.median; *bytes = M * 4; }
+            else if (which == VOLDOR_BUF_EPI_VALID) { *dev = e.valid; *bytes = M * 4; }
+            else if (which == VOLDOR_BUF_EPI_INFO) { *dev = e.info; *bytes = 8 * 8; }
+            else { *dev = e.refined; *bytes = 27 * 8; }
+            return true;
+        }
     }
     return false;
 }

@@ -119,7 +119,7 @@ __device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_
     return o;
 }
 
-enum { kStreamPose = 1, kStreamDepth = 2 };
+enum { kStreamPose = 1, kStreamDepth = 2, kStreamEpi = 3 };
 
 // ---------------------------------------------------------------------------
 // Flow access.
@@ -276,6 +276,30 @@ int score_chunks(int S, int N);
 // *kernels gets the number of kernels launched.
 voldor_status net_bootstrap(voldor_net* n, const void* flows, int f16, int W, int H, int T, float d_min, float d_max, int flags,
                             float* theta, float* wmap, cudaStream_t st, int* kernels);
+// Epipolar bootstrap scratch (a separate allocation of the context, sized by
+// the number of samples M; the correspondence records reuse the pose
+// preparation's pixel-record buffer).
+struct EpiState {
+    int M;                    // samples
+    float4* rec;              // [N] calibrated correspondences (NaN: invalid)
+    int* valid;               // [M] 1 valid; -1 repeated pixel, -2 target outside I_1, -3 rank < 8, -4 rank(E) < 2
+    double* E;                // [M][9] projected essential matrix
+    double* UV;               // [M][18] U, V (row-major, det +1)
+    float* form;              // [M][12] Q = R - I (9), t (3)
+    unsigned* hist;           // [3][M][kEpiBins]
+    unsigned* prefix;         // [M] bits selected so far
+    unsigned* rank;           // [M] remaining rank
+    float* median;            // [M]
+    long long* info;          // [8]: chosen, candidate, n_valid, n_inliers, count[4]
+    double* partial;          // [blocks][46] A^T A partials (45) + inlier count
+    double* refined;          // [9 E][9 U][9 V]
+    double* cand;             // [4][12] [R | t]
+    double* T1;               // [12]
+    int partial_blocks;
+};
+size_t epi_scratch_bytes(int M);
+size_t epi_layout(void* base, int M, float4* rec, EpiState* e);
+int launch_epipolar(const DevParams& p, const DevState& s, const EpiState& e, double baseline, cudaStream_t st);
 int score_chunks_for(int S, int N, int hpt, int waves);
 int score_chunks_max(int S, int N);
 void score_hyps_from_host(const DevParams& p, const DevState& s, int n, cudaStream_t st);

@@ -221,12 +221,22 @@ def compare(net, ds, S=4096, max_iters=8, plain_iters=5, inv_range=(1 / 16.0, 1 
            "iteration_ms": it_ms, "bootstrap_ms": boot,
            "init_depth_log_err": {m: float(np.median(depth_err[m])) for m in depth_err},
            "plain_ms": boot["plain"] + plain_iters * it_ms}
+    med = {m: np.median(err[m], axis=0) for m in err}
+    out["median_target_err_m"] = float(med["plain"][plain_iters, 0])
     for m in MODES:
         out[f"{m}_err_m"] = [float(v) for v in mean[m][:, 0]]
         out[f"{m}_rot_deg"] = [float(v) for v in mean[m][:, 1]]
+        out[f"{m}_median_err_m"] = [float(v) for v in med[m][:, 0]]
+        out[f"{m}_median_rot_deg"] = [float(v) for v in med[m][:, 1]]
+        # windows whose error after plain_iters iterations exceeds 10 cm
+        out[f"{m}_failures"] = int(np.sum(err[m][:, plain_iters, 0] > 0.1))
+        out[f"{m}_per_window_err_m"] = [[float(v) for v in err[m][i, :, 0]] for i in range(n)]
         if m == "plain":
             continue
         k_m = next((k for k in range(max_iters + 1) if mean[m][k, 0] <= 1.01 * target), None)
+        k_med = next((k for k in range(max_iters + 1) if med[m][k, 0] <= 1.01 * med["plain"][plain_iters, 0]), None)
+        out[f"{m}_median_iters_to_target"] = k_med
+        out[f"{m}_median_ms"] = None if k_med is None else boot[m] + k_med * it_ms
         out[f"{m}_iters_to_target"] = k_m
         out[f"{m}_ms"] = None if k_m is None else boot[m] + k_m * it_ms
         out[f"{m}_per_window_reached"] = float(np.mean([

@@ -20,7 +20,9 @@ FLOW_F32, FLOW_F16 = 0, 1
 LEARNED_DEPTH, LEARNED_RIGIDNESS = 1, 2
 BOOT_GIVEN_POSE = 0
 (BUF_SMOOTHED, BUF_LABELS, BUF_HYPS, BUF_HYP_INFO, BUF_HYP_WEIGHT, BUF_SCORES, BUF_POSE_INFO,
- BUF_DEPTH_SAMPLES, BUF_HYPS_F32) = range(9)
+ BUF_DEPTH_SAMPLES, BUF_HYPS_F32, BUF_EPI_E, BUF_EPI_MEDIANS, BUF_EPI_VALID, BUF_EPI_INFO,
+ BUF_EPI_REFINED) = range(14)
+EPI_MAX_SAMPLES = 4096
 
 
 class VoldorError(RuntimeError):
@@ -98,6 +100,7 @@ def lib():
             "voldor_net_forward": (i, [vp, vp, i, i, i, i, vp, vp]),
             "voldor_net_train_step": (i, [vp, vp, i, vp, i, i, i, C.c_float, C.c_float, P(C.c_float), vp]),
             "voldor_bootstrap_learned": (i, [vp, P(d), vp, i]),
+            "voldor_bootstrap_epipolar": (i, [vp, i, d, P(d)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -194,6 +197,29 @@ class Window:
     def bootstrap(self, T1):
         T1, p = _f64(T1)
         _check(lib().voldor_bootstrap(self._h, BOOT_GIVEN_POSE, p), "voldor_bootstrap", handle=self._h)
+
+    def bootstrap_epipolar(self, n_samples=512, baseline=1.0):
+        """T_1 by least median of squares on X_1, then the bootstrap; returns T_1."""
+        T1 = np.zeros(16)
+        _check(lib().voldor_bootstrap_epipolar(self._h, int(n_samples), float(baseline),
+                                               T1.ctypes.data_as(C.POINTER(C.c_double))),
+               "voldor_bootstrap_epipolar", handle=self._h)
+        self._epi_M = int(n_samples)
+        return T1.reshape(4, 4)
+
+    def epipolar_results(self):
+        """Per-sample essential matrices, medians and validity, and the
+        chosen sample / candidate, valid-pixel and inlier counts, cheirality
+        counts and the refined E, U, V of the last epipolar bootstrap."""
+        M = self._epi_M
+        E = self.get_buffer(BUF_EPI_E, (M, 3, 3), np.float64)
+        med = self.get_buffer(BUF_EPI_MEDIANS, (M,), np.float32)
+        valid = self.get_buffer(BUF_EPI_VALID, (M,), np.int32)
+        info = self.get_buffer(BUF_EPI_INFO, (8,), np.int64)
+        ref = self.get_buffer(BUF_EPI_REFINED, (3, 3, 3), np.float64)
+        return dict(E=E, medians=med, valid=valid > 0, why=valid, chosen=int(info[0]), candidate=int(info[1]),
+                    n_valid=int(info[2]), n_inliers=int(info[3]), counts=info[4:].copy(),
+                    E_refined=ref[0], U=ref[1], V=ref[2])
 
     def em_step(self, n_iters, allow_degenerate=True):
         allow = (ERR_DEGENERATE,) if allow_degenerate else ()
