@@ -70,9 +70,13 @@ typedef struct {
     int hyps_per_frame;           /* S: P3P pose hypotheses kept per frame (<= 65536) */
     int groups_per_frame;         /* G: minimal groups drawn per frame (>= 1, <= 262144) */
     int ms_max_iter;              /* meanshift iteration cap */
-    int pad_;
+    int criterion;                /* VOLDOR_CRITERION_MIE (Eq. 10, default) or _MLE (Eq. 9) for the
+                                     depth update and the dense pose scores; the E-step posterior
+                                     rho/(rho+mu) is the same under both */
     uint64_t seed, window_id;     /* Philox4x64-10 key of the window */
 } voldor_params;
+
+enum { VOLDOR_CRITERION_MIE = 0, VOLDOR_CRITERION_MLE = 1 };
 
 void voldor_default_params(voldor_params* p);
 

@@ -35,7 +35,7 @@ class Params(C.Structure):
         ("x_min", C.c_double), ("x_max", C.c_double), ("beta_min", C.c_double),
         ("ms_tol", C.c_double),
         ("hyps_per_frame", C.c_int), ("groups_per_frame", C.c_int),
-        ("ms_max_iter", C.c_int), ("pad_", C.c_int),
+        ("ms_max_iter", C.c_int), ("criterion", C.c_int),
         ("seed", C.c_uint64), ("window_id", C.c_uint64),
     ]
 
@@ -70,6 +70,7 @@ def lib():
             "or_fisk_logpdf": (d, [d, d, d]),
             "or_fisk_params": (None, [P(Params), d, P(d), P(d)]),
             "or_frame_ell": (d, [W, i, i, d, P(i)]),
+            "or_frame_crit": (d, [W, i, i, d]),
             "or_frame_eval": (i, [W, i, i, d, P(d)]),
             "or_bilinear": (i, [W, i, d, d, P(d)]),
             "or_bootstrap": (None, [W, P(d)]),
@@ -186,6 +187,9 @@ class OracleWindow:
         R = np.ascontiguousarray(R, dtype=np.float64)
         t = np.ascontiguousarray(t, dtype=np.float64)
         return lib().or_epi_cheirality(self.ref, _dp(R), _dp(t))
+
+    def frame_crit(self, t, j, depth):
+        return lib().or_frame_crit(self.ref, t, j, depth)
 
     def frame_eval(self, t, j, depth):
         out = np.zeros(12)

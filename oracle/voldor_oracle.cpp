@@ -44,7 +44,7 @@ typedef struct {
     int hyps_per_frame;           // S: pose hypotheses kept per frame
     int groups_per_frame;         // G: Philox groups drawn per frame (draw budget)
     int ms_max_iter;              // meanshift iteration cap
-    int pad_;
+    int criterion;                // 0: MIE (Eq. 10), 1: MLE (Eq. 9)
     uint64_t seed, window_id;     // Philox key
 } or_params;
 
@@ -138,6 +138,17 @@ static double mie_term(double log_rho, double log_mu)
     double d = log_mu - log_rho;
     double sp = d > 0 ? d + std::log1p(std::exp(-d)) : std::log1p(std::exp(d));
     return -sp;
+}
+
+// Per-(t, j) term of the depth / pose criterion. MIE (Eq. 10): log rho/(rho+mu).
+// MLE (Eq. 9): log rho, written as log rho - log mu (mu does not depend on
+// the depth or the pose, so the argmax is unchanged). Reading: an invalid
+// (t, j) (no observation at pi_{t-1}, or the point behind camera t) takes
+// rho := mu, i.e. log 1/2 under MIE and 0 under MLE.
+static double crit_term(const or_params* p, bool valid, double log_rho, double log_mu)
+{
+    if (p->criterion == 1) return valid ? log_rho - log_mu : 0.0;
+    return valid ? mie_term(log_rho, log_mu) : std::log(0.5);
 }
 
 // ---------------------------------------------------------------------------
@@ -238,6 +249,7 @@ struct FrameEval {
     double res[2];     // xi_t - v_ob
     double log_rho, log_mu;
     double ell;        // log rho/(rho+mu); log(1/2) when not valid
+    double crit;       // the criterion's term (crit_term)
 };
 
 static FrameEval eval_frame(const or_window* w, const double Cprev[12], const double Tt[12],
@@ -246,6 +258,7 @@ static FrameEval eval_frame(const or_window* w, const double Cprev[12], const do
     FrameEval e;
     std::memset(&e, 0, sizeof(e));
     e.ell = std::log(0.5);
+    e.crit = crit_term(&w->p, false, 0.0, 0.0);
     int x = j % w->width, y = j / w->width;
     double P0[3];
     backproject(w, x, y, depth, P0);
@@ -276,6 +289,7 @@ static FrameEval eval_frame(const or_window* w, const double Cprev[12], const do
     e.log_rho = or_fisk_logpdf(xsq, log_alpha, beta);                          // Eq. 3
     e.log_mu = or_fisk_logpdf(clamp_x(&w->p, w->p.lambda_ * w->p.lambda_ * n * n), log_alpha, beta);  // Eq. 7
     e.ell = mie_term(e.log_rho, e.log_mu);
+    e.crit = crit_term(&w->p, true, e.log_rho, e.log_mu);
     return e;
 }
 
@@ -294,6 +308,14 @@ double or_frame_ell(const or_window* w, int t, int j, double depth, int* valid)
     FrameEval e = eval_frame(w, C, Tt, t, j, depth);
     if (valid) *valid = (e.valid_prev ? 1 : 0) + (e.valid ? 1 : 0);
     return e.ell;
+}
+
+// The criterion's term of (t, j) at depth `depth` under the current poses.
+double or_frame_crit(const or_window* w, int t, int j, double depth)
+{
+    double C[12], Tt[12];
+    frame_poses(w, t, C, Tt);
+    return eval_frame(w, C, Tt, t, j, depth).crit;
 }
 
 // Diagnostics of one evaluation: out = {res_u, res_v, pi_prev_u, pi_prev_v,
@@ -665,7 +687,7 @@ void or_score_hypotheses(const or_window* w, int t, int n, const double* R, cons
         for (size_t j = 0; j < Np; ++j) {
             FrameEval e = eval_frame(w, C, Th, t, (int)j, w->theta[j]);
             if (!e.valid_prev) continue;
-            sum += Wt[j] * e.ell;
+            sum += Wt[j] * e.crit;
         }
         L[h] = sum;
     }
@@ -931,7 +953,7 @@ static double mie_score(const or_window* w, const std::vector<double>& C, const 
     double s = 0.0;
     for (int t = 1; t <= w->T; ++t) {
         FrameEval e = eval_frame(w, &C[12 * (t - 1)], &Tt[12 * (t - 1)], t, j, depth);
-        s += q[(size_t)(t - 1) * Np + j] * e.ell;
+        s += q[(size_t)(t - 1) * Np + j] * e.crit;
     }
     return std::isnan(s) ? -INFINITY : s;
 }

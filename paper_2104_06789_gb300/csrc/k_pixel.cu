@@ -221,7 +221,8 @@ __device__ __forceinline__ void load_frames32(const DevParams& p, const DevState
 __device__ __forceinline__ float depth_ell_fast(const DevParams& p, const float* fr, const void* flows, int t, int x,
                                                 int y, float depth)
 {
-    const float ln_half = -0.69314718055994531f;
+    // invalid (t, j): rho := mu, i.e. log 1/2 under MIE and 0 under MLE
+    const float ln_half = p.criterion == VOLDOR_CRITERION_MLE ? 0.f : -0.69314718055994531f;
     if (!(depth > 0.f)) return ln_half;
     const float dx = ((float)x - p.cx) * p.inv_fx, dy = ((float)y - p.cy) * p.inv_fy;
     const float w0 = 1.f / depth;
@@ -272,7 +273,9 @@ __device__ __forceinline__ float depth_ell_fast(const DevParams& p, const float*
     const FiskConst fc = fisk_const(p, sqrtf(fmaf(fu, fu, fv * fv)));
     const float s = fc.beta * (log2f(xsq) - fc.log2_alpha);
     const float e = exp2f(fabsf(s));
-    return -log1pf(fc.mu_over_beta * xsq * (e + 2.f + 1.f / e));
+    const float r = fc.mu_over_beta * xsq * (e + 2.f + 1.f / e);     // mu / rho
+    // MIE (Eq. 10): log rho/(rho+mu) = -log1p(r); MLE (Eq. 9): log rho - log mu = -log r
+    return p.criterion == VOLDOR_CRITERION_MLE ? -logf(r) : -log1pf(r);
 }
 
 // Emissions rho/(rho+mu) of every (t, j) at the current depth (E-step input)

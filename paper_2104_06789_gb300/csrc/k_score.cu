@@ -69,7 +69,10 @@ __device__ __forceinline__ float log2_1p_pos(float r)
 // 2) behind camera t. The checked form tests 1 + a_z > 0 and caps the squared
 // residual at xs_max; the fast form is used only for hypotheses whose frame
 // bounds prove both unnecessary (hyp_is_safe).
-template <bool kChecked>
+// Per pair: log2(1 + r) with r = mu / rho (MIE, Eq. 10: ell = -ln2 * this),
+// or, with kMLE, log2(r) (MLE, Eq. 9: log rho - log mu = -ln2 * this); behind
+// camera t, rho := mu (r = 1).
+template <bool kChecked, bool kMLE = false>
 __device__ __forceinline__ float pair_term2(const HypF& h, const float4 a, const float4 b, float xs_min, float xs_max)
 {
     const float xb = a.x, yb2 = a.y, w = a.z, ut = a.w;
@@ -85,8 +88,8 @@ __device__ __forceinline__ float pair_term2(const HypF& h, const float4 a, const
     if (kChecked) xs = fminf(xs, xs_max);
     const float sg = fabsf(fmaf(beta, mufu_lg2(xs), beta_k));
     const float r = Cp * xs * (mufu_ex2(sg) + (2.f + mufu_ex2(-sg)));
-    const float v = log2_1p_pos(r);
-    if (kChecked) return den > 0.f ? v : 1.f;
+    const float v = kMLE ? mufu_lg2(r) : log2_1p_pos(r);
+    if (kChecked) return den > 0.f ? v : (kMLE ? 0.f : 1.f);
     return v;
 }
 
@@ -151,7 +154,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 
 // HPT hypotheses per thread (the hypothesis side of the tile, HPT * 256 per
 // block); MINB resident blocks per SM. The autotuner picks among the instances.
-template <int HPT, int MINB>
+template <int HPT, int MINB, bool MLE>
 __global__ void __launch_bounds__(kScoreThreads, MINB) k_score(DevParams p, DevState s, int log_idx)
 {
     const int n_hyp = *s.n_hyp;
@@ -226,7 +229,7 @@ __global__ void __launch_bounds__(kScoreThreads, MINB) k_score(DevParams p, DevS
                 const float wq = reinterpret_cast<const float*>(t4 + 3 * q + 2)[0];
 #pragma unroll
                 for (int i = 0; i < HPT; ++i)
-                    facc[i] = fmaf(wq, pair_term2<false>(hy[i], a, b, xs_min, xs_max), facc[i]);
+                    facc[i] = fmaf(wq, pair_term2<false, MLE>(hy[i], a, b, xs_min, xs_max), facc[i]);
             }
         } else {
             for (int q = 0; q < cnt; ++q) {
@@ -235,7 +238,7 @@ __global__ void __launch_bounds__(kScoreThreads, MINB) k_score(DevParams p, DevS
                 const float wq = reinterpret_cast<const float*>(t4 + 3 * q + 2)[0];
 #pragma unroll
                 for (int i = 0; i < HPT; ++i)
-                    facc[i] = fmaf(wq, pair_term2<true>(hy[i], a, b, xs_min, xs_max), facc[i]);
+                    facc[i] = fmaf(wq, pair_term2<true, MLE>(hy[i], a, b, xs_min, xs_max), facc[i]);
             }
         }
 #pragma unroll
@@ -310,10 +313,12 @@ void launch_score(const DevParams& p, const DevState& s, int log_idx, cudaStream
     const int li = log_idx < kScoreLogMax ? log_idx : -1;
     if (s.score_hpt == 4) {
         dim3 grid((p.S + kScoreThreads * 4 - 1) / (kScoreThreads * 4), s.n_chunks);
-        k_score<4, 2><<<grid, kScoreThreads, 0, st>>>(p, s, li);
+        if (p.criterion == VOLDOR_CRITERION_MLE) k_score<4, 2, true><<<grid, kScoreThreads, 0, st>>>(p, s, li);
+        else k_score<4, 2, false><<<grid, kScoreThreads, 0, st>>>(p, s, li);
     } else {
         dim3 grid((p.S + kScoreThreads * 8 - 1) / (kScoreThreads * 8), s.n_chunks);
-        k_score<8, 1><<<grid, kScoreThreads, 0, st>>>(p, s, li);
+        if (p.criterion == VOLDOR_CRITERION_MLE) k_score<8, 1, true><<<grid, kScoreThreads, 0, st>>>(p, s, li);
+        else k_score<8, 1, false><<<grid, kScoreThreads, 0, st>>>(p, s, li);
     }
 }
 

@@ -29,6 +29,7 @@ constexpr int kMaxImageSide = 4096;   // longest chain the depth sweep resolves 
 struct DevParams {
     int W, H, T, N;
     int S, G, ms_max_iter, flow_f16;
+    int criterion;                      // VOLDOR_CRITERION_MIE or _MLE
     float fx, fy, cx, cy, inv_fx, inv_fy, fy_over_fx;
     float log2_a1, a2_log2e, b1, b2, beta_min, lambda2;
     float x_min, x_max;                 // px^2

@@ -6,9 +6,13 @@ correspondences, different null-space and projection methods), the FP32 median
 Sampson error to 2e-5 relative (an order statistic moves by no more than the
 largest perturbation of the values, ~1e-6 relative for the cancellation-free
 FP32 form). The winner is judged by the oracle: its oracle score is within
-2e-5 of the smallest. The refined T_1 depends on the inlier set, which
-borderline pixels can enter or leave between FP32 and FP64, so the pose is
-compared to 1e-5 rad / 1e-4 relative on noisy windows. On noiseless windows
+2e-5 of the smallest. The refined T_1 is the least-squares fit over the
+winner's inliers, which are decided by the Sampson error at a threshold: in
+FP32 on the GPU, in FP64 in the oracle, so a few borderline pixels flip; the
+two smallest eigenvalues of the fit's normal matrix are 0.0025 and 0.4 here,
+so each flip moves the fit by ~1e-5, and on noisy windows the inlier counts
+are compared to 0.1 % and T_1 to 1e-4 rad (rotation) and 1e-3 (unit
+translation). On noiseless windows
 both sides recover the generating pose; the GPU's reweighted fit solves the
 normal equations A^T A (the oracle works on A), which squares the condition
 number, so there the bound is 1e-7 (matrix entries, not an arccos angle, whose
@@ -86,8 +90,10 @@ def test_samples_medians_and_pose_match_the_oracle(vd, seed):
     assert n_cmp >= 8           # many samples hold a pixel whose target leaves the image (fast forward motion)
     assert scores[r["chosen"]] <= (1 + 2e-5) * scores.min()
     assert r["n_valid"] == sum(1 for j in range(w.W * w.H) if _valid(flows[0], j, w.W, w.H))
-    assert rotation_angle(T1[:3, :3], T1_or[:3, :3]) < 1e-5
-    assert np.abs(T1[:3, 3] - T1_or[:3, 3]).max() < 1e-4
+    n_or, _, _ = ow.epi_refine(ow.epi_sample(r["chosen"])[1], scores[r["chosen"]])
+    assert abs(r["n_inliers"] - n_or) <= 1e-3 * n_or
+    assert rotation_angle(T1[:3, :3], T1_or[:3, :3]) < 1e-4
+    assert np.abs(T1[:3, 3] - T1_or[:3, 3]).max() < 1e-3
     # the triangulated depth follows the GPU's own T_1 exactly
     _, D, _ = g.get_pose_depth_rigidness(poses=False, rigidness=False)
     ref = oracle.OracleWindow(flows.astype(np.float64), w.K, inv_depth_min=w.inv_depth_range[0],
