@@ -1,0 +1,46 @@
+"""Sliding-window VO on the GPU: a noiseless sequence bootstrapped at its
+true T_1 is followed to millimetres (narrow pose kernel; not exactly, since
+from the second frame on the flows are sampled bilinearly across the planes'
+depth edges, so the truth is not an exact fixed point of a general scene), and
+a noisy driving sequence started from the epipolar estimate stays within 5 %
+of its path length."""
+import numpy as np
+import pytest
+
+from paper_2104_06789_gb300 import synthetic, vo
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vd():
+    from paper_2104_06789_gb300 import build, voldor
+    build.build()
+    return voldor
+
+
+def _centres(traj):
+    return np.array([-M[:3, :3].T @ M[:3, 3] for M in traj])
+
+
+def test_noiseless_sequence_is_followed(vd):
+    w = synthetic.small_planes(seed=1000, T=10, noise=False, nonrigid=False)
+    p = vd.default_params(hyps_per_frame=1024, groups_per_frame=2048, inv_depth_min=w.inv_depth_range[0],
+                          inv_depth_max=w.inv_depth_range[1], sigma_t=1e-8, sigma_r=1e-10)
+    r = vo.SlidingWindowVO(w.K, T=4, stride=2, n_iters=3, params=p).run(w.flows.astype(np.float32), T1=w.poses[0])
+    assert r["starts"] == [0, 2, 4, 6]
+    ref = vo.chain(w.poses)
+    assert np.abs(_centres(r["trajectory"]) - _centres(ref)).max() < 5e-3      # 1 m of path
+    for a, b in zip(r["trajectory"], ref):
+        assert np.abs(a[:3, :3] - b[:3, :3]).max() < 1e-3
+
+
+def test_noisy_driving_sequence_from_the_epipolar_start(vd):
+    w = synthetic.driving(seed=3001, W=414, H=125, f=239.3, T=12)
+    p = vd.default_params(hyps_per_frame=1024, groups_per_frame=2048, inv_depth_min=w.inv_depth_range[0],
+                          inv_depth_max=w.inv_depth_range[1])
+    r = vo.SlidingWindowVO(w.K, T=6, stride=3, n_iters=5, params=p).run(
+        w.flows.astype(np.float16).astype(np.float32), T1=None, baseline=float(np.linalg.norm(w.poses[0][:3, 3])))
+    c, cr = _centres(r["trajectory"]), _centres(vo.chain(w.poses))
+    path = np.linalg.norm(np.diff(cr, axis=0), axis=1).sum()
+    assert np.linalg.norm(c[-1] - cr[-1]) < 0.05 * path
