@@ -100,6 +100,7 @@ def lib():
             "or_epi_cheirality": (C.c_int64, [W, P(d), P(d)]),
             "or_epipolar_bootstrap": (i, [W, i, d, P(d), P(d), P(i), P(i)]),
             "or_epi_refine": (C.c_int64, [W, P(d), d, P(d), P(d)]),
+            "or_ground_scale": (i, [W, d, d, P(d), P(d), P(C.c_int64)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -182,6 +183,13 @@ class OracleWindow:
         out, thr = np.zeros(9), C.c_double(0.0)
         n = lib().or_epi_refine(self.ref, _dp(E), float(median), _dp(out), C.byref(thr))
         return n, out.reshape(3, 3), thr.value
+
+    def ground_scale(self, camera_height, max_tilt_deg=10.0):
+        """(status, scale, mode of log2 height, candidate pixels)."""
+        s, m, n = C.c_double(0), C.c_double(0), C.c_int64(0)
+        st = lib().or_ground_scale(self.ref, float(camera_height), float(np.deg2rad(max_tilt_deg)), C.byref(s),
+                                   C.byref(m), C.byref(n))
+        return st, s.value, m.value, n.value
 
     def epi_cheirality(self, R, t):
         R = np.ascontiguousarray(R, dtype=np.float64)

@@ -1396,4 +1396,96 @@ int or_epipolar_bootstrap(or_window* w, int n_samples, double baseline, double T
     return OR_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Absolute scale from the ground plane (Sec. 6.1: the mode of the pixels whose
+// surface normal is near perpendicular; the paper's appendix with the details
+// is not part of its text). Readings:
+//  - P_j = theta_j K^-1 [x y 1]^T; the normal of pixel j is the unit
+//    (P(x+1,y) - P(x-1,y)) x (P(x,y+1) - P(x,y-1)), turned to face the camera
+//    (n . P < 0); border pixels, pixels with a neighbour at either end of the
+//    depth range, and pixels with mean rigidness over the frames below 1/2 are
+//    skipped;
+//  - ground candidates: below the camera (P_y > 0, the image y axis pointing
+//    down) with |n . (0, 1, 0)| >= cos(max_tilt);
+//  - each candidate's camera height is the distance |n . P| of its tangent
+//    plane from the camera centre;
+//  - the histogram of log2(height) over [-8, 8) in 4096 bins; the bin m of the
+//    largest count of the 5-bin box-filtered histogram (the lowest on ties);
+//    the mode is the count-weighted mean of the bin centres of the raw
+//    histogram over bins m-2 .. m+2;
+//  - scale = camera_height / 2^mode (multiply translations and depths by it).
+// ---------------------------------------------------------------------------
+static void ground_point(const or_window* w, int x, int y, double P[3])
+{
+    const double th = w->theta[(size_t)y * w->width + x];
+    P[0] = th * (x - w->cx) / w->fx;
+    P[1] = th * (y - w->cy) / w->fy;
+    P[2] = th;
+}
+
+int or_ground_scale(const or_window* w, double camera_height, double max_tilt_rad, double* scale_out,
+                    double* mode_log2_out, int64_t* candidates_out)
+{
+    const int W = w->width, H = w->height, T = w->T;
+    const int nb = 4096;
+    const double lo = -8.0, hi = 8.0, binw = (hi - lo) / nb;
+    const double dmin = 1.0 / w->p.inv_depth_max, dmax = 1.0 / w->p.inv_depth_min;
+    const double cthr = std::cos(max_tilt_rad);
+    std::vector<int64_t> hist(nb, 0);
+    int64_t cand = 0;
+    for (int y = 1; y < H - 1; ++y) {
+        for (int x = 1; x < W - 1; ++x) {
+            const size_t j = (size_t)y * W + x;
+            bool ok = true;
+            const size_t nbj[5] = {j, j - 1, j + 1, j - W, j + W};
+            for (int i = 0; i < 5; ++i) {
+                const double th = w->theta[nbj[i]];
+                if (!(th > dmin && th < dmax)) ok = false;
+            }
+            double wm = 0.0;
+            for (int t = 0; t < T; ++t) wm += w->wmap[(size_t)t * W * H + j];
+            if (!ok || !(wm / T >= 0.5)) continue;
+            double P[3], Pl[3], Pr[3], Pu[3], Pd[3];
+            ground_point(w, x, y, P);
+            ground_point(w, x - 1, y, Pl); ground_point(w, x + 1, y, Pr);
+            ground_point(w, x, y - 1, Pu); ground_point(w, x, y + 1, Pd);
+            double a[3], c[3], n[3];
+            sub3(Pr, Pl, a);
+            sub3(Pd, Pu, c);
+            cross3(a, c, n);
+            if (!normalize3(n)) continue;
+            if (dot3(n, P) > 0) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; }
+            if (!(P[1] > 0.0) || !(std::fabs(n[1]) >= cthr)) continue;
+            const double h = std::fabs(dot3(n, P));
+            if (!(h > 0.0)) continue;
+            const double l = std::log2(h);
+            if (!(l >= lo && l < hi)) continue;
+            int bin = (int)std::floor((l - lo) / binw);
+            if (bin >= nb) bin = nb - 1;
+            hist[bin] += 1;
+            ++cand;
+        }
+    }
+    if (candidates_out) *candidates_out = cand;
+    if (cand == 0) return OR_DEGENERATE;
+    std::vector<int64_t> sm(nb, 0);
+    for (int i = 0; i < nb; ++i)
+        for (int k = -2; k <= 2; ++k)
+            if (i + k >= 0 && i + k < nb) sm[i] += hist[i + k];
+    int m = 0;
+    for (int i = 1; i < nb; ++i)
+        if (sm[i] > sm[m]) m = i;
+    double num = 0.0, cnt = 0.0;
+    for (int k = -2; k <= 2; ++k)
+        if (m + k >= 0 && m + k < nb) {
+            num += (double)hist[m + k] * (lo + (m + k + 0.5) * binw);
+            cnt += (double)hist[m + k];
+        }
+    const double mode = num / cnt;
+    if (mode_log2_out) *mode_log2_out = mode;
+    if (scale_out) *scale_out = camera_height / std::exp2(mode);
+    return OR_OK;
+}
+
 }  // extern "C"
