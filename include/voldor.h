@@ -302,6 +302,23 @@ void voldor_batch_destroy(voldor_batch* batch);
 voldor_status voldor_em_batch(voldor_ctx* const* ctxs, int n, int n_iters);
 
 /* ---------------------------------------------------------------------------
+ * Absolute scale from the ground plane (Sec. 6.1: the scale is taken from the
+ * mode over the pixels whose surface normal is near the vertical; the paper's
+ * details are in an appendix that is not part of its text). From the current
+ * depth of I_0: normals by central differences of the back-projected depth
+ * map; rigid pixels (mean W >= 1/2) below the camera (image y axis down) whose
+ * normal is within max_tilt_rad of the camera's y axis, with all five depths of
+ * the stencil strictly inside the depth range, give the distance of their
+ * tangent plane from the camera; the mode of log2 of those heights (4096 bins
+ * over [-8, 8), argmax of the 5-bin box-filtered histogram, centroid of the raw
+ * bins around it) gives scale = camera_height / 2^mode. With apply != 0 the
+ * depth and every translation are multiplied by it. Synchronises the
+ * context's stream. VOLDOR_ERR_DEGENERATE if no pixel qualifies.
+ * ------------------------------------------------------------------------- */
+voldor_status voldor_ground_scale(voldor_ctx* ctx, double camera_height, double max_tilt_rad, int apply,
+                                  double* scale_out);
+
+/* ---------------------------------------------------------------------------
  * Learned proposal (no counterpart in the paper): a 6-layer
  * 3x3 convolutional network, 2T -> 32 -> 32 -> 32 -> 32 -> 32 -> 2 channels
  * with ReLU between layers, reads the flows (divided by 32 px, 2 channels per

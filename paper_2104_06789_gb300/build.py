@@ -27,6 +27,7 @@ UNITS = {
     "voldor_api.cu": [],
     "k_net.cu": [],
     "k_epi.cu": [],
+    "k_ground.cu": [],
 }
 
 

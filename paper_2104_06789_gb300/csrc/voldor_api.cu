@@ -40,6 +40,7 @@ struct voldor_ctx {
     void* epi_base = nullptr;                        // epipolar bootstrap scratch
     int epi_cap = 0;                                 // samples it holds
     int epi_M = 0;                                   // samples of the last epipolar bootstrap
+    void* ground_base = nullptr;                     // ground-plane scale scratch
 };
 
 namespace {
@@ -469,6 +470,35 @@ voldor_status voldor_bootstrap_epipolar(voldor_ctx* c, int n_samples, double bas
     return VOLDOR_OK;
 }
 
+voldor_status voldor_ground_scale(voldor_ctx* c, double camera_height, double max_tilt_rad, int apply,
+                                 double* scale_out)
+{
+    if (!c || !finite_pos(camera_height) || !(max_tilt_rad > 0.0 && max_tilt_rad < 1.5707963267948966))
+        return VOLDOR_ERR_INVALID_ARG;
+    if (c->poisoned) return kCuda;
+    if (!c->bootstrapped) return VOLDOR_ERR_NOT_BOOTSTRAPPED;
+    if (!c->ground_base) {
+        if (cudaMalloc(&c->ground_base, kGroundScratchBytes) != cudaSuccess) {
+            cudaGetLastError();
+            c->ground_base = nullptr;
+            return VOLDOR_ERR_OOM;
+        }
+    }
+    unsigned* hist = static_cast<unsigned*>(c->ground_base);
+    double* out = reinterpret_cast<double*>(static_cast<char*>(c->ground_base) + 4096 * 4);
+    c->launches += launch_ground_scale(c->dp, c->ds, camera_height, std::cos(max_tilt_rad),
+                                       1.0 / c->params.inv_depth_max, 1.0 / c->params.inv_depth_min, apply, hist,
+                                       out, c->stream);
+    if (!launched(c)) return kCuda;
+    double h[3];
+    if (!cuda_ok(c, cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, c->stream)) ||
+        !cuda_ok(c, cudaStreamSynchronize(c->stream)))
+        return kCuda;
+    if (!(h[2] > 0.0)) return VOLDOR_ERR_DEGENERATE;
+    if (scale_out) *scale_out = h[0];
+    return VOLDOR_OK;
+}
+
 voldor_status voldor_bootstrap_learned(voldor_ctx* c, const double* T1, voldor_net* net, int flags)
 {
     if (!c || !net || !T1 || (flags & ~(VOLDOR_LEARNED_DEPTH | VOLDOR_LEARNED_RIGIDNESS))) return VOLDOR_ERR_INVALID_ARG;
@@ -543,6 +573,7 @@ void voldor_destroy(voldor_ctx* c)
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->arena) cudaFree(c->arena);
     if (c->epi_base) cudaFree(c->epi_base);
+    if (c->ground_base) cudaFree(c->ground_base);
     cudaGetLastError();
     delete c;
 }

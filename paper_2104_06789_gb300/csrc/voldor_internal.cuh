@@ -301,6 +301,11 @@ struct EpiState {
 size_t epi_scratch_bytes(int M);
 size_t epi_layout(void* base, int M, float4* rec, EpiState* e);
 int launch_epipolar(const DevParams& p, const DevState& s, const EpiState& e, double baseline, cudaStream_t st);
+// Ground-plane scale: hist [4096] and out [3] are device scratch; returns the
+// number of kernels launched.
+constexpr int kGroundScratchBytes = 4096 * 4 + 256;
+int launch_ground_scale(const DevParams& p, const DevState& s, double camera_height, double cos_tilt, double dmin,
+                        double dmax, int apply, unsigned* hist, double* out, cudaStream_t st);
 int score_chunks_for(int S, int N, int hpt, int waves);
 int score_chunks_max(int S, int N);
 void score_hyps_from_host(const DevParams& p, const DevState& s, int n, cudaStream_t st);

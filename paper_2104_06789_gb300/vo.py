@@ -14,7 +14,11 @@ driver does that over the C ABI with one reused window context:
 - window k contributes its first `stride` relative poses to the trajectory (the
   last window contributes all of its remaining ones);
 - the trajectory is chained as world-to-camera transforms M_0 = I,
-  M_{f+1} = T_{f+1} M_f (T_f maps camera f-1 coordinates to camera f).
+  M_{f+1} = T_{f+1} M_f (T_f maps camera f-1 coordinates to camera f);
+- with a camera height, every window's depth and translations are rescaled
+  after its EM so that its ground plane lies that far below the camera
+  (Sec. 6.1's absolute scale from the ground plane), instead of inheriting the
+  scale of the window before.
 """
 from __future__ import annotations
 
@@ -57,7 +61,7 @@ class SlidingWindowVO:
         self.params = params
         self.make_window = make_window or (lambda f, K, p: voldor.Window(f, K, p))
 
-    def run(self, flows, T1=None, baseline=1.0, epi_samples=512):
+    def run(self, flows, T1=None, baseline=1.0, epi_samples=512, camera_height=None, max_tilt_deg=10.0):
         """flows [n][H][W][2] (numpy or torch, FP16 or FP32). Returns a dict:
         `relative` [n][4][4] (T_1..T_n), `trajectory` [n+1][4][4]
         (world-to-camera), `starts` (first frame of each window) and
@@ -79,6 +83,8 @@ class SlidingWindowVO:
             else:
                 win.bootstrap(next_T1)
             win.em_step(self.n_iters)
+            if camera_height is not None:
+                win.ground_scale(camera_height, max_tilt_deg, apply=True)
             P, _, _ = win.get_pose_depth_rigidness(depth=False, rigidness=False)
             window_poses.append(P)
             last = k == len(starts) - 1

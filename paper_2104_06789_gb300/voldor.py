@@ -102,6 +102,7 @@ def lib():
             "voldor_net_train_step": (i, [vp, vp, i, vp, i, i, i, C.c_float, C.c_float, P(C.c_float), vp]),
             "voldor_bootstrap_learned": (i, [vp, P(d), vp, i]),
             "voldor_bootstrap_epipolar": (i, [vp, i, d, P(d)]),
+            "voldor_ground_scale": (i, [vp, d, d, i, P(d)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -207,6 +208,15 @@ class Window:
                "voldor_bootstrap_epipolar", handle=self._h)
         self._epi_M = int(n_samples)
         return T1.reshape(4, 4)
+
+    def ground_scale(self, camera_height, max_tilt_deg=10.0, apply=False):
+        """Scale that puts the ground plane of the current depth at
+        camera_height below the camera (applied to the depth and the
+        translations if apply)."""
+        s = C.c_double(0.0)
+        _check(lib().voldor_ground_scale(self._h, float(camera_height), float(np.deg2rad(max_tilt_deg)),
+                                         1 if apply else 0, C.byref(s)), "voldor_ground_scale", handle=self._h)
+        return s.value
 
     def epipolar_results(self):
         """Per-sample essential matrices, medians and validity, and the

@@ -92,4 +92,5 @@ def test_net_arguments_are_checked_on_the_host(vd):
     assert L.voldor_net_forward(None, None, 0, 1, 1, 1, None, None) == vd.ERR_INVALID_ARG
     assert L.voldor_bootstrap_learned(None, None, None, 3) == vd.ERR_INVALID_ARG
     assert L.voldor_bootstrap_epipolar(None, 64, 1.0, None) == vd.ERR_INVALID_ARG
+    assert L.voldor_ground_scale(None, 1.65, 0.17, 0, None) == vd.ERR_INVALID_ARG
     L.voldor_net_destroy(None)

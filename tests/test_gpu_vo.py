@@ -44,3 +44,18 @@ def test_noisy_driving_sequence_from_the_epipolar_start(vd):
     c, cr = _centres(r["trajectory"]), _centres(vo.chain(w.poses))
     path = np.linalg.norm(np.diff(cr, axis=0), axis=1).sum()
     assert np.linalg.norm(c[-1] - cr[-1]) < 0.05 * path
+
+
+def test_ground_plane_fixes_a_wrong_initial_scale(vd):
+    w = synthetic.driving(seed=3001, W=414, H=125, f=239.3, T=12)
+    p = vd.default_params(hyps_per_frame=1024, groups_per_frame=2048, inv_depth_min=w.inv_depth_range[0],
+                          inv_depth_max=w.inv_depth_range[1])
+    d = vo.SlidingWindowVO(w.K, T=6, stride=3, n_iters=5, params=p)
+    flows = w.flows.astype(np.float16).astype(np.float32)
+    r = d.run(flows, T1=None, baseline=0.3, camera_height=1.65)       # true baseline 1 m
+    c, cr = _centres(r["trajectory"]), _centres(vo.chain(w.poses))
+    path = np.linalg.norm(np.diff(cr, axis=0), axis=1).sum()
+    assert np.linalg.norm(c[-1] - cr[-1]) < 0.05 * path
+    r0 = d.run(flows, T1=None, baseline=0.3)                          # without it the scale stays 0.3
+    c0 = _centres(r0["trajectory"])
+    assert np.linalg.norm(c0[-1] - cr[-1]) > 0.5 * path

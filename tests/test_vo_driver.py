@@ -52,6 +52,12 @@ class FakeWindow:
     def em_step(self, n):
         pass
 
+    def ground_scale(self, h, tilt, apply=False):
+        s = 1.0 / self.scale                 # the ground puts the window back at the true scale
+        if apply:
+            self.scale = 1.0
+        return s
+
     def get_pose_depth_rigidness(self, **kw):
         P = np.array([self.truth[f].copy() for f in self.frames])
         P[:, :3, 3] *= self.scale
@@ -116,3 +122,13 @@ def test_driver_epipolar_start_uses_the_baseline():
     ratio = np.linalg.norm(r["relative"][:, :3, 3], axis=1) / np.linalg.norm(truth[:, :3, 3], axis=1)
     s = 0.5 / np.linalg.norm(truth[0][:3, 3])
     assert np.allclose(ratio, s)
+
+
+def test_driver_ground_scale_restores_the_true_scale():
+    truth = _truth(9, seed=5)
+    d = vo.SlidingWindowVO((100.0, 100.0, 10.0, 10.0), T=4, stride=2, n_iters=1,
+                           make_window=lambda f, K, p: FakeWindow(truth, f))
+    first = truth[0].copy()
+    first[:3, 3] *= 3.0
+    r = d.run(_flows(9), T1=first, camera_height=1.65)
+    assert np.allclose(r["relative"], truth)
