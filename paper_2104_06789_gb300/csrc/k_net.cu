@@ -24,7 +24,9 @@
 #include <new>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include "voldor_internal.cuh"
 
@@ -92,89 +94,408 @@ __device__ __forceinline__ void load_halo(bf16* s, const bf16* in, int cin_g, in
 }
 
 // ---------------------------------------------------------------------------
-// 3x3 convolution (implicit GEMM): out[p][n] = sum_{tap, c} in[p + off(tap)][c]
-// w[n][tap][c] (+ bias[n]), for NT*8 output channels. Each warp computes one
-// tile row of 32 pixels as two m16 tiles; K runs over 9 taps x CIN channels in
-// k16 steps. Epilogue: optional bias, ReLU, and the ReLU mask of a previous
-// activation (for the input gradient); bf16 or fp32 output.
+// 3x3 convolution on the fifth-generation tensor cores (implicit GEMM):
+// out[p][n] = sum_{tap, c} in[p + off(tap)][c] w[n][tap][c] (+ bias[n]).
+//
+// A CTA owns a strip of kTcM = 128 output pixels of a row and walks down
+// kTcRows rows of it (persistent over strips). Warp roles:
+//   warp 4, one lane: TMA loads of input rows (box 8 channels x 130 columns,
+//     zero fill outside the image) into a ring of kTcSlots row slots laid out
+//     [channel block][column][8 channels], which is the K-major, unswizzled
+//     core-matrix layout of the A operand: an A tile of 128 pixels x 16
+//     channels is a descriptor into the slot (8-pixel groups 128 B apart,
+//     the two 8-channel halves one channel-block row apart), and the taps'
+//     column shift kx is 16 kx bytes on its start address.
+//   warp 5, one lane: per output row, 9 taps x CIN/16 tcgen05.mma
+//     (M = 128, N, K = 16, BF16 in, FP32 accumulators in TMEM), alternating
+//     between two accumulators, committed to mbarriers that release the
+//     accumulator to the epilogue and the oldest input row to the loader.
+//   warps 0-3: epilogue: tcgen05.ld of the accumulator rows of their 32 TMEM
+//     lanes (one pixel per thread), bias, ReLU, the ReLU mask of a previous
+//     activation (input gradient), bf16 or fp32 stores.
+// Weights [N][9][CIN] are staged once per CTA in the B operand's core-matrix
+// layout. Every mbarrier wait is bounded: on expiry the CTA raises *err,
+// drains its own copies and MMAs, frees its TMEM and returns.
 // ---------------------------------------------------------------------------
 struct ConvArgs {
     const bf16* in;
     int cin_g;
-    const bf16* w;          // [NT*8][9][CIN] bf16
-    const float* bias;      // NT*8 or null
+    const bf16* w;          // [w_rows][9][CIN] bf16; rows w_rows..N-1 are taken as zero
+    int w_rows;
+    const float* bias;      // N or null
     bf16* out;              // bf16 output (channel stride cout_g) or null
     float* out_f;           // fp32 output (channel stride cout_g) or null
     int cout_g;
     int n_out;              // real output channels written
     const bf16* mask;       // zero the output where mask <= 0 (channel stride cout_g), or null
     int relu;
-    int H, W;
+    int H, W, B;
+    int* err;               // set to 1 if a wait expired
 };
 
-template <int CIN, int NT>
-__global__ void __launch_bounds__(128) k_conv3x3(ConvArgs a)
+constexpr int kTcM = 128;                        // output pixels per row strip (MMA M)
+constexpr int kTcCols = kTcM + 2;                // input columns per row slot
+constexpr int kTcRowBytes = 2176;                // one channel block of a slot: 130 x 16 B, padded to 128 B
+constexpr int kTcSlots = 4;                      // input rows in flight
+constexpr int kTcRows = 16;                      // output rows per work item
+constexpr int kTcThreads = 192;
+constexpr long long kTcWaitLimit = 1ll << 24;    // polls of one mbarrier phase before giving up
+
+template <int CIN, int N>
+struct TcShape {
+    static constexpr int kCB = CIN / 8;                          // channel blocks
+    static constexpr int kSlotBytes = kCB * kTcRowBytes;
+    static constexpr int kSlotTxBytes = kCB * kTcCols * 16;         // bytes the row's TMA boxes deliver
+    static constexpr int kKSteps = 9 * CIN / 16;                 // MMAs per output row
+    static constexpr int kWStepBytes = N * 16 * 2;               // one K step of B
+    static constexpr int kRingBytes = kTcSlots * kSlotBytes;
+    static constexpr int kWBytes = kKSteps * kWStepBytes;
+    // ring | weights | barriers: full[4] empty[4] acc_full[2] acc_empty[2] done | tmem address
+    static constexpr int kBarOff = kRingBytes + kWBytes;
+    static constexpr int kSmemBytes = kBarOff + 16 * 8 + 16;      // + tmem address, abort flag
+    static constexpr int kTmemCols = 2 * N < 32 ? 32 : 2 * N;
+    static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+                                       ((uint32_t)(kTcM >> 4) << 24);
+};
+
+__device__ __forceinline__ void tc_mbar_init(uint32_t bar, uint32_t count)
 {
-    constexpr int CS = CIN + 8;                 // padded pixel stride (bank-conflict free)
-    constexpr int WS = 9 * CIN + 8;             // padded weight row stride
-    __shared__ __align__(16) bf16 in_s[kHaloH * kHaloW * CS];
-    __shared__ __align__(16) bf16 w_s[NT * 8 * WS];
-    const int x0 = blockIdx.x * kTileW, y0 = blockIdx.y * kTileH, b = blockIdx.z;
-    for (int i = threadIdx.x; i < NT * 8 * (9 * CIN / 8); i += blockDim.x) {
-        const int n = i / (9 * CIN / 8), v = i % (9 * CIN / 8);
-        *reinterpret_cast<uint4*>(w_s + n * WS + v * 8) = *reinterpret_cast<const uint4*>(a.w + (size_t)n * 9 * CIN + v * 8);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ bool tc_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}"
+                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; false (and *bad set) on expiry or when another role already gave up.
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity, volatile int* bad)
+{
+    for (long long i = 0; i < kTcWaitLimit; ++i) {
+        if (tc_try_wait(bar, parity)) return true;
+        if ((i & 1023) == 1023 && *bad) return false;
     }
-    load_halo<CIN, CS>(in_s, a.in, a.cin_g, a.H, a.W, b, x0, y0);
+    *bad = 1;
+    return false;
+}
+
+__device__ __forceinline__ void tc_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tc_tma_row(uint32_t dst, const CUtensorMap* map, int c, int x, int y, int b, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+                 ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c), "r"(x), "r"(y), "r"(b), "r"(bar) : "memory");
+}
+
+// Shared-memory matrix descriptor, K-major without swizzle: start, leading
+// (K-direction core-matrix) offset, stride (M/N-direction 8-row group) offset.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                 ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+template <int NC>
+__device__ __forceinline__ void tc_ld(uint32_t taddr, float* v);
+
+template <>
+__device__ __forceinline__ void tc_ld<32>(uint32_t taddr, float* v)
+{
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                   "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <>
+__device__ __forceinline__ void tc_ld<16>(uint32_t taddr, float* v)
+{
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Work item i: image b, strip sx (128 columns), row chunk cy (kTcRows rows).
+struct TcItem {
+    int b, x0, y0, rows;
+};
+
+__device__ __forceinline__ TcItem tc_item(int i, int H, int W)
+{
+    const int strips = (W + kTcM - 1) / kTcM, chunks = (H + kTcRows - 1) / kTcRows;
+    TcItem t;
+    t.b = i / (strips * chunks);
+    const int r = i % (strips * chunks);
+    t.x0 = (r % strips) * kTcM;
+    t.y0 = (r / strips) * kTcRows;
+    t.rows = min(kTcRows, H - t.y0);
+    return t;
+}
+
+template <int CIN, int N>
+__global__ void __launch_bounds__(kTcThreads, 2) k_conv_tc(const __grid_constant__ CUtensorMap tin, ConvArgs a)
+{
+    using S = TcShape<CIN, N>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const uint32_t sbase = smem_addr(smem);
+    const uint32_t ring = sbase, wsm = sbase + S::kRingBytes, bars = sbase + S::kBarOff;
+    const uint32_t full = bars, empty = bars + 4 * 8, acc_full = bars + 8 * 8, acc_empty = bars + 10 * 8,
+                   done = bars + 12 * 8;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + S::kBarOff + 16 * 8);
+    volatile int& bad = *reinterpret_cast<volatile int*>(smem + S::kBarOff + 16 * 8 + 4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_items = a.B * ((a.H + kTcRows - 1) / kTcRows) * ((a.W + kTcM - 1) / kTcM);
+
+    // weights -> B operand layout: [K step][n group][k half][8 rows][8 channels]
+    for (int i = threadIdx.x; i < N * 9 * (CIN / 8); i += blockDim.x) {
+        const int n = i / (9 * (CIN / 8)), rem = i % (9 * (CIN / 8));
+        const int tap = rem / (CIN / 8), cb = rem % (CIN / 8);
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (n < a.w_rows) v = *reinterpret_cast<const uint4*>(a.w + ((size_t)n * 9 + tap) * CIN + cb * 8);
+        const int step = tap * (CIN / 16) + cb / 2;
+        const uint32_t off = step * S::kWStepBytes + (n >> 3) * 256 + (cb & 1) * 128 + (n & 7) * 16;
+        *reinterpret_cast<uint4*>(smem + S::kRingBytes + off) = v;
+    }
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kTcSlots; ++i) {
+            tc_mbar_init(full + 8 * i, 1);
+            tc_mbar_init(empty + 8 * i, 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            tc_mbar_init(acc_full + 8 * i, 1);
+            tc_mbar_init(acc_empty + 8 * i, 4 * 32);
+        }
+        tc_mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        bad = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                     "r"((uint32_t)S::kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");     // weights visible to the tensor cores
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gid = lane >> 2, tig = lane & 3;
-    for (int mt = 0; mt < 2; ++mt) {
-        float acc[NT][4];
-#pragma unroll
-        for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-#pragma unroll
-        for (int tap = 0; tap < 9; ++tap) {
-            const int ky = tap / 3, kx = tap % 3;
-#pragma unroll
-            for (int kc = 0; kc < CIN / 16; ++kc) {
-                uint32_t a0, a1, a2, a3;
-                const int px = mt * 16 + (lane & 15) + kx;
-                ldsm_x4(smem_addr(in_s + ((warp + ky) * kHaloW + px) * CS + kc * 16 + (lane >> 4) * 8), a0, a1, a2, a3);
-#pragma unroll
-                for (int n = 0; n < NT; ++n) {
-                    uint32_t b0, b1;
-                    ldsm_x2(smem_addr(w_s + (n * 8 + (lane & 7)) * WS + tap * CIN + kc * 16 + ((lane >> 3) & 1) * 8), b0, b1);
-                    mma_bf16(acc[n], a0, a1, a2, a3, b0, b1);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            // loader
+            uint32_t ld = 0;
+            for (int it = blockIdx.x; it < n_items && !bad; it += gridDim.x) {
+                const TcItem t = tc_item(it, a.H, a.W);
+                for (int r = t.y0 - 1; r <= t.y0 + t.rows && !bad; ++r, ++ld) {
+                    const uint32_t slot = ld % kTcSlots;
+                    if (ld >= kTcSlots && !tc_wait(empty + 8 * slot, ((ld / kTcSlots) - 1) & 1, &bad)) break;
+                    tc_expect_tx(full + 8 * slot, (uint32_t)S::kSlotTxBytes);
+                    for (int cb = 0; cb < S::kCB; ++cb)
+                        tc_tma_row(ring + slot * S::kSlotBytes + cb * kTcRowBytes, &tin, cb * 8, t.x0 - 1, r, t.b,
+                                   full + 8 * slot);
                 }
             }
+            // the last loads may still be landing when another role gave up
+            for (uint32_t j = ld > kTcSlots ? ld - kTcSlots : 0; j < ld; ++j) {
+                for (long long i = 0; i < kTcWaitLimit; ++i)
+                    if (tc_try_wait(full + 8 * (j % kTcSlots), (j / kTcSlots) & 1)) break;
+            }
         }
-        const int py = y0 + warp;
+    } else if (warp == 5) {
+        if (lane == 0) {
+            // MMA issuer
+            uint32_t ld = 0, orow = 0;
+            for (int it = blockIdx.x; it < n_items && !bad; it += gridDim.x) {
+                const TcItem t = tc_item(it, a.H, a.W);
+                const uint32_t L0 = ld;
+                if (!tc_wait(full + 8 * (L0 % kTcSlots), (L0 / kTcSlots) & 1, &bad)) break;
+                if (!tc_wait(full + 8 * ((L0 + 1) % kTcSlots), ((L0 + 1) / kTcSlots) & 1, &bad)) break;
+                for (int k = 0; k < t.rows; ++k, ++orow) {
+                    const uint32_t li = L0 + k + 2;
+                    if (!tc_wait(full + 8 * (li % kTcSlots), (li / kTcSlots) & 1, &bad)) break;
+                    const uint32_t buf = orow & 1;
+                    if (orow >= 2 && !tc_wait(acc_empty + 8 * buf, ((orow >> 1) - 1) & 1, &bad)) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t d = tmem + buf * N;
+                    uint32_t acc = 0;
 #pragma unroll
-        for (int n = 0; n < NT; ++n) {
+                    for (int ky = 0; ky < 3; ++ky) {
+                        const uint32_t row = ring + ((L0 + k + ky) % kTcSlots) * S::kSlotBytes;
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const int px = x0 + mt * 16 + gid + 8 * half;
-                if (py >= a.H || px >= a.W) continue;
-                const int co = n * 8 + 2 * tig;
-                const size_t o = (((size_t)b * a.H + py) * a.W + px) * a.cout_g + co;
-                float v0 = acc[n][2 * half], v1 = acc[n][2 * half + 1];
-                if (a.bias) { v0 += a.bias[co]; v1 += a.bias[co + 1]; }
-                if (a.relu) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
+                        for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+                            for (int cp = 0; cp < CIN / 16; ++cp) {
+                                const int step = (ky * 3 + kx) * (CIN / 16) + cp;
+                                const uint64_t ad = tc_desc(row + cp * 2 * kTcRowBytes + kx * 16, kTcRowBytes, 128);
+                                const uint64_t bd = tc_desc(wsm + step * S::kWStepBytes, 128, 256);
+                                tc_mma(d, ad, bd, S::kIdesc, acc);
+                                acc = 1;
+                            }
+                    }
+                    tc_commit(acc_full + 8 * buf);
+                    tc_commit(empty + 8 * ((L0 + k) % kTcSlots));           // input row y - 1 is done
+                }
+                if (bad) break;
+                // the item's last two input rows
+                tc_commit(empty + 8 * ((L0 + t.rows) % kTcSlots));
+                tc_commit(empty + 8 * ((L0 + t.rows + 1) % kTcSlots));
+                ld = L0 + t.rows + 2;
+            }
+            tc_commit(done);                  // arrives once every MMA issued above has completed
+            for (long long i = 0; i < kTcWaitLimit; ++i)
+                if (tc_try_wait(done, 0)) break;
+        }
+    } else {
+        // epilogue: warp w reads TMEM lanes 32w .. 32w + 31 = pixels x0 + 32w + lane
+        float bias[N];
+#pragma unroll
+        for (int n = 0; n < N; ++n) bias[n] = a.bias ? __ldg(a.bias + n) : 0.f;
+        uint32_t orow = 0;
+        bool go = true;
+        for (int it = blockIdx.x; it < n_items && go; it += gridDim.x) {
+            const TcItem t = tc_item(it, a.H, a.W);
+            for (int k = 0; k < t.rows; ++k, ++orow) {
+                const uint32_t buf = orow & 1;
+                // every lane polls; the warp proceeds only together (tcgen05.ld is warp-wide)
+                go = __all_sync(0xffffffffu, tc_wait(acc_full + 8 * buf, (orow >> 1) & 1, &bad));
+                if (!go) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                float v[N];
+                tc_ld<N>(tmem + ((uint32_t)(warp * 32) << 16) + buf * N, v);
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                tc_arrive(acc_empty + 8 * buf);
+                const int px = t.x0 + warp * 32 + lane, py = t.y0 + k;
+                if (px >= a.W) continue;
+                const size_t o = (((size_t)t.b * a.H + py) * a.W + px) * a.cout_g;
+#pragma unroll
+                for (int n = 0; n < N; ++n) v[n] += bias[n];
+                if (a.relu) {
+#pragma unroll
+                    for (int n = 0; n < N; ++n) v[n] = fmaxf(v[n], 0.f);
+                }
                 if (a.mask) {
-                    if (!(__bfloat162float(a.mask[o]) > 0.f)) v0 = 0.f;
-                    if (!(__bfloat162float(a.mask[o + 1]) > 0.f)) v1 = 0.f;
+#pragma unroll
+                    for (int q = 0; q < N / 8; ++q) {
+                        const uint4 m = *reinterpret_cast<const uint4*>(a.mask + o + 8 * q);
+                        const bf16* mb = reinterpret_cast<const bf16*>(&m);
+#pragma unroll
+                        for (int e = 0; e < 8; ++e)
+                            if (!(__bfloat162float(mb[e]) > 0.f)) v[8 * q + e] = 0.f;
+                    }
                 }
                 if (a.out) {
-                    if (co < a.n_out) a.out[o] = __float2bfloat16_rn(v0);
-                    if (co + 1 < a.n_out) a.out[o + 1] = __float2bfloat16_rn(v1);
+#pragma unroll
+                    for (int q = 0; q < N / 8; ++q) {
+                        if (8 * q >= a.n_out) break;
+                        __align__(16) bf16 h[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16_rn(v[8 * q + e]);
+                        *reinterpret_cast<uint4*>(a.out + o + 8 * q) = *reinterpret_cast<const uint4*>(h);
+                    }
                 }
                 if (a.out_f) {
-                    if (co < a.n_out) a.out_f[o] = v0;
-                    if (co + 1 < a.n_out) a.out_f[o + 1] = v1;
+#pragma unroll
+                    for (int q = 0; q < N / 4; ++q) {
+                        if (4 * q >= a.n_out) break;
+                        *reinterpret_cast<float4*>(a.out_f + o + 4 * q) =
+                            make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                    }
                 }
             }
         }
     }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)S::kTmemCols));
+    }
+    if (threadIdx.x == 0 && bad) atomicExch(a.err, 1);
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode_tiled = nullptr;
+
+static bool tensor_map_rows(CUtensorMap* m, const bf16* base, int C, int W, int H, int B)
+{
+    if (!g_encode_tiled) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        g_encode_tiled = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+    const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
+    const cuuint32_t box[4] = {8, (cuuint32_t)kTcCols, 1, 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    return g_encode_tiled(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(base), dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static int g_tc_sms = 0;
+
+template <int CIN, int N>
+static bool launch_conv_tc(const ConvArgs& a, cudaStream_t st)
+{
+    using S = TcShape<CIN, N>;
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_conv_tc<CIN, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmemBytes) !=
+            cudaSuccess)
+            return false;
+        attr = true;
+    }
+    if (g_tc_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&g_tc_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || g_tc_sms <= 0)
+            g_tc_sms = 152;
+    }
+    CUtensorMap m;
+    if (!tensor_map_rows(&m, a.in, CIN, a.W, a.H, a.B)) return false;
+    const int items = a.B * ((a.H + kTcRows - 1) / kTcRows) * ((a.W + kTcM - 1) / kTcM);
+    const int grid = std::min(items, 2 * g_tc_sms);
+    k_conv_tc<CIN, N><<<grid, kTcThreads, S::kSmemBytes, st>>>(m, a);
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -527,6 +848,7 @@ struct voldor_net {
     float* fbias = nullptr;
     float* loss = nullptr;
     float* align = nullptr;          // [8] scale alignment state
+    int* tc_err = nullptr;           // set by a convolution whose bounded wait expired
     unsigned* hist = nullptr;        // [2][kAlignBins]
     float* fsum = nullptr;           // [cap_bt] sum of |flow| per (image, frame)
     size_t cap_bt = 0;
@@ -587,16 +909,19 @@ void pack(voldor_net* n, cudaStream_t st)
     k_pack_weights<<<dim3(32, kNetLayers), 256, 0, st>>>(n->L, n->master, n->fw, n->bw, n->fbias);
 }
 
-void conv(int cin_pad, int ntiles, const ConvArgs& a, int B, cudaStream_t st)
+// Dispatch on (input channels, output channels rounded up to 16).
+bool conv(int cin_pad, int n_out_pad, const ConvArgs& a, cudaStream_t st)
 {
-    dim3 grid((a.W + kTileW - 1) / kTileW, (a.H + kTileH - 1) / kTileH, B);
-    if (cin_pad == 16 && ntiles == 4) k_conv3x3<16, 4><<<grid, 128, 0, st>>>(a);
-    else if (cin_pad == 32 && ntiles == 4) k_conv3x3<32, 4><<<grid, 128, 0, st>>>(a);
-    else if (cin_pad == 32 && ntiles == 1) k_conv3x3<32, 1><<<grid, 128, 0, st>>>(a);
+    if (a.cin_g != cin_pad) return false;
+    if (cin_pad == 16 && n_out_pad == 32) return launch_conv_tc<16, 32>(a, st);
+    if (cin_pad == 32 && n_out_pad == 32) return launch_conv_tc<32, 32>(a, st);
+    if (cin_pad == 32 && n_out_pad == 16) return launch_conv_tc<32, 16>(a, st);
+    return false;
 }
 
 // Forward pass of B images of H x W; predictions in n->pred (8 floats per pixel).
-void forward(voldor_net* n, const void* flows, int f16, int B, int H, int W, cudaStream_t st)
+// False if a convolution could not be launched.
+bool forward(voldor_net* n, const void* flows, int f16, int B, int H, int W, cudaStream_t st)
 {
     const size_t pix = (size_t)B * H * W;
     const size_t N = (size_t)H * W;
@@ -612,11 +937,13 @@ void forward(voldor_net* n, const void* flows, int f16, int B, int H, int W, cud
         a.in = in; a.cin_g = cin_g; a.w = n->fw + n->L.fw_off[l]; a.bias = n->fbias + l * kNetWidth;
         a.out = last ? nullptr : n->act[l]; a.out_f = last ? n->pred : nullptr;
         a.cout_g = last ? 8 : 32; a.n_out = last ? 8 : 32; a.mask = nullptr; a.relu = last ? 0 : 1; a.H = H; a.W = W;
-        conv(n->L.cin_pad[l], n->L.cout_pad[l] / 8, a, B, st);
+        a.B = B; a.w_rows = n->L.cout_pad[l]; a.err = n->tc_err;
+        if (!conv(n->L.cin_pad[l], last ? 16 : 32, a, st)) return false;
         if (last) break;
         in = n->act[l];
         cin_g = 32;
     }
+    return true;
 }
 
 void wgrad(voldor_net* n, int l, const bf16* in, int cin_g, const bf16* dout, int cout_g, int B, int H, int W, cudaStream_t st)
@@ -638,7 +965,7 @@ void wgrad(voldor_net* n, int l, const bf16* in, int cin_g, const bf16* dout, in
 }
 
 // Backward pass after forward(); target [pix][2] (log-depth, rigidness).
-void backward(voldor_net* n, const float* tgt, int B, int H, int W, float lam_r, cudaStream_t st)
+bool backward(voldor_net* n, const float* tgt, int B, int H, int W, float lam_r, cudaStream_t st)
 {
     const size_t pix = (size_t)B * H * W;
     cudaMemsetAsync(n->grad, 0, n->L.n_params * sizeof(float), st);
@@ -657,11 +984,27 @@ void backward(voldor_net* n, const float* tgt, int B, int H, int W, float lam_r,
         a.in = dout; a.cin_g = dout_g; a.w = n->bw + n->L.bw_off[l]; a.bias = nullptr;
         bf16* o = bufs[l & 1];
         a.out = o; a.out_f = nullptr; a.cout_g = 32; a.n_out = 32; a.mask = n->act[l - 1]; a.relu = 0; a.H = H; a.W = W;
+        a.B = B; a.w_rows = n->L.cin_pad[l]; a.err = n->tc_err;
         const int cout_b = n->L.cout_pad[l] < 16 ? 16 : n->L.cout_pad[l];
-        conv(cout_b, n->L.cin_pad[l] / 8, a, B, st);
+        if (!conv(cout_b, 32, a, st)) return false;
         dout = o;
         dout_g = 32;
     }
+    return true;
+}
+
+// Reads (synchronising the stream) and clears the convolutions' timeout flag.
+voldor_status net_status(voldor_net* n, cudaStream_t st)
+{
+    int e = 0;
+    if (!net_ok(cudaMemcpyAsync(&e, n->tc_err, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
+        !net_ok(cudaStreamSynchronize(st)))
+        return VOLDOR_ERR_CUDA;
+    if (e) {
+        cudaMemsetAsync(n->tc_err, 0, sizeof(int), st);
+        return VOLDOR_ERR_TIMEOUT;
+    }
+    return net_ok(cudaGetLastError()) ? VOLDOR_OK : VOLDOR_ERR_CUDA;
 }
 
 }  // namespace
@@ -688,9 +1031,10 @@ voldor_status voldor_net_create(int T, voldor_net** out)
               net_ok(cudaMalloc(&n->grad, P * 4)) && net_ok(cudaMalloc(&n->fw, n->L.n_fw * sizeof(bf16))) &&
               net_ok(cudaMalloc(&n->bw, n->L.n_bw * sizeof(bf16))) && net_ok(cudaMalloc(&n->fbias, kNetLayers * kNetWidth * 4)) &&
               net_ok(cudaMalloc(&n->loss, 4)) && net_ok(cudaMalloc(&n->align, 8 * sizeof(float))) &&
-              net_ok(cudaMalloc(&n->hist, 2 * kAlignBins * sizeof(unsigned)));
+              net_ok(cudaMalloc(&n->hist, 2 * kAlignBins * sizeof(unsigned))) && net_ok(cudaMalloc(&n->tc_err, sizeof(int)));
     if (ok) ok = net_ok(cudaMemset(n->master, 0, P * 4)) && net_ok(cudaMemset(n->m, 0, P * 4)) &&
-                 net_ok(cudaMemset(n->v, 0, P * 4)) && net_ok(cudaMemset(n->grad, 0, P * 4));
+                 net_ok(cudaMemset(n->v, 0, P * 4)) && net_ok(cudaMemset(n->grad, 0, P * 4)) &&
+                 net_ok(cudaMemset(n->tc_err, 0, sizeof(int)));
     if (!ok) {
         cudaGetLastError();
         voldor_net_destroy(n);
@@ -707,7 +1051,7 @@ void voldor_net_destroy(voldor_net* n)
     net_free_acts(n);
     cudaFree(n->master); cudaFree(n->m); cudaFree(n->v); cudaFree(n->grad);
     cudaFree(n->fw); cudaFree(n->bw); cudaFree(n->fbias); cudaFree(n->loss);
-    cudaFree(n->align); cudaFree(n->hist); cudaFree(n->fsum);
+    cudaFree(n->align); cudaFree(n->hist); cudaFree(n->fsum); cudaFree(n->tc_err);
     cudaGetLastError();
     delete n;
 }
@@ -745,10 +1089,10 @@ voldor_status voldor_net_forward(voldor_net* n, const void* flows, int flow_dtyp
     cudaStream_t st = (cudaStream_t)stream;
     voldor_status s = net_reserve(n, (size_t)B * H * W, (size_t)B * n->T);
     if (s != VOLDOR_OK) return s;
-    forward(n, flows, flow_dtype == VOLDOR_FLOW_F16, B, H, W, st);
+    if (!forward(n, flows, flow_dtype == VOLDOR_FLOW_F16, B, H, W, st)) return VOLDOR_ERR_CUDA;
     if (!net_ok(cudaMemcpyAsync(pred, n->pred, (size_t)B * H * W * 8 * sizeof(float), cudaMemcpyDeviceToDevice, st)))
         return VOLDOR_ERR_CUDA;
-    return net_ok(cudaGetLastError()) ? VOLDOR_OK : VOLDOR_ERR_CUDA;
+    return net_status(n, st);
 }
 
 voldor_status voldor_net_train_step(voldor_net* n, const void* flows, int flow_dtype, const float* target, int B, int H,
@@ -760,8 +1104,8 @@ voldor_status voldor_net_train_step(voldor_net* n, const void* flows, int flow_d
     cudaStream_t st = (cudaStream_t)stream;
     voldor_status s = net_reserve(n, (size_t)B * H * W, (size_t)B * n->T);
     if (s != VOLDOR_OK) return s;
-    forward(n, flows, flow_dtype == VOLDOR_FLOW_F16, B, H, W, st);
-    backward(n, target, B, H, W, lam_r, st);
+    if (!forward(n, flows, flow_dtype == VOLDOR_FLOW_F16, B, H, W, st) || !backward(n, target, B, H, W, lam_r, st))
+        return VOLDOR_ERR_CUDA;
     if (lr > 0.f) {
         n->step += 1;
         const float b1 = 0.9f, b2 = 0.999f;
@@ -771,8 +1115,7 @@ voldor_status voldor_net_train_step(voldor_net* n, const void* flows, int flow_d
         pack(n, st);
     }
     if (loss_host && !net_ok(cudaMemcpyAsync(loss_host, n->loss, 4, cudaMemcpyDeviceToHost, st))) return VOLDOR_ERR_CUDA;
-    if (!net_ok(cudaStreamSynchronize(st))) return VOLDOR_ERR_CUDA;
-    return net_ok(cudaGetLastError()) ? VOLDOR_OK : VOLDOR_ERR_CUDA;
+    return net_status(n, st);
 }
 
 }  // extern "C"
@@ -788,7 +1131,7 @@ voldor_status net_bootstrap(voldor_net* n, const void* flows, int f16, int W, in
     if (!flags) return VOLDOR_OK;
     voldor_status s = net_reserve(n, (size_t)W * H, (size_t)T);
     if (s != VOLDOR_OK) return s;
-    forward(n, flows, f16, 1, H, W, st);
+    if (!forward(n, flows, f16, 1, H, W, st)) return VOLDOR_ERR_CUDA;
     const int N = W * H;
     const unsigned nb = (unsigned)std::min(152 * 2, (N + 255) / 256);
     *kernels = 8 + 1;
@@ -804,6 +1147,6 @@ voldor_status net_bootstrap(voldor_net* n, const void* flows, int f16, int W, in
     k_net_to_state<<<(N + 255) / 256, 256, 0, st>>>(n->pred, 8, N, T, d_min, d_max, n->align,
                                                     depth ? theta : nullptr,
                                                     (flags & VOLDOR_LEARNED_RIGIDNESS) ? wmap : nullptr);
-    return net_ok(cudaGetLastError()) ? VOLDOR_OK : VOLDOR_ERR_CUDA;
+    return net_status(n, st);
 }
 }  // namespace vd

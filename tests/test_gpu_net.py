@@ -168,3 +168,73 @@ def test_learned_bootstrap_scale_alignment(vd):
     assert np.allclose(Wm, 1 / (1 + np.exp(0.4)), rtol=1e-6)
     net.destroy()
     win.destroy()
+
+
+def _emulated_at(params, x0, T, ys, xs):
+    """Emulated forward output at pixels (ys, xs) of the BF16 network input x0
+    [H][W][2T], each from its own 13 x 13 crop (six 3x3 layers see six pixels
+    to each side; the crop's zero border coincides with the image's)."""
+    layers = [(_bf16(W), b.astype(np.float32).astype(np.float64)) for W, b in cn.unpack(params, T)]
+    H, W = x0.shape[:2]
+    out = []
+    for y, x in zip(ys, xs):
+        y0, y1, x0_, x1 = max(0, y - 6), min(H, y + 7), max(0, x - 6), min(W, x + 7)
+        a = x0[y0:y1, x0_:x1]
+        for i, (Wl, b) in enumerate(layers):
+            a = cn.conv3x3(a, Wl, b)
+            if i < len(layers) - 1:
+                a = _bf16(np.maximum(a, 0.0))
+        out.append(a[y - y0, x - x0_])
+    return np.array(out)
+
+
+def test_forward_full_size_sampled(vd):
+    """8 images of 1242 x 375, T = 8, the launch shape of the proposal
+    benchmark (1920 row strips on a persistent grid): every image of the batch
+    bit-identical to its own single-image forward, and outputs at the strip
+    and row-chunk edges, image corners and interior points equal to the
+    emulated BF16 network on crops."""
+    import torch
+    T, H, W, B = 8, 375, 1242, 8
+    rng = np.random.default_rng(11)
+    params = cn.he_init(T, seed=11) + rng.normal(0, 0.02, size=cn.he_init(T, seed=11).shape).astype(np.float32)
+    flows = rng.normal(0, 12.0, size=(B, T, H, W, 2)).astype(np.float16)
+    net = vd.Net(T, params)
+    dev = torch.from_numpy(flows).cuda()
+    pred = net.forward(dev).cpu().numpy()
+    for k in (0, 5, 7):
+        one = net.forward(dev[k:k + 1].contiguous()).cpu().numpy()[0]
+        assert np.array_equal(one, pred[k]), k
+    ys = np.array([0, 1, 15, 16, 17, 200, 367, 368, 374])
+    xs = np.array([0, 1, 127, 128, 129, 640, 1151, 1152, 1241])
+    for k in (0, 7):
+        x0 = _bf16(cn.net_input(flows[k].astype(np.float64)))
+        yy, xx = np.meshgrid(ys, xs, indexing="ij")
+        ref = _emulated_at(params, x0, T, yy.ravel(), xx.ravel())
+        got = pred[k][yy.ravel(), xx.ravel(), :2]
+        assert _rel(got, ref) < 2e-3, _rel(got, ref)
+    net.destroy()
+
+
+def test_gradients_batch_consistency(vd):
+    """Two images of 1242 x 375 (480 row strips, more than one per CTA): the
+    batch gradient equals the mean of the single-image gradients (the loss is
+    a mean over pixels), up to FP32 atomic summation order."""
+    import torch
+    T, H, W = 2, 375, 1242
+    rng = np.random.default_rng(5)
+    params = cn.he_init(T, seed=5) + rng.normal(0, 0.02, size=cn.he_init(T, seed=5).shape).astype(np.float32)
+    flows = rng.normal(0, 12.0, size=(2, T, H, W, 2)).astype(np.float32)
+    target = np.stack([rng.normal(1.5, 0.5, size=(2, H, W)), rng.uniform(0, 1, size=(2, H, W))], -1).astype(np.float32)
+    net = vd.Net(T, params)
+    f, t = torch.from_numpy(flows).cuda(), torch.from_numpy(target).cuda()
+    net.train_step(f, t, lr=0.0, lam_r=0.5)
+    g = net.get_grads().astype(np.float64)
+    gs = []
+    for k in range(2):
+        net.train_step(f[k:k + 1].contiguous(), t[k:k + 1].contiguous(), lr=0.0, lam_r=0.5)
+        gs.append(net.get_grads().astype(np.float64))
+    mean = 0.5 * (gs[0] + gs[1])
+    for (key, a), (_, r) in zip(_blocks(T, g), _blocks(T, mean)):
+        assert _rel(a, r) < 1e-3, (key, _rel(a, r))
+    net.destroy()
