@@ -2,9 +2,10 @@
 // (2T -> 32 -> 32 -> 32 -> 32 -> 32 -> 2, ReLU between layers) that reads the
 // flow stack of a window and predicts, per pixel of I_0, a log-depth and a
 // rigidness logit used in place of the triangulation bootstrap. BF16
-// activations and weights, FP32 accumulation, tensor cores (mma.sync
-// m16n8k16 with ldmatrix operand loads) for the forward pass, the input
-// gradient and the weight gradient; FP32 Adam on master weights.
+// activations and weights, FP32 accumulation: the convolutions of the forward
+// pass and of the input gradient on tcgen05 (TMEM accumulators, TMA row
+// loads), the weight gradient on mma.sync m16n8k16 with ldmatrix operand
+// loads; FP32 Adam on master weights.
 //
 // Input: the flows of each frame divided by that frame's mean flow magnitude
 // (the network sees the shape of the flow field, not its overall size).
@@ -609,8 +610,12 @@ __global__ void __launch_bounds__(128) k_conv_wgrad(WgradArgs a)
 // ---------------------------------------------------------------------------
 // Input packing, loss, parameter packing, Adam, proposal output.
 // ---------------------------------------------------------------------------
-// Sum of |flow| per (image, frame): grid (blocks, B*T), one atomic per block.
-__global__ void k_flow_norm_sum(const void* flows, int f16, size_t N, float* sums)
+// Sum of |flow| per (image, frame), deterministic: grid (kNormBlocks, B*T);
+// each block writes its partial sum, k_flow_norm_fold adds a frame's
+// partials in a fixed order.
+constexpr int kNormBlocks = 64;
+
+__global__ void k_flow_norm_sum(const void* flows, int f16, size_t N, float* partial)
 {
     const int bt = blockIdx.y;
     float s = 0.f;
@@ -626,8 +631,17 @@ __global__ void k_flow_norm_sum(const void* flows, int f16, size_t N, float* sum
     if (threadIdx.x == 0) {
         float t = 0.f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
-        atomicAdd(sums + bt, t);
+        partial[(size_t)bt * kNormBlocks + blockIdx.x] = t;
     }
+}
+
+// One warp per (image, frame): sums[bt] = sum of the kNormBlocks partials.
+__global__ void k_flow_norm_fold(const float* partial, float* sums)
+{
+    const int bt = blockIdx.x;
+    float s = partial[(size_t)bt * kNormBlocks + threadIdx.x] + partial[(size_t)bt * kNormBlocks + threadIdx.x + 32];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) sums[bt] = s;
 }
 
 __global__ void k_pack_input(const void* flows, int f16, int T, int H, int W, int B, const float* sums, bf16* in0)
@@ -850,7 +864,7 @@ struct voldor_net {
     float* align = nullptr;          // [8] scale alignment state
     int* tc_err = nullptr;           // set by a convolution whose bounded wait expired
     unsigned* hist = nullptr;        // [2][kAlignBins]
-    float* fsum = nullptr;           // [cap_bt] sum of |flow| per (image, frame)
+    float* fsum = nullptr;           // [cap_bt] sum of |flow| per (image, frame), then [cap_bt][kNormBlocks] partials
     size_t cap_bt = 0;
     int step = 0;
     size_t cap_pix = 0;
@@ -883,7 +897,7 @@ voldor_status net_reserve(voldor_net* n, size_t pix, size_t bt)
         cudaFree(n->fsum);
         n->fsum = nullptr;
         n->cap_bt = 0;
-        if (!net_ok(cudaMalloc(&n->fsum, bt * sizeof(float)))) {
+        if (!net_ok(cudaMalloc(&n->fsum, bt * (1 + kNormBlocks) * sizeof(float)))) {
             cudaGetLastError();
             return VOLDOR_ERR_OOM;
         }
@@ -925,9 +939,9 @@ bool forward(voldor_net* n, const void* flows, int f16, int B, int H, int W, cud
 {
     const size_t pix = (size_t)B * H * W;
     const size_t N = (size_t)H * W;
-    cudaMemsetAsync(n->fsum, 0, (size_t)B * n->T * sizeof(float), st);
-    const unsigned nb = (unsigned)std::min<size_t>((N + 255) / 256, 64);
-    k_flow_norm_sum<<<dim3(nb, B * n->T), 256, 0, st>>>(flows, f16, N, n->fsum);
+    float* partial = n->fsum + n->cap_bt;
+    k_flow_norm_sum<<<dim3(kNormBlocks, B * n->T), 256, 0, st>>>(flows, f16, N, partial);
+    k_flow_norm_fold<<<B * n->T, 32, 0, st>>>(partial, n->fsum);
     k_pack_input<<<(unsigned)((pix + 255) / 256), 256, 0, st>>>(flows, f16, n->T, H, W, B, n->fsum, n->in0);
     const bf16* in = n->in0;
     int cin_g = 16;
@@ -1134,7 +1148,7 @@ voldor_status net_bootstrap(voldor_net* n, const void* flows, int f16, int W, in
     if (!forward(n, flows, f16, 1, H, W, st)) return VOLDOR_ERR_CUDA;
     const int N = W * H;
     const unsigned nb = (unsigned)std::min(152 * 2, (N + 255) / 256);
-    *kernels = 8 + 1;
+    *kernels = 9 + 1;            // forward (norm sum, fold, packing, 6 convolutions), to_state
     const bool depth = flags & VOLDOR_LEARNED_DEPTH;
     if (depth) {
         cudaMemsetAsync(n->hist, 0, 2 * kAlignBins * sizeof(unsigned), st);

@@ -125,7 +125,6 @@ __global__ void k_prep_count(DevParams p, DevState s, int t)
     }
     const int cnt = __syncthreads_count(valid);
     if (threadIdx.x == 0) s.pix_block_count[blockIdx.x] = cnt;
-    if (blockIdx.x == 0 && threadIdx.x < 8) s.pix_bounds[threadIdx.x] = 0.f;
 }
 
 __global__ void k_prep_write(DevParams p, DevState s, int t)
@@ -167,14 +166,6 @@ __global__ void k_prep_write(DevParams p, DevState s, int t)
                           (float)(p.fxd * p.fxd) * fc.mu_over_beta);
         r.c = make_float4(s.wmap[(size_t)(t - 1) * p.N + j], 0.f, 0.f, 0.f);
         s.pix[base + rank] = r;
-        // frame bounds for the dense scoring's fast path (non-negative floats
-        // order like their bit patterns)
-        int* b = reinterpret_cast<int*>(s.pix_bounds);
-        atomicMax(b + 0, __float_as_int(fabsf(r.a.x)));
-        atomicMax(b + 1, __float_as_int(fabsf(r.a.y)));
-        atomicMax(b + 2, __float_as_int(fabsf(r.a.z)));
-        atomicMax(b + 3, __float_as_int(fabsf(r.a.w)));
-        atomicMax(b + 4, __float_as_int(fabsf(r.b.x)));
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
         int tot = base;

@@ -1,22 +1,28 @@
 // Dense hypothesis scoring: for every P3P hypothesis h of frame t,
 //   L_h = sum_j W_t^j log[rho_j(h) / (rho_j(h) + mu_j)]
 // over the pixels whose pi_{t-1} is valid -- the MIE criterion of Eq. 10 with
-// the pose as the free variable. Arithmetic-bound on the SFU (MUFU) and FP32
-// pipes.
+// the pose as the free variable (Eq. 9's MLE form as the ablation variant).
 //
 // Per pair, with the pixel record (xb, yb2, w, ut, vt, beta, beta_k, Cp, wq)
 // and the hypothesis in scaled form (E, tt):
 //   a    = E (xb, yb2, 1) + tt w                (camera-t point / z_{t-1} - p)
 //   r_u  = (a_x - xb a_z) / (1 + a_z) - ut      (residual / fx, no cancellation
 //   r_v  = (a_y - yb2 a_z) / (1 + a_z) - vt      against the pixel position)
-//   xs   = r_u^2 + r_v^2                        (squared residual / fx^2)
+//   xs   = r_u^2 + r_v^2, clamped to [xs_min, xs_max]  (squared residual / fx^2)
 //   s    = beta log2(xs) + beta_k               (log2 of (x/alpha)^beta)
 //   r    = Cp xs (2^s + 2 + 2^-s)               (= mu / rho, Eqs. 3-4, 7)
-//   ell  = -log1p(r)
-// MUFU work: rcp, lg2, ex2, ex2, lg2 (for r >= 1/4); log1p(r) for r < 1/4 is
-// a polynomial on the FMA pipe, because lg2 near 1 has only absolute
-// accuracy. Each thread carries 8 hypotheses (instruction-level parallelism
-// over occupancy); sums are FP32 per 256-pixel tile, then FP64.
+//   ell  = -log1p(r); behind camera t (1 + a_z <= 0) rho := mu, ell = -log 2.
+// SFU work: rcp, lg2, ex2, ex2, lg2 (for r >= 1/4); log1p(r) for r < 1/4 is a
+// polynomial on the FMA pipe, because lg2 near 1 has only absolute accuracy.
+//
+// The FP32 add / mul / fma work runs on packed pairs: two hypotheses share a
+// 64-bit register pair and one .f32x2 instruction does both lanes, which
+// halves the issue slots of the FMA-pipe work (the pipe still does 128 lane
+// operations per SM clock, and it is what bounds this kernel). Each thread
+// carries 4 pairs (8 hypotheses, instruction-level parallelism over
+// occupancy); pixel records are bulk-copied into shared memory tile by tile
+// and expanded there into both lanes; sums are FP32 per 256-pixel tile, then
+// FP64.
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -66,13 +72,11 @@ __device__ __forceinline__ float log2_1p_pos(float r)
     return r < 0.25f ? small : big;
 }
 
-// -ell / ln2 = log2(1 + mu/rho) of one (hypothesis, pixel) pair; 1 (log2 of
-// 2) behind camera t. The checked form tests 1 + a_z > 0 and caps the squared
-// residual at xs_max; the fast form is used only for hypotheses whose frame
-// bounds prove both unnecessary (hyp_is_safe).
-// Per pair: log2(1 + r) with r = mu / rho (MIE, Eq. 10: ell = -ln2 * this),
-// or, with kMLE, log2(r) (MLE, Eq. 9: log rho - log mu = -ln2 * this); behind
-// camera t, rho := mu (r = 1).
+// Scalar pair term (the allocation-free entry point's form): -ell / ln2 =
+// log2(1 + mu/rho) of one (hypothesis, pixel) pair (MIE, Eq. 10), or with kMLE
+// log2(r) (MLE, Eq. 9: log rho - log mu = -ln2 * this); behind camera t,
+// rho := mu (r = 1). The checked form tests 1 + a_z > 0 and caps the squared
+// residual at xs_max.
 template <bool kChecked, bool kMLE = false>
 __device__ __forceinline__ float pair_term2(const HypF& h, const float4 a, const float4 b, float xs_min, float xs_max)
 {
@@ -92,22 +96,6 @@ __device__ __forceinline__ float pair_term2(const HypF& h, const float4 a, const
     const float v = kMLE ? mufu_lg2(r) : log2_1p_pos(r);
     if (kChecked) return den > 0.f ? v : (kMLE ? 0.f : 1.f);
     return v;
-}
-
-// A hypothesis is safe for a frame if, for every record within the frame
-// bounds (|xb| <= bx, |yb2| <= by, 0 < w <= bw, |ut| <= bu, |vt| <= bv),
-// 1 + a_z >= 1/4 and the squared residual stays below xs_max; then the checks
-// of the pair term cannot change its value.
-__device__ __forceinline__ bool hyp_is_safe(const HypF& h, const float* bd, float xs_max)
-{
-    const float bx = bd[0], by = bd[1], bw = bd[2], bu = bd[3], bv = bd[4];
-    const float az_max = fabsf(h.e6) * bx + fabsf(h.e7) * by + fabsf(h.e8) + fabsf(h.t2) * bw;
-    const float ax_max = fabsf(h.e0) * bx + fabsf(h.e1) * by + fabsf(h.e2) + fabsf(h.t0) * bw;
-    const float ay_max = fabsf(h.e3) * bx + fabsf(h.e4) * by + fabsf(h.e5) + fabsf(h.t1) * bw;
-    if (!(az_max <= 0.75f)) return false;               // 1 + a_z >= 1/4, so 1/(1 + a_z) <= 4
-    const float ru = 4.f * (ax_max + bx * az_max) + bu;
-    const float rv = 4.f * (ay_max + by * az_max) + bv;
-    return ru * ru + rv * rv < 0.5f * xs_max;
 }
 
 // Bulk-copy staging of pixel-record tiles: one thread issues
@@ -153,25 +141,162 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return false;
 }
 
-// HPT hypotheses per thread (the hypothesis side of the tile, HPT * 256 per
-// block); MINB resident blocks per SM. The autotuner picks among the instances.
-template <int HPT, int MINB, bool MLE>
+// ---------------------------------------------------------------------------
+// Packed pair arithmetic (.f32x2) and the packed pair term.
+// ---------------------------------------------------------------------------
+typedef unsigned long long f2;      // {lo, hi} FP32 lanes
+
+__device__ __forceinline__ f2 f2_pack(float lo, float hi)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ float f2_lo(f2 v)
+{
+    float lo;
+    asm("mov.b64 {%0, _}, %1;" : "=f"(lo) : "l"(v));
+    return lo;
+}
+
+__device__ __forceinline__ float f2_hi(f2 v)
+{
+    float hi;
+    asm("mov.b64 {_, %0}, %1;" : "=f"(hi) : "l"(v));
+    return hi;
+}
+
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b)
+{
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b)
+{
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b)
+{
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f2 f2_lg2(f2 v) { return f2_pack(mufu_lg2(f2_lo(v)), mufu_lg2(f2_hi(v))); }
+
+// c >= 0 ? a : b, one instruction per lane
+__device__ __forceinline__ float slct(float a, float b, float c)
+{
+    float d;
+    asm("slct.f32.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// A hypothesis pair in packed form: the rows of a_x and a_y negated, a_z as is.
+struct HypX2 {
+    f2 x0, x1, x2, xt, y0, y1, y2, yt, z0, z1, z2, zt;
+};
+
+// Pixel record expanded in shared memory: each field in both lanes.
+struct PixX2 {
+    f2 xb, yb2, w, ut, vt, beta, beta_k, Cp, wq, pad;
+};
+static_assert(sizeof(PixX2) == 80, "PixX2 is five 16-byte words");
+
+
+// log2(1 + r) (MIE) or log2(r) (MLE) for two hypotheses against one pixel;
+// the packed form of pair_term2<false, MLE>, with the residual's sign flipped
+// (it is squared).
+// log2(1 + r) (MIE) or log2(r) (MLE) of two hypotheses against one pixel,
+// with the checks of pair_term2<true>; the residual's sign is flipped (it is
+// squared).
+template <bool kMLE>
+__device__ __forceinline__ f2 pair_x2(const HypX2& h, const PixX2& q, float xs_min, float xs_max)
+{
+    const f2 ONE = f2_pack(1.f, 1.f), TWO = f2_pack(2.f, 2.f);
+    const f2 nax = f2_fma(h.x0, q.xb, f2_fma(h.x1, q.yb2, f2_fma(h.xt, q.w, h.x2)));   // -a_x
+    const f2 nay = f2_fma(h.y0, q.xb, f2_fma(h.y1, q.yb2, f2_fma(h.yt, q.w, h.y2)));   // -a_y
+    const f2 az = f2_fma(h.z0, q.xb, f2_fma(h.z1, q.yb2, f2_fma(h.zt, q.w, h.z2)));
+    const f2 mu = f2_fma(q.xb, az, nax);         // xb a_z - a_x
+    const f2 mv = f2_fma(q.yb2, az, nay);
+    const f2 nden = f2_sub(f2_pack(-1.f, -1.f), az);                     // -(1 + a_z), exactly
+    const f2 rd = f2_pack(mufu_rcp(-f2_lo(nden)), mufu_rcp(-f2_hi(nden)));
+    const f2 ru = f2_fma(mu, rd, q.ut);          // -(residual u) / fx
+    const f2 rv = f2_fma(mv, rd, q.vt);
+    f2 xs = f2_fma(ru, ru, f2_mul(rv, rv));
+    xs = f2_pack(fminf(fmaxf(f2_lo(xs), xs_min), xs_max), fminf(fmaxf(f2_hi(xs), xs_min), xs_max));
+    const f2 sg = f2_fma(q.beta, f2_lg2(xs), q.beta_k);
+    const float s0 = f2_lo(sg), s1 = f2_hi(sg);
+    const f2 ep = f2_pack(mufu_ex2(s0), mufu_ex2(s1)), en = f2_pack(mufu_ex2(-s0), mufu_ex2(-s1));
+    const f2 r = f2_mul(f2_mul(q.Cp, xs), f2_add(ep, f2_add(en, TWO)));
+    const float behind = kMLE ? 0.f : 1.f;       // 1 + a_z <= 0: rho := mu
+    if (kMLE) {
+        const f2 v = f2_lg2(r);
+        return f2_pack(slct(behind, f2_lo(v), f2_lo(nden)), slct(behind, f2_hi(v), f2_hi(nden)));
+    }
+    f2 ps = f2_fma(r, f2_pack(1.784831882e-01f, 1.784831882e-01f), f2_pack(-3.390570283e-01f, -3.390570283e-01f));
+    ps = f2_fma(r, ps, f2_pack(4.790599346e-01f, 4.790599346e-01f));
+    ps = f2_fma(r, ps, f2_pack(-7.212913036e-01f, -7.212913036e-01f));
+    ps = f2_fma(r, ps, f2_pack(1.442694783e+00f, 1.442694783e+00f));
+    const f2 small = f2_mul(r, ps);
+    const f2 big = f2_lg2(f2_add(r, ONE));
+    const f2 d = f2_add(r, f2_pack(-0.25f, -0.25f));
+    const float v0 = slct(f2_lo(big), f2_lo(small), f2_lo(d)), v1 = slct(f2_hi(big), f2_hi(small), f2_hi(d));
+    return f2_pack(slct(behind, v0, f2_lo(nden)), slct(behind, v1, f2_hi(nden)));
+}
+
+// One shared-memory tile against the first NS hypothesis pairs of the thread.
+template <int NS, bool MLE>
+__device__ __forceinline__ void score_tile(const HypX2* hy, const PixX2* xt, int cnt, float xs_min, float xs_max,
+                                           f2* facc)
+{
+    for (int q = 0; q < cnt; ++q) {
+        const PixX2 px = xt[q];
+#pragma unroll
+        for (int k = 0; k < NS; ++k) facc[k] = f2_fma(px.wq, pair_x2<MLE>(hy[k], px, xs_min, xs_max), facc[k]);
+    }
+}
+
+// SLOTS hypothesis pairs per thread (the hypothesis side of the tile is
+// 2 * SLOTS * 256 per block: pair k holds hypotheses tile0 + 2k * 256 + tid and
+// tile0 + (2k + 1) * 256 + tid); MINB resident blocks per SM. Pairs wholly past
+// the frame's hypothesis count are skipped (block-uniform), so a partial tile
+// costs at most 511 idle hypotheses. The autotuner picks among the instances.
+template <int SLOTS, int MINB, bool MLE>
 __global__ void __launch_bounds__(kScoreThreads, MINB) k_score(DevParams p, DevState s, int log_idx)
 {
+    constexpr int HPT = 2 * SLOTS;
     const int n_hyp = *s.n_hyp;
     const int n_pix = *s.pix_count;
     if (log_idx >= 0 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
         s.score_log[2 * log_idx] = n_hyp;
         s.score_log[2 * log_idx + 1] = n_pix;
     }
-    const int tile0 = blockIdx.x * (kScoreThreads * HPT);
+    // tile-major block order: the partial last hypothesis tile's (lighter)
+    // blocks are scheduled after every full tile's, so they fill the last wave
+    const int blk = blockIdx.x + gridDim.x * blockIdx.y;
+    const int n_chunks = gridDim.y, chunk = blk % n_chunks;
+    const int tile0 = (blk / n_chunks) * (kScoreThreads * HPT);
     if (tile0 >= n_hyp) return;
-    const int chunk = blockIdx.y, n_chunks = gridDim.y;
     const long long lo = (long long)n_pix * chunk / n_chunks;
     const long long hi = (long long)n_pix * (chunk + 1) / n_chunks;
     const int n_tiles = (int)((hi - lo + kTilePix - 1) / kTilePix);
 
     __shared__ __align__(128) float4 tile[kStages][kTilePix * 3];
+    __shared__ __align__(16) PixX2 xt[kTilePix];
     __shared__ __align__(8) uint64_t full[kStages];
     __shared__ int timed_out;
     const float4* gpix = reinterpret_cast<const float4*>(s.pix);
@@ -192,63 +317,66 @@ __global__ void __launch_bounds__(kScoreThreads, MINB) k_score(DevParams p, DevS
     if (threadIdx.x == 0)
         for (int i = 0; i < kStages && i < n_tiles; ++i) issue(i);
 
-    HypF hy[HPT];
+    HypX2 hy[SLOTS];
+    {
 #pragma unroll
-    for (int i = 0; i < HPT; ++i) {
-        const int h = tile0 + i * kScoreThreads + threadIdx.x;
-        const float* f = s.hyp_f32 + (size_t)min(h, n_hyp - 1) * 12;
-        hy[i] = HypF{f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7], f[8], f[9], f[10], f[11]};
+        for (int k = 0; k < SLOTS; ++k) {
+            HypF a[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int h = tile0 + (2 * k + u) * kScoreThreads + threadIdx.x;
+                const float* f = s.hyp_f32 + (size_t)min(h, n_hyp - 1) * 12;
+                a[u] = HypF{f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7], f[8], f[9], f[10], f[11]};
+            }
+            hy[k] = HypX2{f2_pack(-a[0].e0, -a[1].e0), f2_pack(-a[0].e1, -a[1].e1), f2_pack(-a[0].e2, -a[1].e2),
+                          f2_pack(-a[0].t0, -a[1].t0), f2_pack(-a[0].e3, -a[1].e3), f2_pack(-a[0].e4, -a[1].e4),
+                          f2_pack(-a[0].e5, -a[1].e5), f2_pack(-a[0].t1, -a[1].t1), f2_pack(a[0].e6, a[1].e6),
+                          f2_pack(a[0].e7, a[1].e7), f2_pack(a[0].e8, a[1].e8), f2_pack(a[0].t2, a[1].t2)};
+        }
     }
     double acc[HPT];
 #pragma unroll
     for (int i = 0; i < HPT; ++i) acc[i] = 0.0;
     const float xs_min = p.xs_min, xs_max = p.xs_max;
-    bool safe = true;
-    {
-        float bd[5];
-        for (int q = 0; q < 5; ++q) bd[q] = s.pix_bounds[q];
-#pragma unroll
-        for (int i = 0; i < HPT; ++i) safe = safe && hyp_is_safe(hy[i], bd, xs_max);
-    }
-    const bool warp_safe = __all_sync(0xffffffffu, safe);
+    const int ns = min(SLOTS, (n_hyp - tile0 + 2 * kScoreThreads - 1) / (2 * kScoreThreads));
 
     int it = 0;
     for (; it < n_tiles; ++it) {
         const int slot = it % kStages;
         if (!mbar_wait_bounded(&full[slot], (uint32_t)((it / kStages) & 1))) atomicExch(&timed_out, 1);
-        __syncthreads();
-        if (timed_out) break;
         const int cnt = (int)min((long long)kTilePix, hi - (lo + (long long)it * kTilePix));
-        const float4* t4 = &tile[slot][0];
-        float facc[HPT];
-#pragma unroll
-        for (int i = 0; i < HPT; ++i) facc[i] = 0.f;
-        if (warp_safe) {
-            for (int q = 0; q < cnt; ++q) {
-                const float4 a = t4[3 * q];
-                const float4 b = t4[3 * q + 1];
-                const float wq = reinterpret_cast<const float*>(t4 + 3 * q + 2)[0];
-#pragma unroll
-                for (int i = 0; i < HPT; ++i)
-                    facc[i] = fmaf(wq, pair_term2<false, MLE>(hy[i], a, b, xs_min, xs_max), facc[i]);
-            }
-        } else {
-            for (int q = 0; q < cnt; ++q) {
-                const float4 a = t4[3 * q];
-                const float4 b = t4[3 * q + 1];
-                const float wq = reinterpret_cast<const float*>(t4 + 3 * q + 2)[0];
-#pragma unroll
-                for (int i = 0; i < HPT; ++i)
-                    facc[i] = fmaf(wq, pair_term2<true, MLE>(hy[i], a, b, xs_min, xs_max), facc[i]);
-            }
+        if ((int)threadIdx.x < cnt) {
+            // expand record threadIdx.x into both lanes (a timed-out tile's
+            // contents are never used)
+            const float4* r = &tile[slot][3 * threadIdx.x];
+            const float4 a = r[0], b = r[1];
+            const float wq = r[2].x;
+            float4* x = reinterpret_cast<float4*>(&xt[threadIdx.x]);
+            x[0] = make_float4(a.x, a.x, a.y, a.y);
+            x[1] = make_float4(a.z, a.z, a.w, a.w);
+            x[2] = make_float4(b.x, b.x, b.y, b.y);
+            x[3] = make_float4(b.z, b.z, b.w, b.w);
+            x[4] = make_float4(wq, wq, 0.f, 0.f);
         }
-#pragma unroll
-        for (int i = 0; i < HPT; ++i) acc[i] += (double)facc[i];
-        __syncthreads();                       // every thread is done with this slot
+        __syncthreads();                       // tile expanded; the raw slot is free
+        if (timed_out) break;
         if (threadIdx.x == 0 && it + kStages < n_tiles) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             issue(it + kStages);
         }
+        f2 facc[SLOTS];
+#pragma unroll
+        for (int k = 0; k < SLOTS; ++k) facc[k] = 0ull;
+        if (ns >= SLOTS) score_tile<SLOTS, MLE>(hy, xt, cnt, xs_min, xs_max, facc);
+        else if (SLOTS > 3 && ns == 3) score_tile<(SLOTS > 3 ? 3 : 1), MLE>(hy, xt, cnt, xs_min, xs_max, facc);
+        else if (SLOTS > 2 && ns == 2) score_tile<(SLOTS > 2 ? 2 : 1), MLE>(hy, xt, cnt, xs_min, xs_max, facc);
+        else score_tile<1, MLE>(hy, xt, cnt, xs_min, xs_max, facc);
+#pragma unroll
+        for (int k = 0; k < SLOTS; ++k) {
+            acc[2 * k] += (double)f2_lo(facc[k]);
+            acc[2 * k + 1] += (double)f2_hi(facc[k]);
+        }
+        __syncthreads();                       // every thread is done with the expanded tile
     }
     if (timed_out) {
         // drain the copies this block issued (bounded) before leaving
@@ -314,12 +442,12 @@ void launch_score(const DevParams& p, const DevState& s, int log_idx, cudaStream
     const int li = log_idx < kScoreLogMax ? log_idx : -1;
     if (s.score_hpt == 4) {
         dim3 grid((p.S + kScoreThreads * 4 - 1) / (kScoreThreads * 4), s.n_chunks);
-        if (p.criterion == VOLDOR_CRITERION_MLE) k_score<4, 2, true><<<grid, kScoreThreads, 0, st>>>(p, s, li);
-        else k_score<4, 2, false><<<grid, kScoreThreads, 0, st>>>(p, s, li);
+        if (p.criterion == VOLDOR_CRITERION_MLE) k_score<2, 2, true><<<grid, kScoreThreads, 0, st>>>(p, s, li);
+        else k_score<2, 2, false><<<grid, kScoreThreads, 0, st>>>(p, s, li);
     } else {
         dim3 grid((p.S + kScoreThreads * 8 - 1) / (kScoreThreads * 8), s.n_chunks);
-        if (p.criterion == VOLDOR_CRITERION_MLE) k_score<8, 1, true><<<grid, kScoreThreads, 0, st>>>(p, s, li);
-        else k_score<8, 1, false><<<grid, kScoreThreads, 0, st>>>(p, s, li);
+        if (p.criterion == VOLDOR_CRITERION_MLE) k_score<4, 1, true><<<grid, kScoreThreads, 0, st>>>(p, s, li);
+        else k_score<4, 1, false><<<grid, kScoreThreads, 0, st>>>(p, s, li);
     }
 }
 

@@ -68,7 +68,6 @@ struct DevState {
     PixRec* pix;              // [N] compacted valid pixels of the current frame
     int* pix_block_count;     // [ceil(N / kPixThreads)]
     int* pix_count;           // [1]
-    float* pix_bounds;        // [8] max |xb|, |yb2|, w, |ut|, |vt| over the current frame's records
     // P3P
     double* grp_sols;         // [G][4][12]
     double* grp_weight;       // [G]
