@@ -35,7 +35,7 @@ class Params(C.Structure):
         ("x_min", C.c_double), ("x_max", C.c_double), ("beta_min", C.c_double),
         ("ms_tol", C.c_double),
         ("hyps_per_frame", C.c_int), ("groups_per_frame", C.c_int),
-        ("ms_max_iter", C.c_int), ("criterion", C.c_int),
+        ("ms_max_iter", C.c_int), ("criterion", C.c_int), ("residual", C.c_int),
         ("seed", C.c_uint64), ("window_id", C.c_uint64),
     ]
 
@@ -68,6 +68,7 @@ def lib():
         sig = {
             "or_philox4x64_10": (None, [P(u64), P(u64), P(u64)]),
             "or_fisk_logpdf": (d, [d, d, d]),
+            "or_gauss_logpdf": (d, [d, d]),
             "or_fisk_params": (None, [P(Params), d, P(d), P(d)]),
             "or_frame_ell": (d, [W, i, i, d, P(i)]),
             "or_frame_crit": (d, [W, i, i, d]),
@@ -299,6 +300,12 @@ def philox4x64_10(ctr, key):
 
 def fisk_logpdf(x, log_alpha, beta):
     return lib().or_fisk_logpdf(float(x), float(log_alpha), float(beta))
+
+
+def gauss_logpdf(x, log_alpha):
+    """Log density of the squared EPE under the Gaussian residual model with
+    the Fisk median alpha = exp(log_alpha)."""
+    return lib().or_gauss_logpdf(float(x), float(log_alpha))
 
 
 def p3p(P, b):

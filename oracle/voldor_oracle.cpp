@@ -45,6 +45,7 @@ typedef struct {
     int groups_per_frame;         // G: Philox groups drawn per frame (draw budget)
     int ms_max_iter;              // meanshift iteration cap
     int criterion;                // 0: MIE (Eq. 10), 1: MLE (Eq. 9)
+    int residual;                 // 0: Fisk (Eqs. 3-6), 1: Gaussian (the ablation's alternative model)
     uint64_t seed, window_id;     // Philox key
 } or_params;
 
@@ -125,6 +126,17 @@ void or_fisk_params(const or_params* p, double n, double* log_alpha, double* bet
 {
     *log_alpha = std::log(p->a1) + p->a2 * n;
     *beta = std::max(p->b1 * n + p->b2, p->beta_min);
+}
+
+// Gaussian residual model of the ablation study (Sec. 6.4): the 2-D flow
+// residual isotropic normal, so the squared EPE x is exponential with mean
+// 2 sigma^2. The paper gives no parameters for it; reading: sigma^2(n) is
+// matched to the Fisk model at the same flow magnitude by the median of x,
+// i.e. 2 sigma^2 ln 2 = alpha(n) (the Fisk median), so
+//   log rho = log(ln 2 / alpha) - x ln 2 / alpha.
+double or_gauss_logpdf(double x, double log_alpha)
+{
+    return std::log(std::log(2.0)) - log_alpha - x * std::log(2.0) * std::exp(-log_alpha);
 }
 
 static double clamp_x(const or_params* p, double x)
@@ -286,8 +298,14 @@ static FrameEval eval_frame(const or_window* w, const double Cprev[12], const do
     double n = std::sqrt(e.vob[0] * e.vob[0] + e.vob[1] * e.vob[1]);
     double log_alpha, beta;
     or_fisk_params(&w->p, n, &log_alpha, &beta);
-    e.log_rho = or_fisk_logpdf(xsq, log_alpha, beta);                          // Eq. 3
-    e.log_mu = or_fisk_logpdf(clamp_x(&w->p, w->p.lambda_ * w->p.lambda_ * n * n), log_alpha, beta);  // Eq. 7
+    const double x_mu = clamp_x(&w->p, w->p.lambda_ * w->p.lambda_ * n * n);      // Eq. 7
+    if (w->p.residual == 1) {
+        e.log_rho = or_gauss_logpdf(xsq, log_alpha);
+        e.log_mu = or_gauss_logpdf(x_mu, log_alpha);
+    } else {
+        e.log_rho = or_fisk_logpdf(xsq, log_alpha, beta);                      // Eq. 3
+        e.log_mu = or_fisk_logpdf(x_mu, log_alpha, beta);
+    }
     e.ell = mie_term(e.log_rho, e.log_mu);
     e.crit = crit_term(&w->p, true, e.log_rho, e.log_mu);
     return e;
