@@ -58,6 +58,8 @@ def parse_args():
     ap.add_argument("--workers", type=int, default=0, help="scene-generator processes (0: cpu count - 1)")
     ap.add_argument("--save-weights", default="")
     ap.add_argument("--weights", default="", help="with --learned: evaluate these weights instead of training")
+    ap.add_argument("--net", type=int, default=0,
+                    help="time the proposal network instead: forward passes on this many 1242x375 T=8 flow stacks")
     return ap.parse_args()
 
 
@@ -434,6 +436,79 @@ def run_batch(args):
         g.destroy()
 
 
+def measured_peaks():
+    """The measured HBM copy bandwidth (GB/s) and bf16 GEMM rate
+    (TFLOP/s, burst) of this GPU model, else the fallback figures."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, 1900.0, "fallback"
+
+
+def run_net(args):
+    """Proposal network forward throughput on B seeded random flow stacks of
+    the learned workload's shape (1242x375, T = 8, FP16 flows; activations of
+    238 MB per layer, larger than L2), and the training step at batch 2.
+    Roofline of the forward pass as a whole (flow normalisation, input
+    packing, six tcgen05 convolutions), layer by layer: HBM bytes per pixel =
+    FP16 flows read twice (the per-frame magnitude sum, then the packing),
+    2 x 32 B + packed input written and read 2 x 32 B + five 32-channel
+    activations written and read 5 x 2 x 64 B + FP32 predictions 32 B = 800 B;
+    FLOP per pixel = 2 x 9 x (2T x 32 + 4 x 32 x 32 + 32 x 2)."""
+    import torch
+
+    from paper_2104_06789_gb300 import build, learned, voldor
+    torch.cuda.set_device(0)
+    build.build()
+    T, H, W, B = 8, 375, 1242, args.net
+    rng = np.random.default_rng(0)
+    flows = torch.from_numpy(rng.normal(0, 8, size=(B, T, H, W, 2)).astype(np.float16)).cuda()
+    tgt = torch.from_numpy(np.stack([rng.normal(0, 0.5, size=(2, H, W)), rng.uniform(0, 1, size=(2, H, W))],
+                                    -1).astype(np.float32)).cuda()
+    net = voldor.Net(T, learned.init_weights(T))
+    stream = torch.cuda.Stream()
+    for _ in range(args.warmup):
+        net.forward(flows, stream=stream)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(0) as clk:
+        for e0, e1 in evs:
+            e0.record(stream)
+            net.forward(flows, stream=stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    f2, t2 = flows[:2].contiguous(), tgt
+    for _ in range(args.warmup):
+        net.train_step(f2, t2, 1e-4, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        net.train_step(f2, t2, 1e-4, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1) / args.steps
+    net.destroy()
+    hbm, bf16, src = measured_peaks()
+    npx = B * H * W
+    gbs = npx * 800 / (ms * 1e-3) / 1e9
+    tflops = npx * 2 * 9 * (2 * T * 32 + 4 * 32 * 32 + 32 * 2) / (ms * 1e-3) / 1e12
+    line = {"metric": "proposal network forward, images/s at 1242x375 T=8", "value": B / (ms * 1e-3),
+            "unit": "images/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "dtype": "bf16", "data": "synthetic (seeded normal flows)",
+            "config": {"workload": "proposal_net_1242x375_T8", "images": B, "flows": "fp16",
+                       "l2": "activations 238 MB per layer, larger than L2"},
+            "roofline": {"kernel": "forward pass (normalisation, packing, 6 x k_conv_tc)", "bound": "hbm", "achieved": gbs,
+                         "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
+                         "tensor_tflops": tflops, "tensor_frac": tflops / bf16, "peak_source": src},
+            "train_step_batch2_ms": train_ms, "train_mpix_per_s": 2 * H * W / (train_ms * 1e-3) / 1e6,
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def run_learned(args):
     """Plain vs learned initialisation: generate and label the training
     windows, train the proposal network with the library's kernels, compare
@@ -492,7 +567,9 @@ def run_learned(args):
 
 def main():
     args = parse_args()
-    if args.learned:
+    if args.net:
+        run_net(args)
+    elif args.learned:
         run_learned(args)
     elif args.batch:
         run_batch(args)

@@ -73,10 +73,16 @@ typedef struct {
     int criterion;                /* VOLDOR_CRITERION_MIE (Eq. 10, default) or _MLE (Eq. 9) for the
                                      depth update and the dense pose scores; the E-step posterior
                                      rho/(rho+mu) is the same under both */
+    int residual;                 /* VOLDOR_RESIDUAL_FISK (Eqs. 3-6, default) or _GAUSSIAN: the
+                                     ablation study's alternative model (Sec. 6.3), an isotropic
+                                     normal 2-D residual whose squared EPE is exponential with the
+                                     Fisk median alpha(|v_ob|) (Eq. 5); used for rho and mu (Eq. 7)
+                                     everywhere the density enters */
     uint64_t seed, window_id;     /* Philox4x64-10 key of the window */
 } voldor_params;
 
 enum { VOLDOR_CRITERION_MIE = 0, VOLDOR_CRITERION_MLE = 1 };
+enum { VOLDOR_RESIDUAL_FISK = 0, VOLDOR_RESIDUAL_GAUSSIAN = 1 };
 
 void voldor_default_params(voldor_params* p);
 

@@ -128,7 +128,7 @@ void or_fisk_params(const or_params* p, double n, double* log_alpha, double* bet
     *beta = std::max(p->b1 * n + p->b2, p->beta_min);
 }
 
-// Gaussian residual model of the ablation study (Sec. 6.4): the 2-D flow
+// Gaussian residual model of the ablation study (Sec. 6.3): the 2-D flow
 // residual isotropic normal, so the squared EPE x is exponential with mean
 // 2 sigma^2. The paper gives no parameters for it; reading: sigma^2(n) is
 // matched to the Fisk model at the same flow magnitude by the median of x,

@@ -108,8 +108,8 @@ __device__ __forceinline__ void load_halo(bf16* s, const bf16* in, int cin_g, in
 //     the two 8-channel halves one channel-block row apart), and the taps'
 //     column shift kx is 16 kx bytes on its start address.
 //   warp 5, one lane: per output row, 9 taps x CIN/16 tcgen05.mma
-//     (M = 128, N, K = 16, BF16 in, FP32 accumulators in TMEM), alternating
-//     between two accumulators, committed to mbarriers that release the
+//     (M = 128, N, K = 16, BF16 in, FP32 accumulators in TMEM), cycling
+//     through kTcAcc accumulators, committed to mbarriers that release the
 //     accumulator to the epilogue and the oldest input row to the loader.
 //   warps 0-3: epilogue: tcgen05.ld of the accumulator rows of their 32 TMEM
 //     lanes (one pixel per thread), bias, ReLU, the ReLU mask of a previous
@@ -137,7 +137,9 @@ struct ConvArgs {
 constexpr int kTcM = 128;                        // output pixels per row strip (MMA M)
 constexpr int kTcCols = kTcM + 2;                // input columns per row slot
 constexpr int kTcRowBytes = 2176;                // one channel block of a slot: 130 x 16 B, padded to 128 B
-constexpr int kTcSlots = 4;                      // input rows in flight
+constexpr int kTcSlots = 6;                      // input-row ring slots
+constexpr int kTcAcc = 4;                        // TMEM accumulators (output rows in flight)
+constexpr int kTcCtasPerSm = 2;
 constexpr int kTcRows = 16;                      // output rows per work item
 constexpr int kTcThreads = 192;
 constexpr long long kTcWaitLimit = 1ll << 24;    // polls of one mbarrier phase before giving up
@@ -151,10 +153,12 @@ struct TcShape {
     static constexpr int kWStepBytes = N * 16 * 2;               // one K step of B
     static constexpr int kRingBytes = kTcSlots * kSlotBytes;
     static constexpr int kWBytes = kKSteps * kWStepBytes;
-    // ring | weights | barriers: full[4] empty[4] acc_full[2] acc_empty[2] done | tmem address
+    // ring | weights | barriers: full[slots] empty[slots] acc_full[acc] acc_empty[acc] done |
+    // tmem address | abort flag
     static constexpr int kBarOff = kRingBytes + kWBytes;
-    static constexpr int kSmemBytes = kBarOff + 16 * 8 + 16;      // + tmem address, abort flag
-    static constexpr int kTmemCols = 2 * N < 32 ? 32 : 2 * N;
+    static constexpr int kBarBytes = ((2 * kTcSlots + 2 * kTcAcc + 1) * 8 + 15) / 16 * 16;
+    static constexpr int kSmemBytes = kBarOff + kBarBytes + 16;
+    static constexpr int kTmemCols = kTcAcc * N <= 32 ? 32 : (kTcAcc * N <= 64 ? 64 : (kTcAcc * N <= 128 ? 128 : 256));
     static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
                                        ((uint32_t)(kTcM >> 4) << 24);
 };
@@ -269,16 +273,16 @@ __device__ __forceinline__ TcItem tc_item(int i, int H, int W)
 }
 
 template <int CIN, int N>
-__global__ void __launch_bounds__(kTcThreads, 2) k_conv_tc(const __grid_constant__ CUtensorMap tin, ConvArgs a)
+__global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_conv_tc(const __grid_constant__ CUtensorMap tin, ConvArgs a)
 {
     using S = TcShape<CIN, N>;
     extern __shared__ __align__(1024) unsigned char smem[];
     const uint32_t sbase = smem_addr(smem);
     const uint32_t ring = sbase, wsm = sbase + S::kRingBytes, bars = sbase + S::kBarOff;
-    const uint32_t full = bars, empty = bars + 4 * 8, acc_full = bars + 8 * 8, acc_empty = bars + 10 * 8,
-                   done = bars + 12 * 8;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + S::kBarOff + 16 * 8);
-    volatile int& bad = *reinterpret_cast<volatile int*>(smem + S::kBarOff + 16 * 8 + 4);
+    const uint32_t full = bars, empty = bars + kTcSlots * 8, acc_full = bars + 2 * kTcSlots * 8,
+                   acc_empty = acc_full + kTcAcc * 8, done = acc_empty + kTcAcc * 8;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + S::kBarOff + S::kBarBytes);
+    volatile int& bad = *reinterpret_cast<volatile int*>(smem + S::kBarOff + S::kBarBytes + 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_items = a.B * ((a.H + kTcRows - 1) / kTcRows) * ((a.W + kTcM - 1) / kTcM);
 
@@ -297,7 +301,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_conv_tc(const __grid_constant
             tc_mbar_init(full + 8 * i, 1);
             tc_mbar_init(empty + 8 * i, 1);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < kTcAcc; ++i) {
             tc_mbar_init(acc_full + 8 * i, 1);
             tc_mbar_init(acc_empty + 8 * i, 4 * 32);
         }
@@ -349,8 +353,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_conv_tc(const __grid_constant
                 for (int k = 0; k < t.rows; ++k, ++orow) {
                     const uint32_t li = L0 + k + 2;
                     if (!tc_wait(full + 8 * (li % kTcSlots), (li / kTcSlots) & 1, &bad)) break;
-                    const uint32_t buf = orow & 1;
-                    if (orow >= 2 && !tc_wait(acc_empty + 8 * buf, ((orow >> 1) - 1) & 1, &bad)) break;
+                    const uint32_t buf = orow % kTcAcc;
+                    if (orow >= kTcAcc && !tc_wait(acc_empty + 8 * buf, ((orow / kTcAcc) - 1) & 1, &bad)) break;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t d = tmem + buf * N;
                     uint32_t acc = 0;
@@ -391,9 +395,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_conv_tc(const __grid_constant
         for (int it = blockIdx.x; it < n_items && go; it += gridDim.x) {
             const TcItem t = tc_item(it, a.H, a.W);
             for (int k = 0; k < t.rows; ++k, ++orow) {
-                const uint32_t buf = orow & 1;
+                const uint32_t buf = orow % kTcAcc;
                 // every lane polls; the warp proceeds only together (tcgen05.ld is warp-wide)
-                go = __all_sync(0xffffffffu, tc_wait(acc_full + 8 * buf, (orow >> 1) & 1, &bad));
+                go = __all_sync(0xffffffffu, tc_wait(acc_full + 8 * buf, (orow / kTcAcc) & 1, &bad));
                 if (!go) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 float v[N];
@@ -494,7 +498,7 @@ static bool launch_conv_tc(const ConvArgs& a, cudaStream_t st)
     CUtensorMap m;
     if (!tensor_map_rows(&m, a.in, CIN, a.W, a.H, a.B)) return false;
     const int items = a.B * ((a.H + kTcRows - 1) / kTcRows) * ((a.W + kTcM - 1) / kTcM);
-    const int grid = std::min(items, 2 * g_tc_sms);
+    const int grid = std::min(items, kTcCtasPerSm * g_tc_sms);
     k_conv_tc<CIN, N><<<grid, kTcThreads, S::kSmemBytes, st>>>(m, a);
     return true;
 }

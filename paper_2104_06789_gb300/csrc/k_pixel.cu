@@ -158,12 +158,18 @@ __global__ void k_prep_write(DevParams p, DevState s, int t)
     for (int w = 0; w < warp; ++w) rank += warp_sum[w];
     if (valid) {
         const float n = sqrtf((float)(g.fu * g.fu + g.fv * g.fv));
-        const FiskConst fc = fisk_const(p, n);
         const double iz = rcp64(g.Pz);
         PixRec r;
         r.a = make_float4((float)(g.Px * iz), (float)(p.fy_over_fx_d * g.Py * iz), (float)iz, (float)(g.fu * p.inv_fxd));
-        r.b = make_float4((float)(g.fv * p.inv_fxd), fc.beta, fc.beta * (p.log2_fx2 - fc.log2_alpha),
-                          (float)(p.fxd * p.fxd) * fc.mu_over_beta);
+        if (p.residual == VOLDOR_RESIDUAL_GAUSSIAN) {
+            const GaussConst gc = gauss_const(p, n);
+            r.b = make_float4((float)(g.fv * p.inv_fxd), (float)(p.fxd * p.fxd) * gc.inv_alpha, -gc.x_mu * gc.inv_alpha,
+                              0.f);
+        } else {
+            const FiskConst fc = fisk_const(p, n);
+            r.b = make_float4((float)(g.fv * p.inv_fxd), fc.beta, fc.beta * (p.log2_fx2 - fc.log2_alpha),
+                              (float)(p.fxd * p.fxd) * fc.mu_over_beta);
+        }
         r.c = make_float4(s.wmap[(size_t)(t - 1) * p.N + j], 0.f, 0.f, 0.f);
         s.pix[base + rank] = r;
     }
@@ -261,12 +267,8 @@ __device__ __forceinline__ float depth_ell_fast(const DevParams& p, const float*
     const float ru = fmaf(p.fx * fmaf(-pbx, bz, bx), rd, -fu);
     const float rv = fmaf(p.fy * fmaf(-pby, bz, by), rd, -fv);
     const float xsq = fminf(fmaxf(fmaf(ru, ru, rv * rv), p.x_min), p.x_max);
-    const FiskConst fc = fisk_const(p, sqrtf(fmaf(fu, fu, fv * fv)));
-    const float s = fc.beta * (log2f(xsq) - fc.log2_alpha);
-    const float e = exp2f(fabsf(s));
-    const float r = fc.mu_over_beta * xsq * (e + 2.f + 1.f / e);     // mu / rho
-    // MIE (Eq. 10): log rho/(rho+mu) = -log1p(r); MLE (Eq. 9): log rho - log mu = -log r
-    return p.criterion == VOLDOR_CRITERION_MLE ? -logf(r) : -log1pf(r);
+    // MIE (Eq. 10): log rho/(rho+mu); MLE (Eq. 9): log rho - log mu
+    return -neg_ell(p, xsq, sqrtf(fmaf(fu, fu, fv * fv)), p.criterion == VOLDOR_CRITERION_MLE);
 }
 
 // Emissions rho/(rho+mu) of every (t, j) at the current depth (E-step input)

@@ -220,10 +220,12 @@ static_assert(sizeof(PixX2) == 80, "PixX2 is five 16-byte words");
 // log2(1 + r) (MIE) or log2(r) (MLE) for two hypotheses against one pixel;
 // the packed form of pair_term2<false, MLE>, with the residual's sign flipped
 // (it is squared).
-// log2(1 + r) (MIE) or log2(r) (MLE) of two hypotheses against one pixel,
-// with the checks of pair_term2<true>; the residual's sign is flipped (it is
-// squared).
-template <bool kMLE>
+// log2(1 + r) (MIE) or log2(r) (MLE), r = mu / rho, of two hypotheses against
+// one pixel, with the checks of pair_term2<true>; the residual's sign is
+// flipped (it is squared). kGauss: the Gaussian residual model, r = 2^s with
+// s = xs fx^2 / alpha - x_mu / alpha (record fields beta, beta_k), and
+// log2(1 + 2^s) = max(s, 0) + log2(1 + 2^-|s|).
+template <bool kMLE, bool kGauss>
 __device__ __forceinline__ f2 pair_x2(const HypX2& h, const PixX2& q, float xs_min, float xs_max)
 {
     const f2 ONE = f2_pack(1.f, 1.f), TWO = f2_pack(2.f, 2.f);
@@ -238,11 +240,27 @@ __device__ __forceinline__ f2 pair_x2(const HypX2& h, const PixX2& q, float xs_m
     const f2 rv = f2_fma(mv, rd, q.vt);
     f2 xs = f2_fma(ru, ru, f2_mul(rv, rv));
     xs = f2_pack(fminf(fmaxf(f2_lo(xs), xs_min), xs_max), fminf(fmaxf(f2_hi(xs), xs_min), xs_max));
+    const float behind = kMLE ? 0.f : 1.f;       // 1 + a_z <= 0: rho := mu
+    if (kGauss) {
+        const f2 sq = f2_fma(q.beta, xs, q.beta_k);                      // log2(mu / rho)
+        const float g0 = f2_lo(sq), g1 = f2_hi(sq);
+        if (kMLE) return f2_pack(slct(behind, g0, f2_lo(nden)), slct(behind, g1, f2_hi(nden)));
+        const f2 e = f2_pack(mufu_ex2(-fabsf(g0)), mufu_ex2(-fabsf(g1)));
+        f2 ps = f2_fma(e, f2_pack(1.784831882e-01f, 1.784831882e-01f), f2_pack(-3.390570283e-01f, -3.390570283e-01f));
+        ps = f2_fma(e, ps, f2_pack(4.790599346e-01f, 4.790599346e-01f));
+        ps = f2_fma(e, ps, f2_pack(-7.212913036e-01f, -7.212913036e-01f));
+        ps = f2_fma(e, ps, f2_pack(1.442694783e+00f, 1.442694783e+00f));
+        const f2 small = f2_mul(e, ps);
+        const f2 big = f2_lg2(f2_add(e, ONE));
+        const f2 d = f2_add(e, f2_pack(-0.25f, -0.25f));
+        const float v0 = fmaxf(g0, 0.f) + slct(f2_lo(big), f2_lo(small), f2_lo(d));
+        const float v1 = fmaxf(g1, 0.f) + slct(f2_hi(big), f2_hi(small), f2_hi(d));
+        return f2_pack(slct(behind, v0, f2_lo(nden)), slct(behind, v1, f2_hi(nden)));
+    }
     const f2 sg = f2_fma(q.beta, f2_lg2(xs), q.beta_k);
     const float s0 = f2_lo(sg), s1 = f2_hi(sg);
     const f2 ep = f2_pack(mufu_ex2(s0), mufu_ex2(s1)), en = f2_pack(mufu_ex2(-s0), mufu_ex2(-s1));
     const f2 r = f2_mul(f2_mul(q.Cp, xs), f2_add(ep, f2_add(en, TWO)));
-    const float behind = kMLE ? 0.f : 1.f;       // 1 + a_z <= 0: rho := mu
     if (kMLE) {
         const f2 v = f2_lg2(r);
         return f2_pack(slct(behind, f2_lo(v), f2_lo(nden)), slct(behind, f2_hi(v), f2_hi(nden)));
@@ -259,14 +277,14 @@ __device__ __forceinline__ f2 pair_x2(const HypX2& h, const PixX2& q, float xs_m
 }
 
 // One shared-memory tile against the first NS hypothesis pairs of the thread.
-template <int NS, bool MLE>
+template <int NS, bool MLE, bool GAUSS>
 __device__ __forceinline__ void score_tile(const HypX2* hy, const PixX2* xt, int cnt, float xs_min, float xs_max,
                                            f2* facc)
 {
     for (int q = 0; q < cnt; ++q) {
         const PixX2 px = xt[q];
 #pragma unroll
-        for (int k = 0; k < NS; ++k) facc[k] = f2_fma(px.wq, pair_x2<MLE>(hy[k], px, xs_min, xs_max), facc[k]);
+        for (int k = 0; k < NS; ++k) facc[k] = f2_fma(px.wq, pair_x2<MLE, GAUSS>(hy[k], px, xs_min, xs_max), facc[k]);
     }
 }
 
@@ -275,7 +293,7 @@ __device__ __forceinline__ void score_tile(const HypX2* hy, const PixX2* xt, int
 // tile0 + (2k + 1) * 256 + tid); MINB resident blocks per SM. Pairs wholly past
 // the frame's hypothesis count are skipped (block-uniform), so a partial tile
 // costs at most 511 idle hypotheses. The autotuner picks among the instances.
-template <int SLOTS, int MINB, bool MLE>
+template <int SLOTS, int MINB, bool MLE, bool GAUSS>
 __global__ void __launch_bounds__(kScoreThreads, MINB) k_score(DevParams p, DevState s, int log_idx)
 {
     constexpr int HPT = 2 * SLOTS;
@@ -367,10 +385,10 @@ __global__ void __launch_bounds__(kScoreThreads, MINB) k_score(DevParams p, DevS
         f2 facc[SLOTS];
 #pragma unroll
         for (int k = 0; k < SLOTS; ++k) facc[k] = 0ull;
-        if (ns >= SLOTS) score_tile<SLOTS, MLE>(hy, xt, cnt, xs_min, xs_max, facc);
-        else if (SLOTS > 3 && ns == 3) score_tile<(SLOTS > 3 ? 3 : 1), MLE>(hy, xt, cnt, xs_min, xs_max, facc);
-        else if (SLOTS > 2 && ns == 2) score_tile<(SLOTS > 2 ? 2 : 1), MLE>(hy, xt, cnt, xs_min, xs_max, facc);
-        else score_tile<1, MLE>(hy, xt, cnt, xs_min, xs_max, facc);
+        if (ns >= SLOTS) score_tile<SLOTS, MLE, GAUSS>(hy, xt, cnt, xs_min, xs_max, facc);
+        else if (SLOTS > 3 && ns == 3) score_tile<(SLOTS > 3 ? 3 : 1), MLE, GAUSS>(hy, xt, cnt, xs_min, xs_max, facc);
+        else if (SLOTS > 2 && ns == 2) score_tile<(SLOTS > 2 ? 2 : 1), MLE, GAUSS>(hy, xt, cnt, xs_min, xs_max, facc);
+        else score_tile<1, MLE, GAUSS>(hy, xt, cnt, xs_min, xs_max, facc);
 #pragma unroll
         for (int k = 0; k < SLOTS; ++k) {
             acc[2 * k] += (double)f2_lo(facc[k]);
@@ -437,18 +455,25 @@ int score_chunks_max(int S, int N)
     return a > b ? a : b;
 }
 
+template <int SLOTS, int MINB>
+static void launch_score_shape(const DevParams& p, const DevState& s, int li, cudaStream_t st)
+{
+    dim3 grid((p.S + kScoreThreads * 2 * SLOTS - 1) / (kScoreThreads * 2 * SLOTS), s.n_chunks);
+    const bool mle = p.criterion == VOLDOR_CRITERION_MLE, gauss = p.residual == VOLDOR_RESIDUAL_GAUSSIAN;
+    if (gauss) {
+        if (mle) k_score<SLOTS, MINB, true, true><<<grid, kScoreThreads, 0, st>>>(p, s, li);
+        else k_score<SLOTS, MINB, false, true><<<grid, kScoreThreads, 0, st>>>(p, s, li);
+    } else {
+        if (mle) k_score<SLOTS, MINB, true, false><<<grid, kScoreThreads, 0, st>>>(p, s, li);
+        else k_score<SLOTS, MINB, false, false><<<grid, kScoreThreads, 0, st>>>(p, s, li);
+    }
+}
+
 void launch_score(const DevParams& p, const DevState& s, int log_idx, cudaStream_t st)
 {
     const int li = log_idx < kScoreLogMax ? log_idx : -1;
-    if (s.score_hpt == 4) {
-        dim3 grid((p.S + kScoreThreads * 4 - 1) / (kScoreThreads * 4), s.n_chunks);
-        if (p.criterion == VOLDOR_CRITERION_MLE) k_score<2, 2, true><<<grid, kScoreThreads, 0, st>>>(p, s, li);
-        else k_score<2, 2, false><<<grid, kScoreThreads, 0, st>>>(p, s, li);
-    } else {
-        dim3 grid((p.S + kScoreThreads * 8 - 1) / (kScoreThreads * 8), s.n_chunks);
-        if (p.criterion == VOLDOR_CRITERION_MLE) k_score<4, 1, true><<<grid, kScoreThreads, 0, st>>>(p, s, li);
-        else k_score<4, 1, false><<<grid, kScoreThreads, 0, st>>>(p, s, li);
-    }
+    if (s.score_hpt == 4) launch_score_shape<2, 2>(p, s, li, st);
+    else launch_score_shape<4, 1>(p, s, li, st);
 }
 
 void launch_score_reduce(const DevParams& p, const DevState& s, cudaStream_t st)

@@ -76,6 +76,7 @@ bool params_ok(const voldor_params& p)
     if (p.groups_per_frame < 1 || p.groups_per_frame > 262144) return false;
     if (p.ms_max_iter < 1 || p.ms_max_iter > 100000) return false;
     if (p.criterion != VOLDOR_CRITERION_MIE && p.criterion != VOLDOR_CRITERION_MLE) return false;
+    if (p.residual != VOLDOR_RESIDUAL_FISK && p.residual != VOLDOR_RESIDUAL_GAUSSIAN) return false;
     return true;
 }
 
@@ -86,6 +87,7 @@ DevParams make_dev_params(const voldor_ctx& c)
     d.W = c.W; d.H = c.H; d.T = c.T; d.N = c.N;
     d.S = p.hyps_per_frame; d.G = p.groups_per_frame; d.ms_max_iter = p.ms_max_iter;
     d.criterion = p.criterion;
+    d.residual = p.residual;
     d.flow_f16 = c.flow_dtype == VOLDOR_FLOW_F16;
     d.fx = (float)c.K.fx; d.fy = (float)c.K.fy; d.cx = (float)c.K.cx; d.cy = (float)c.K.cy;
     d.inv_fx = (float)(1.0 / c.K.fx); d.inv_fy = (float)(1.0 / c.K.fy);
@@ -344,6 +346,7 @@ void voldor_default_params(voldor_params* p)
     p->ms_tol = 1e-10;
     p->hyps_per_frame = 256; p->groups_per_frame = 512; p->ms_max_iter = 100;
     p->criterion = VOLDOR_CRITERION_MIE;
+    p->residual = VOLDOR_RESIDUAL_FISK;
     p->seed = 0; p->window_id = 0;
 }
 

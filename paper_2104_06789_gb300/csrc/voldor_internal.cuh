@@ -30,6 +30,7 @@ struct DevParams {
     int W, H, T, N;
     int S, G, ms_max_iter, flow_f16;
     int criterion;                      // VOLDOR_CRITERION_MIE or _MLE
+    int residual;                       // VOLDOR_RESIDUAL_FISK or _GAUSSIAN
     float fx, fy, cx, cy, inv_fx, inv_fy, fy_over_fx;
     float log2_a1, a2_log2e, b1, b2, beta_min, lambda2;
     float x_min, x_max;                 // px^2
@@ -47,7 +48,8 @@ struct DevParams {
 //  a = {xb, yb2, w, ut}: normalised coords x/z, (fy/fx) y/z, inverse depth 1/z
 //      in camera t-1, observed flow u / fx
 //  b = {vt, beta, beta_k, Cp}: observed flow v / fx, Fisk shape, beta *
-//      log2(fx^2 / alpha), mu / beta * fx^2
+//      log2(fx^2 / alpha), mu / beta * fx^2; under the Gaussian residual
+//      model {vt, fx^2 / alpha, -x_mu / alpha, 0}
 //  c = {wq, 0, 0, 0}: rigidness weight W_t^j
 struct PixRec {
     float4 a, b, c;
@@ -232,11 +234,44 @@ __device__ __forceinline__ FiskConst fisk_const(const DevParams& p, float n)
     return c;
 }
 
+// Gaussian residual model (the ablation study's alternative, Sec. 6.3): the
+// squared EPE x is exponential with the Fisk median alpha(n) (reading:
+// variance matched by the median), so log2(mu / rho) = (x - x_mu) / alpha.
+struct GaussConst {
+    float inv_alpha, x_mu;
+};
+
+__device__ __forceinline__ GaussConst gauss_const(const DevParams& p, float n)
+{
+    GaussConst c;
+    c.inv_alpha = exp2f(-fmaf(p.a2_log2e, n, p.log2_a1));
+    c.x_mu = fminf(fmaxf(p.lambda2 * n * n, p.x_min), p.x_max);
+    return c;
+}
+
+// -(the criterion's term) of one (t, j) in FP32 from the clamped squared
+// residual x (px^2) and the observed flow magnitude n: log(1 + mu/rho)
+// (MIE, Eq. 10) or log(mu/rho) (MLE, Eq. 9), under the window's residual model.
+//   Fisk:     mu / rho = (mu / beta) x (y + 2 + 1/y),  y = (x / alpha)^beta
+//   Gaussian: mu / rho = 2^s,  s = (x - x_mu) / alpha; log(1 + 2^s) taken as
+//             max(s, 0) ln 2 + log1p(2^-|s|) (finite for any s)
+__device__ __forceinline__ float neg_ell(const DevParams& p, float x, float n, bool mle)
+{
+    if (p.residual == VOLDOR_RESIDUAL_GAUSSIAN) {
+        const GaussConst gc = gauss_const(p, n);
+        const float s = (x - gc.x_mu) * gc.inv_alpha;
+        return mle ? s * 0.69314718055994531f : fmaxf(s, 0.f) * 0.69314718055994531f + log1pf(exp2f(-fabsf(s)));
+    }
+    const FiskConst fc = fisk_const(p, n);
+    const float s = fc.beta * (log2f(x) - fc.log2_alpha);
+    const float e = exp2f(fabsf(s));
+    const float r = fc.mu_over_beta * x * (e + 2.f + 1.f / e);
+    return mle ? logf(r) : log1pf(r);
+}
+
 // log[rho/(rho+mu)] (Eq. 10 term) for frame pose T_t (FP64 [R | t]): rigid
-// flow and residual in FP64, the likelihood in FP32:
-//   r = mu / rho = (mu / beta) x (y + 2 + 1/y),  y = (x / alpha)^beta,
-//   ell = -log1p(r).
-// log(1/2) when the point is behind camera t (the model's rho := mu).
+// flow and residual in FP64, the likelihood in FP32 (neg_ell). log(1/2)
+// when the point is behind camera t (the model's rho := mu).
 __device__ __forceinline__ float ell_frame(const DevParams& p, const double* Tt, const GeomD& g)
 {
     const double Qx = Tt[0] * g.Px + Tt[1] * g.Py + Tt[2] * g.Pz + Tt[3];
@@ -248,11 +283,7 @@ __device__ __forceinline__ float ell_frame(const DevParams& p, const double* Tt,
     const double rv = (p.fyd * Qy * iq + p.cyd - g.v) - g.fv;
     const float x = (float)fmin(fmax(ru * ru + rv * rv, (double)p.x_min), (double)p.x_max);
     const float n = sqrtf((float)(g.fu * g.fu + g.fv * g.fv));
-    const FiskConst fc = fisk_const(p, n);
-    const float s = fc.beta * (log2f(x) - fc.log2_alpha);
-    const float e = exp2f(fabsf(s));
-    const float r = fc.mu_over_beta * x * (e + 2.f + 1.f / e);
-    return -log1pf(r);
+    return -neg_ell(p, x, n, false);
 }
 
 // ---------------------------------------------------------------------------

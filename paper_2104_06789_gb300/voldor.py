@@ -19,6 +19,7 @@ OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_BOOTSTRAPPED, ERR_DEGENERATE, ER
 FLOW_F32, FLOW_F16 = 0, 1
 LEARNED_DEPTH, LEARNED_RIGIDNESS = 1, 2
 CRITERION_MIE, CRITERION_MLE = 0, 1
+RESIDUAL_FISK, RESIDUAL_GAUSSIAN = 0, 1
 BOOT_GIVEN_POSE = 0
 (BUF_SMOOTHED, BUF_LABELS, BUF_HYPS, BUF_HYP_INFO, BUF_HYP_WEIGHT, BUF_SCORES, BUF_POSE_INFO,
  BUF_DEPTH_SAMPLES, BUF_HYPS_F32, BUF_EPI_E, BUF_EPI_MEDIANS, BUF_EPI_VALID, BUF_EPI_INFO,
@@ -41,7 +42,7 @@ class Params(C.Structure):
         ("x_min", C.c_double), ("x_max", C.c_double), ("beta_min", C.c_double),
         ("ms_tol", C.c_double),
         ("hyps_per_frame", C.c_int), ("groups_per_frame", C.c_int),
-        ("ms_max_iter", C.c_int), ("criterion", C.c_int),
+        ("ms_max_iter", C.c_int), ("criterion", C.c_int), ("residual", C.c_int),
         ("seed", C.c_uint64), ("window_id", C.c_uint64),
     ]
 

@@ -37,6 +37,7 @@ def test_default_params_are_the_papers(vd):
     assert (p.a1, p.a2, p.b1, p.b2) == (0.01, 0.09, -0.0022, 1.0)
     assert (p.lambda_, p.gamma, p.sigma_t, p.sigma_r) == (0.15, 0.9, 0.1, 0.004)
     assert p.criterion == vd.CRITERION_MIE
+    assert p.residual == vd.RESIDUAL_FISK
 
 
 def test_invalid_arguments_are_rejected_on_the_host(vd):
@@ -58,7 +59,7 @@ def test_invalid_arguments_are_rejected_on_the_host(vd):
                                 None) == vd.ERR_INVALID_ARG
     for field, val in [("gamma", 1.0), ("gamma", 0.0), ("hyps_per_frame", 0), ("sigma_t", -1.0),
                        ("inv_depth_max", 0.01), ("x_min", 0.0), ("ms_max_iter", 0), ("a1", float("nan")),
-                       ("criterion", 2), ("criterion", -1)]:
+                       ("criterion", 2), ("criterion", -1), ("residual", 2), ("residual", -1)]:
         q = vd.default_params(**{field: val})
         assert L.voldor_init_window(ctypes.byref(h), 8, 8, 2, ctypes.byref(K), ctypes.byref(q), fp, 0, 0,
                                     None) == vd.ERR_INVALID_ARG, field

@@ -1,5 +1,5 @@
 """Pins of the oracle's Gaussian residual model (the alternative model of the
-ablation study, Sec. 6.4), checked against scipy: the squared EPE of an
+ablation study, Sec. 6.3), checked against scipy: the squared EPE of an
 isotropic 2-D normal residual is chi-square with 2 degrees of freedom scaled
 by sigma^2; the variance is matched to the Fisk model by the median (the
 Fisk median is alpha); and the window's per-(t, j) terms use that density for
