@@ -85,3 +85,22 @@ def test_autotune_keeps_results(vd):
     # another tile shape only reorders the FP64 sums of the dense scores
     assert np.abs(Pa - Pb).max() < 1e-9
     assert np.mean(Da == Db) > 0.999
+
+
+def test_autotune_hyps_on_a_window(vd):
+    """The hypothesis-count autotuner on the library's windows: an impossible
+    tolerance keeps the window's own count, an unbounded one takes the
+    smallest candidate, and the chosen count's window runs."""
+    from paper_2104_06789_gb300 import synthetic, tuning
+    w = synthetic.small_planes(seed=1003)
+    p = vd.default_params(hyps_per_frame=256, groups_per_frame=512, inv_depth_min=w.inv_depth_range[0],
+                          inv_depth_max=w.inv_depth_range[1])
+    flows = w.flows.astype(np.float32)
+    S, tried, _ = tuning.autotune_hyps(flows, w.K, p, w.poses[0], rot_tol=-1.0, trans_tol=-1.0)
+    assert S == 256 and [s for s, _, _ in tried] == [64, 128]
+    S, tried, _ = tuning.autotune_hyps(flows, w.K, p, w.poses[0], rot_tol=np.inf, trans_tol=np.inf)
+    assert S == 64 and len(tried) == 1
+    S, tried, (rt, tt) = tuning.autotune_hyps(flows, w.K, p, w.poses[0])
+    assert S in (64, 128, 256) and np.isfinite(rt) and np.isfinite(tt)
+    for s, ang, rel in tried:
+        assert np.isfinite(ang) and np.isfinite(rel)
