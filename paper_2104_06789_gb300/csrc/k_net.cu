@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -456,17 +457,18 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_conv_tc(const __gr
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
 // against the driver library).
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode_tiled = nullptr;
+static std::once_flag g_encode_once;
 
 static bool tensor_map_rows(CUtensorMap* m, const bf16* base, int C, int W, int H, int B)
 {
-    if (!g_encode_tiled) {
+    std::call_once(g_encode_once, [] {
         void* fn = nullptr;
         cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess || !fn)
-            return false;
-        g_encode_tiled = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    }
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess && fn)
+            g_encode_tiled = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    if (!g_encode_tiled) return false;
     const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
     const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
     const cuuint32_t box[4] = {8, (cuuint32_t)kTcCols, 1, 1};
@@ -476,29 +478,38 @@ static bool tensor_map_rows(CUtensorMap* m, const bf16* base, int C, int W, int 
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-static int g_tc_sms = 0;
+// Per-device launch state: SM count, and whether an instance's dynamic
+// shared-memory limit has been raised on that device.
+constexpr int kTcMaxDevices = 64;
+static std::mutex g_tc_mutex;
+static int g_tc_sms[kTcMaxDevices];
 
 template <int CIN, int N>
 static bool launch_conv_tc(const ConvArgs& a, cudaStream_t st)
 {
     using S = TcShape<CIN, N>;
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(k_conv_tc<CIN, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmemBytes) !=
-            cudaSuccess)
-            return false;
-        attr = true;
-    }
-    if (g_tc_sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&g_tc_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || g_tc_sms <= 0)
-            g_tc_sms = 152;
+    static bool attr[kTcMaxDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kTcMaxDevices) return false;
+    int sms = 0;
+    {
+        std::lock_guard<std::mutex> lock(g_tc_mutex);
+        if (!attr[dev]) {
+            if (cudaFuncSetAttribute(k_conv_tc<CIN, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmemBytes) !=
+                cudaSuccess)
+                return false;
+            attr[dev] = true;
+        }
+        if (g_tc_sms[dev] <= 0 &&
+            (cudaDeviceGetAttribute(&g_tc_sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+             g_tc_sms[dev] <= 0))
+            g_tc_sms[dev] = 152;
+        sms = g_tc_sms[dev];
     }
     CUtensorMap m;
     if (!tensor_map_rows(&m, a.in, CIN, a.W, a.H, a.B)) return false;
     const int items = a.B * ((a.H + kTcRows - 1) / kTcRows) * ((a.W + kTcM - 1) / kTcM);
-    const int grid = std::min(items, kTcCtasPerSm * g_tc_sms);
+    const int grid = std::min(items, kTcCtasPerSm * sms);
     k_conv_tc<CIN, N><<<grid, kTcThreads, S::kSmemBytes, st>>>(m, a);
     return true;
 }
