@@ -273,6 +273,16 @@ voldor_status voldor_score_records_noalloc(const float* records, int n_pix, cons
  * few KB; synchronises the device. Errors: INVALID_ARG, OOM, CUDA. */
 voldor_status voldor_probe_sfu_rate(int op, double* results_per_sm_clock);
 
+/* Exercises the expiry path of the bounded device-side waits (every mbarrier
+ * wait of the library's kernels gives up after a poll limit and the call
+ * reports VOLDOR_ERR_TIMEOUT): one block of 128 threads waits, with the dense
+ * scoring's bounded wait, on an mbarrier phase that nothing completes, for
+ * `polls` polls (0 .. 2^26, the kernels' own limit). Returns VOLDOR_ERR_TIMEOUT when every thread gave
+ * up (the expected result), with the SM cycles the wait took in *cycles (may
+ * be NULL); the device stays usable. Synchronises the device. Errors:
+ * INVALID_ARG, OOM, CUDA. */
+voldor_status voldor_probe_bounded_wait(long long polls, long long* cycles);
+
 /* ---------------------------------------------------------------------------
  * Batching and tuning of many windows (no counterpart in the paper).
  * ------------------------------------------------------------------------- */

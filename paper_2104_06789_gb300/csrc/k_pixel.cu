@@ -2,7 +2,7 @@
 // triangulation, pose preparation (dense-scoring records), E-step emissions
 // and forward-backward smoothing, MIE depth sweep, unsmoothed rigidness.
 //
-// Geometry is FP64 and likelihood arithmetic FP32 (see geom_prev/ell_frame).
+// Geometry is FP64 and likelihood arithmetic FP32 (geom_prev, k_emissions, neg_ell).
 // This translation unit is compiled without FMA contraction (--fmad=false):
 // the MIE sweep compares a candidate scored in one kernel with one scored in
 // another, and equal depths must give bit-identical scores.
@@ -118,11 +118,7 @@ __global__ void k_prep_count(DevParams p, DevState s, int t)
     if (threadIdx.x < 12) C[threadIdx.x] = s.cum[12 * (t - 1) + threadIdx.x];
     __syncthreads();
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    bool valid = false;
-    if (j < p.N) {
-        GeomD g;
-        valid = geom_prev(p, C, s.flows, t, j % p.W, j / p.W, s.theta[j], g);
-    }
+    const bool valid = j < p.N && geom_prev_valid(p, C, t, j % p.W, j / p.W, s.theta[j]);
     const int cnt = __syncthreads_count(valid);
     if (threadIdx.x == 0) s.pix_block_count[blockIdx.x] = cnt;
 }
@@ -185,16 +181,6 @@ void launch_pose_prep(const DevParams& p, const DevState& s, int t, cudaStream_t
     const int nb = (p.N + kPixThreads - 1) / kPixThreads;
     k_prep_count<<<nb, kPixThreads, 0, st>>>(p, s, t);
     k_prep_write<<<nb, kPixThreads, 0, st>>>(p, s, t);
-}
-
-// ell_t(j) at a given depth under the current poses; log(1/2) where the model
-// takes rho := mu (pi_{t-1} invalid or behind camera t).
-__device__ __forceinline__ float depth_ell(const DevParams& p, const FramesD& f, const void* flows, int t, int x, int y,
-                                           float depth)
-{
-    GeomD g;
-    if (!geom_prev(p, f.C[t - 1], flows, t, x, y, depth, g)) return -0.69314718055994531f;
-    return ell_frame(p, f.Tt[t - 1], g);
 }
 
 // ell_t(j) at depth d in FP32 for the MIE candidate scores, written without
@@ -272,7 +258,13 @@ __device__ __forceinline__ float depth_ell_fast(const DevParams& p, const float*
 }
 
 // Emissions rho/(rho+mu) of every (t, j) at the current depth (E-step input)
-// or, written into W, the unsmoothed rigidness update.
+// or, written into W, the unsmoothed rigidness update: per (t, j) the rigid
+// flow and residual in FP64 and the likelihood in FP32 (neg_ell); log(1/2)
+// where the model takes rho := mu (pi_{t-1} invalid or the point behind camera
+// t). The point is carried from frame to frame: the point in camera
+// t (T_t applied to the point in camera t-1) and its projection pi_t are the
+// next frame's point in camera (t+1)-1 and pi_{(t+1)-1}, since C_t X =
+// T_t (C_{t-1} X), so each frame transforms and projects once (FP64).
 __global__ void k_emissions(DevParams p, DevState s, float* out)
 {
     __shared__ FramesD f;
@@ -280,8 +272,48 @@ __global__ void k_emissions(DevParams p, DevState s, float* out)
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= p.N) return;
     const int x = j % p.W, y = j / p.W;
-    const float depth = s.theta[j];
-    for (int t = 1; t <= p.T; ++t) out[(size_t)(t - 1) * p.N + j] = expf(depth_ell(p, f, s.flows, t, x, y, depth));
+    const double th = (double)s.theta[j];
+    const double dx = ((double)x - p.cxd) * p.inv_fxd, dy = ((double)y - p.cyd) * p.inv_fyd;
+    double Px = th * dx, Py = th * dy, Pz = th;     // the point in camera t-1 (camera 0 for t = 1)
+    double u = (double)x, v = (double)y;            // pi_{t-1}
+    bool front = th > 0.0;                          // P_z > 0 and (u, v) defined
+    for (int t = 1; t <= p.T; ++t) {
+        float ell = -0.69314718055994531f;          // rho := mu
+        double fu = 0.0, fv = 0.0;
+        const bool valid_prev =
+            front && u >= 0.0 && u <= (double)(p.W - 1) && v >= 0.0 && v <= (double)(p.H - 1);
+        if (valid_prev) {
+            const int x0 = min((int)floor(u), p.W - 2), y0 = min((int)floor(v), p.H - 2);
+            const double ax = u - x0, ay = v - y0;
+            const size_t base = (size_t)(t - 1) * p.N + (size_t)y0 * p.W + x0;
+            const float2 f00 = load_flow(s.flows, p.flow_f16, base), f10 = load_flow(s.flows, p.flow_f16, base + 1);
+            const float2 f01 = load_flow(s.flows, p.flow_f16, base + p.W);
+            const float2 f11 = load_flow(s.flows, p.flow_f16, base + p.W + 1);
+            const double w00 = (1.0 - ax) * (1.0 - ay), w10 = ax * (1.0 - ay), w01 = (1.0 - ax) * ay, w11 = ax * ay;
+            fu = w00 * f00.x + w10 * f10.x + w01 * f01.x + w11 * f11.x;
+            fv = w00 * f00.y + w10 * f10.y + w01 * f01.y + w11 * f11.y;
+        }
+        const double* Tt = f.Tt[t - 1];
+        const double Qx = Tt[0] * Px + Tt[1] * Py + Tt[2] * Pz + Tt[3];
+        const double Qy = Tt[4] * Px + Tt[5] * Py + Tt[6] * Pz + Tt[7];
+        const double Qz = Tt[8] * Px + Tt[9] * Py + Tt[10] * Pz + Tt[11];
+        const bool front_t = Qz > 0.0;
+        double uq = 0.0, vq = 0.0;
+        if (front_t) {
+            const double iq = rcp64(Qz);
+            uq = p.fxd * Qx * iq + p.cxd;
+            vq = p.fyd * Qy * iq + p.cyd;
+        }
+        if (valid_prev && front_t) {
+            const double ru = (uq - u) - fu, rv = (vq - v) - fv;
+            const float xs = (float)fmin(fmax(ru * ru + rv * rv, (double)p.x_min), (double)p.x_max);
+            ell = -neg_ell(p, xs, sqrtf((float)(fu * fu + fv * fv)), false);
+        }
+        out[(size_t)(t - 1) * p.N + j] = expf(ell);
+        Px = Qx; Py = Qy; Pz = Qz;
+        u = uq; v = vq;
+        front = front_t;
+    }
 }
 
 void launch_emissions(const DevParams& p, const DevState& s, float* out, cudaStream_t st)

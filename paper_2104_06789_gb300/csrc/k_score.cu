@@ -134,9 +134,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit = kWaitLimit)
 {
-    for (long long i = 0; i < kWaitLimit; ++i)
+    for (long long i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(kScoreThreads, MINB) k_score(DevParams p, DevS
         if (threadIdx.x == 0) {
             for (int j = it; j < n_tiles && j < it + kStages; ++j)
                 mbar_wait_bounded(&full[j % kStages], (uint32_t)((j / kStages) & 1));
-            atomicOr(s.status + 3, 1 << 16);
+            atomicOr(s.status + 3, kStatusTimeout);
         }
         return;
     }
@@ -662,3 +662,47 @@ extern "C" voldor_status voldor_probe_sfu_rate(int op, double* results_per_sm_cl
     *results_per_sm_clock = sum / blocks;
     return VOLDOR_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Diagnostic: the expiry path of the bounded mbarrier waits.
+// ---------------------------------------------------------------------------
+namespace vd {
+// Bounded-wait probe: every thread of one block waits, with the scoring
+// kernel's bounded wait, on the first phase of an mbarrier that nothing
+// arrives on, for `polls` polls; out[0] = number of threads that gave up,
+// out[1] = SM cycles the wait took on thread 0.
+__global__ void k_wait_probe(long long polls, long long* out)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const long long t0 = clock64();
+    const bool done = mbar_wait_bounded(&bar, 0, polls);
+    const long long t1 = clock64();
+    const int gave_up = __syncthreads_count(!done);
+    if (threadIdx.x == 0) {
+        out[0] = gave_up;
+        out[1] = t1 - t0;
+    }
+}
+
+}  // namespace vd
+
+extern "C" voldor_status voldor_probe_bounded_wait(long long polls, long long* cycles)
+{
+    using namespace vd;
+    if (polls < 0 || polls > kWaitLimit) return VOLDOR_ERR_INVALID_ARG;
+    long long* d = nullptr;
+    if (cudaMalloc(&d, 2 * sizeof(long long)) != cudaSuccess) return VOLDOR_ERR_OOM;
+    k_wait_probe<<<1, 128>>>(polls, d);
+    long long h[2] = {0, 0};
+    const cudaError_t e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return VOLDOR_ERR_CUDA;
+    if (cycles) *cycles = h[1];
+    return h[0] == 128 ? VOLDOR_ERR_TIMEOUT : (h[0] == 0 ? VOLDOR_OK : VOLDOR_ERR_INTERNAL);
+}
+

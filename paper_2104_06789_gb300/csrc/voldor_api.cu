@@ -323,6 +323,14 @@ void drop_graphs(voldor_ctx* c)
     c->graph_kernels.clear();
 }
 
+// Status of a window's status word 3: a bounded wait that gave up outranks
+// degenerate frames.
+voldor_status status_of_word(int w)
+{
+    if (w & kStatusTimeout) return VOLDOR_ERR_TIMEOUT;
+    return w ? VOLDOR_ERR_DEGENERATE : VOLDOR_OK;
+}
+
 voldor_status read_status_word(voldor_ctx* c, int* host4)
 {
     if (!cuda_ok(c, cudaMemcpyAsync(host4, c->ds.status, 16, cudaMemcpyDeviceToHost, c->stream))) return kCuda;
@@ -538,7 +546,7 @@ voldor_status voldor_em_step(voldor_ctx* c, int n_iters)
     int st4[4];
     voldor_status rs = read_status_word(c, st4);
     if (rs != VOLDOR_OK) return rs;
-    return st4[3] ? VOLDOR_ERR_DEGENERATE : VOLDOR_OK;
+    return status_of_word(st4[3]);
 }
 
 voldor_status voldor_get_pose_depth_rigidness(voldor_ctx* c, double* poses, float* depth, float* rigidness)
@@ -616,7 +624,7 @@ voldor_status voldor_pose_update(voldor_ctx* c, int k, int t)
     int st4[4];
     voldor_status rs = read_status_word(c, st4);
     if (rs != VOLDOR_OK) return rs;
-    return st4[3] ? VOLDOR_ERR_DEGENERATE : VOLDOR_OK;
+    return status_of_word(st4[3]);
 }
 
 voldor_status voldor_score_hypotheses(voldor_ctx* c, int t, int n, const double* R, const double* tv, double* L)
@@ -919,7 +927,8 @@ voldor_status voldor_batch_run(voldor_batch* b, void* cuda_stream, float* latenc
         if (latency_ms && cudaEventElapsedTime(&latency_ms[i], b->start, b->done[i]) != cudaSuccess) return kCuda;
         int deg = 0;
         if (cudaMemcpy(&deg, c->ds.status + 3, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return kCuda;
-        if (deg) result = VOLDOR_ERR_DEGENERATE;
+        const voldor_status ws = status_of_word(deg);
+        if (ws == VOLDOR_ERR_TIMEOUT || (ws == VOLDOR_ERR_DEGENERATE && result == VOLDOR_OK)) result = ws;
     }
     return result;
 }

@@ -22,6 +22,9 @@ constexpr int kMeanshiftCtas = 8;      // thread-block cluster of the meanshift
 constexpr int kMeanshiftThreads = 256;
 constexpr int kPixThreads = 256;
 constexpr int kScoreLogMax = 1024;
+// Status word 3 of a window: a count of frames whose pose update was
+// degenerate, plus this bit when a bounded device-side wait gave up.
+constexpr int kStatusTimeout = 1 << 30;
 constexpr int kTuneMaxWaves = 8;       // largest dense-scoring grid the autotuner tries, in waves
 constexpr int kMaxImageSide = 4096;   // longest chain the depth sweep resolves in shared memory
 
@@ -214,6 +217,29 @@ __device__ __forceinline__ bool geom_prev(const DevParams& p, const double* C, c
     return true;
 }
 
+// Whether (t, j) has an observation at pi_{t-1}: geom_prev's test without the
+// flow sample (same arithmetic, so the same decision).
+__device__ __forceinline__ bool geom_prev_valid(const DevParams& p, const double* C, int t, int x, int y, float depth)
+{
+    const double th = (double)depth;
+    const double dx = ((double)x - p.cxd) * p.inv_fxd, dy = ((double)y - p.cyd) * p.inv_fyd;
+    double u, v;
+    if (t == 1) {
+        if (!(th > 0.0)) return false;
+        u = (double)x; v = (double)y;
+    } else {
+        const double X = th * dx, Y = th * dy, Z = th;
+        const double Px = C[0] * X + C[1] * Y + C[2] * Z + C[3];
+        const double Py = C[4] * X + C[5] * Y + C[6] * Z + C[7];
+        const double Pz = C[8] * X + C[9] * Y + C[10] * Z + C[11];
+        if (!(Pz > 0.0)) return false;
+        const double iz = rcp64(Pz);
+        u = p.fxd * Px * iz + p.cxd;
+        v = p.fyd * Py * iz + p.cyd;
+    }
+    return u >= 0.0 && u <= (double)(p.W - 1) && v >= 0.0 && v <= (double)(p.H - 1);
+}
+
 // Fisk quantities of an observed flow of magnitude n (Eqs. 5-7), FP32:
 // beta, log2(alpha), and mu / beta written as ys / (x_mu (1 + ys)^2) with
 // x_mu = lambda^2 n^2 and ys = 2^-|beta log2(x_mu / alpha)|.
@@ -267,23 +293,6 @@ __device__ __forceinline__ float neg_ell(const DevParams& p, float x, float n, b
     const float e = exp2f(fabsf(s));
     const float r = fc.mu_over_beta * x * (e + 2.f + 1.f / e);
     return mle ? logf(r) : log1pf(r);
-}
-
-// log[rho/(rho+mu)] (Eq. 10 term) for frame pose T_t (FP64 [R | t]): rigid
-// flow and residual in FP64, the likelihood in FP32 (neg_ell). log(1/2)
-// when the point is behind camera t (the model's rho := mu).
-__device__ __forceinline__ float ell_frame(const DevParams& p, const double* Tt, const GeomD& g)
-{
-    const double Qx = Tt[0] * g.Px + Tt[1] * g.Py + Tt[2] * g.Pz + Tt[3];
-    const double Qy = Tt[4] * g.Px + Tt[5] * g.Py + Tt[6] * g.Pz + Tt[7];
-    const double Qz = Tt[8] * g.Px + Tt[9] * g.Py + Tt[10] * g.Pz + Tt[11];
-    if (!(Qz > 0.0)) return -0.69314718055994531f;
-    const double iq = rcp64(Qz);
-    const double ru = (p.fxd * Qx * iq + p.cxd - g.u) - g.fu;
-    const double rv = (p.fyd * Qy * iq + p.cyd - g.v) - g.fv;
-    const float x = (float)fmin(fmax(ru * ru + rv * rv, (double)p.x_min), (double)p.x_max);
-    const float n = sqrtf((float)(g.fu * g.fu + g.fv * g.fv));
-    return -neg_ell(p, x, n, false);
 }
 
 // ---------------------------------------------------------------------------

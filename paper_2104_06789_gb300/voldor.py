@@ -87,6 +87,7 @@ def lib():
             "voldor_device_bytes": (sz, [vp]),
             "voldor_score_records_noalloc": (i, [vp, i, vp, i, d, d, vp, vp]),
             "voldor_probe_sfu_rate": (i, [i, P(d)]),
+            "voldor_probe_bounded_wait": (i, [C.c_longlong, P(C.c_longlong)]),
             "voldor_autotune": (i, [vp, P(i), P(i), P(C.c_float)]),
             "voldor_set_score_shape": (i, [vp, i, i]),
             "voldor_batch_create": (i, [P(vp), i, i, P(vp)]),
@@ -353,6 +354,14 @@ def probe_sfu_rate(op):
     v = C.c_double(0.0)
     _check(lib().voldor_probe_sfu_rate(int(op), C.byref(v)), "voldor_probe_sfu_rate")
     return v.value
+
+
+def probe_bounded_wait(polls):
+    """(status, SM cycles) of the bounded-wait expiry probe: ERR_TIMEOUT is the
+    expected status (nothing completes the phase the probe waits on)."""
+    cyc = C.c_longlong(0)
+    st = lib().voldor_probe_bounded_wait(int(polls), C.byref(cyc))
+    return st, cyc.value
 
 
 class Batch:
