@@ -323,64 +323,160 @@ void launch_emissions(const DevParams& p, const DevState& s, float* out, cudaStr
 }
 
 // ---------------------------------------------------------------------------
-// Forward-backward (Eqs. 12-14) on every chain of every frame, one thread per
+// Forward-backward (Eqs. 12-14) on every chain of every frame, one warp per
 // chain. Emissions (1 - w, w) are read from s.qs and replaced by the
-// smoothed q(W = 1). Messages are renormalised at every step; both
-// components are kept so that neither loses relative precision.
+// smoothed q(W = 1). With A = [[g, h], [h, g]] (g = gamma, h = 1 - gamma):
+//   forward   f_0 = e_0,  f_i = diag(e_i) A f_{i-1}
+//   backward  b_{n-1} = 1, b_i = A diag(e_{i+1}) b_{i+1}
+//   q_i = f_i .* b_i (normalised),
+// every message renormalised at every step. The chain is cut into 32
+// contiguous segments, one per lane; each lane forms the product of its
+// segment's 2x2 transfer matrices (renormalised by their entry sum, all
+// entries are non-negative), a 5-step shuffle scan gives each lane the
+// product of the segments before it (forward) or after it (backward), and
+// each lane then walks its own segment with the step-by-step recursion from
+// the message entering it.
 // ---------------------------------------------------------------------------
-__global__ void k_forward_backward(DevParams p, DevState s)
+struct M22 {
+    float a, b, c, d;   // [[a, b], [c, d]]
+};
+
+__device__ __forceinline__ M22 m22_mul(const M22& x, const M22& y)
+{
+    M22 r{x.a * y.a + x.b * y.c, x.a * y.b + x.b * y.d, x.c * y.a + x.d * y.c, x.c * y.b + x.d * y.d};
+    const float s = r.a + r.b + r.c + r.d;
+    if (s > 0.f) {
+        const float is = 1.f / s;
+        r.a *= is; r.b *= is; r.c *= is; r.d *= is;
+    }
+    return r;
+}
+
+__device__ __forceinline__ M22 m22_shfl(const M22& x, int src_delta, bool up)
+{
+    M22 r;
+    if (up) {
+        r.a = __shfl_up_sync(0xffffffffu, x.a, src_delta); r.b = __shfl_up_sync(0xffffffffu, x.b, src_delta);
+        r.c = __shfl_up_sync(0xffffffffu, x.c, src_delta); r.d = __shfl_up_sync(0xffffffffu, x.d, src_delta);
+    } else {
+        r.a = __shfl_down_sync(0xffffffffu, x.a, src_delta); r.b = __shfl_down_sync(0xffffffffu, x.b, src_delta);
+        r.c = __shfl_down_sync(0xffffffffu, x.c, src_delta); r.d = __shfl_down_sync(0xffffffffu, x.d, src_delta);
+    }
+    return r;
+}
+
+__global__ void __launch_bounds__(256) k_forward_backward(DevParams p, DevState s)
 {
     const int dir = (*s.iter) & 3;
     const bool rows = (dir == 0 || dir == 2);
     const int n_chains = rows ? p.H : p.W;
     const int len = rows ? p.W : p.H;
     const int stride = rows ? 1 : p.W;
-    const int id = blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= p.T * n_chains) return;
+    const int lane = threadIdx.x & 31;
+    const int id = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (id >= p.T * n_chains) return;                // whole warps leave together
     const int t = id / n_chains, c = id % n_chains;
     const size_t base = (size_t)t * p.N + (rows ? (size_t)c * p.W : (size_t)c);
     float* e = s.qs + base;
     float2* fw = reinterpret_cast<float2*>(s.fb_fwd) + base;
     const float g = p.gamma, h = 1.f - p.gamma;
+    const int L = (len + 31) / 32;
+    const int i0 = min(lane * L, len), i1 = min(i0 + L, len);    // this lane's segment [i0, i1)
+    const bool has = i0 < i1;
+
+    // ---- forward: segment products of diag(e_i) A for i in [max(i0, 1), i1)
+    M22 P{1.f, 0.f, 0.f, 1.f};
+    for (int i = (i0 > 0 ? i0 : 1); i < i1; ++i) {
+        const float w = e[(size_t)i * stride];
+        const M22 Mi{(1.f - w) * g, (1.f - w) * h, w * h, w * g};
+        P = m22_mul(Mi, P);
+    }
+    // inclusive scan: S_k = P_k ... P_0 (later segments on the left)
+    M22 S = P;
+    for (int d = 1; d < 32; d <<= 1) {
+        const M22 o = m22_shfl(S, d, true);
+        if (lane >= d) S = m22_mul(S, o);
+    }
+    const M22 Sprev = m22_shfl(S, 1, true);          // S_{k-1}
     float f0, f1;
     {
         const float w = e[0];
         const float a0 = 1.f - w, a1 = w, sum = a0 + a1;
         f0 = a0 / sum;
         f1 = a1 / sum;
-        fw[0] = make_float2(f0, f1);
     }
-    for (int i = 1; i < len; ++i) {
-        const float w = e[(size_t)i * stride];
-        const float p0 = g * f0 + h * f1, p1 = h * f0 + g * f1;
-        const float a0 = (1.f - w) * p0, a1 = w * p1, sum = a0 + a1;
+    if (lane > 0) {                                   // f_{i0 - 1} = S_{k-1} f_0
+        const float a0 = Sprev.a * f0 + Sprev.b * f1, a1 = Sprev.c * f0 + Sprev.d * f1, sum = a0 + a1;
         f0 = a0 / sum;
         f1 = a1 / sum;
-        fw[(size_t)i * stride] = make_float2(f0, f1);
     }
-    float b0 = 1.f, b1 = 1.f;
-    float w_next = e[(size_t)(len - 1) * stride];
-    {
-        const float2 f = fw[(size_t)(len - 1) * stride];
-        const float q0 = f.x * b0, q1 = f.y * b1;
-        e[(size_t)(len - 1) * stride] = q1 / (q0 + q1);
+    if (has) {
+        int i = i0;
+        if (i == 0) {
+            fw[0] = make_float2(f0, f1);
+            i = 1;
+        }
+        for (; i < i1; ++i) {
+            const float w = e[(size_t)i * stride];
+            const float p0 = g * f0 + h * f1, p1 = h * f0 + g * f1;
+            const float a0 = (1.f - w) * p0, a1 = w * p1, sum = a0 + a1;
+            f0 = a0 / sum;
+            f1 = a1 / sum;
+            fw[(size_t)i * stride] = make_float2(f0, f1);
+        }
     }
-    for (int i = len - 2; i >= 0; --i) {
-        const float c0 = (1.f - w_next) * b0, c1 = w_next * b1;
-        const float n0 = g * c0 + h * c1, n1 = h * c0 + g * c1, sum = n0 + n1;
+
+    // ---- backward: segment products of A diag(e_{i+1}) for i in [i0, min(i1, len - 1))
+    const int j1 = min(i1, len - 1);
+    M22 R{1.f, 0.f, 0.f, 1.f};
+    for (int i = j1 - 1; i >= i0; --i) {
+        const float w = e[(size_t)(i + 1) * stride];
+        const M22 Ni{g * (1.f - w), h * w, h * (1.f - w), g * w};
+        R = m22_mul(Ni, R);                           // N_i ... N_{j1 - 1}
+    }
+    // the emission just past this segment, read before any lane writes q
+    const float w_after = i1 < len ? e[(size_t)i1 * stride] : 0.f;
+    // suffix scan: U_k = R_k R_{k+1} ... R_31
+    M22 U = R;
+    for (int d = 1; d < 32; d <<= 1) {
+        const M22 o = m22_shfl(U, d, false);
+        if (lane + d < 32) U = m22_mul(U, o);
+    }
+    const M22 Unext = m22_shfl(U, 1, false);          // U_{k+1}
+    float b0 = 1.f, b1 = 1.f;                          // b_{len - 1}
+    if (lane < 31 && i1 < len) {                       // b_{i1} = U_{k+1} 1
+        const float n0 = Unext.a + Unext.b, n1 = Unext.c + Unext.d, sum = n0 + n1;
         b0 = n0 / sum;
         b1 = n1 / sum;
-        w_next = e[(size_t)i * stride];
-        const float2 f = fw[(size_t)i * stride];
-        const float q0 = f.x * b0, q1 = f.y * b1;
-        e[(size_t)i * stride] = q1 / (q0 + q1);
+    }
+    __syncwarp();                                      // every lane has read its emissions
+    if (has) {
+        float w_next = w_after;
+        int i = i1 - 1;
+        if (i1 == len) {                               // the chain's last element: b = 1
+            w_next = e[(size_t)i * stride];
+            const float2 f = fw[(size_t)i * stride];
+            const float q0 = f.x * b0, q1 = f.y * b1;
+            e[(size_t)i * stride] = q1 / (q0 + q1);
+            --i;
+        }
+        for (; i >= i0; --i) {
+            const float c0 = (1.f - w_next) * b0, c1 = w_next * b1;
+            const float n0 = g * c0 + h * c1, n1 = h * c0 + g * c1, sum = n0 + n1;
+            b0 = n0 / sum;
+            b1 = n1 / sum;
+            w_next = e[(size_t)i * stride];
+            const float2 f = fw[(size_t)i * stride];
+            const float q0 = f.x * b0, q1 = f.y * b1;
+            e[(size_t)i * stride] = q1 / (q0 + q1);
+        }
     }
 }
 
 void launch_forward_backward(const DevParams& p, const DevState& s, cudaStream_t st)
 {
-    const int n = p.T * (p.H > p.W ? p.H : p.W);
-    k_forward_backward<<<(n + 127) / 128, 128, 0, st>>>(p, s);
+    const int n = p.T * (p.H > p.W ? p.H : p.W);      // chains (warps) of the longer count
+    k_forward_backward<<<(n + 7) / 8, 256, 0, st>>>(p, s);
 }
 
 // ---------------------------------------------------------------------------
