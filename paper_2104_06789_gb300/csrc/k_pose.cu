@@ -284,15 +284,10 @@ __device__ bool group_point(const DevParams& p, const DevState& s, const double*
     return d3unit(bear);
 }
 
-__global__ void k_p3p_groups(DevParams p, DevState s, int t, int g_begin, int g_end, int skip_if_found)
+__global__ void k_p3p_groups(DevParams p, DevState s, int t)
 {
-    const int g = g_begin + blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= g_end) return;
-    if (skip_if_found && *s.grp_found >= p.S) {   // the first groups already give S hypotheses
-        s.grp_count[g] = 0;
-        s.grp_weight[g] = 0.0;
-        return;
-    }
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= p.G) return;
     const int k = *s.iter;
     const U64x4 r = philox4x64_10((uint64_t)g, (uint64_t)t, (uint64_t)k, (uint64_t)kStreamPose, p.seed, p.window_id);
     long long j[3];
@@ -319,35 +314,14 @@ __global__ void k_p3p_groups(DevParams p, DevState s, int t, int g_begin, int g_
         for (int q = 0; q < 12; ++q) o[i * 12 + q] = sols[i].Rt[q];
 }
 
-// Solutions found by groups [0, n): one block.
-__global__ void k_count_found(DevState s, int n)
-{
-    int acc = 0;
-    for (int g = threadIdx.x; g < n; g += blockDim.x) acc += s.grp_count[g];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    __shared__ int ws[32];
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int tot = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += ws[w];
-        *s.grp_found = tot;
-    }
-}
-
-// Groups are solved in two halves: the second half only if the first gave
-// fewer than S solutions (the collection keeps the first S in group order,
-// so later groups cannot contribute otherwise).
+// All G groups in one launch: one thread per group, one warp per block so
+// that the FP64 solves spread over every SM. The solve is bound by FP64
+// latency with a few warps per SM, so solving the groups past the first S
+// solutions costs little time, and the collection keeps the first S
+// solutions in group order either way.
 void launch_p3p_groups(const DevParams& p, const DevState& s, int t, cudaStream_t st)
 {
-    // one warp per block: the solve is FP64-bound per SM, so the groups are
-    // spread over every SM
-    const int g1 = p.G < p.S ? p.G : p.S;
-    k_p3p_groups<<<(g1 + 31) / 32, 32, 0, st>>>(p, s, t, 0, g1, 0);
-    if (g1 < p.G) {
-        k_count_found<<<1, 1024, 0, st>>>(s, g1);
-        k_p3p_groups<<<(p.G - g1 + 31) / 32, 32, 0, st>>>(p, s, t, g1, p.G, 1);
-    }
+    k_p3p_groups<<<(p.G + 31) / 32, 32, 0, st>>>(p, s, t);
 }
 
 // ---------------------------------------------------------------------------

@@ -148,7 +148,6 @@ size_t layout(voldor_ctx& c, char* base)
     s.hyp_p = (double*)take(S * 6 * 8);
     s.hyp_w = (double*)take(S * 8);
     s.hyp_dp = (float*)take(S * 8 * 4);
-    s.grp_found = (int*)take(4);
     s.hyp_info = (long long*)take(S * 2 * 8);
     s.partial = (double*)take((size_t)chunks_max * S * 8);
     s.scores = (double*)take(S * 8);

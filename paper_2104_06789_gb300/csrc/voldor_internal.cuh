@@ -84,7 +84,6 @@ struct DevState {
     double* hyp_p;            // [S][6] se(3) log
     double* hyp_w;            // [S]
     float* hyp_dp;            // [S][8] meanshift scratch: p_h - p_seed (6), w_h, 0
-    int* grp_found;           // [1] solutions of the first group half
     long long* hyp_info;      // [S][2]
     double* partial;          // [n_chunks][S]
     double* scores;           // [S]
