@@ -436,38 +436,39 @@ __device__ void se3_exp_vec(const double* p6, double* Rt)
     Rt[11] = rho[2] + B * a[2] + C * b[2];
 }
 
+// One thread per (group, solution slot), so that each thread's FP64 chain is
+// a single se(3) logarithm.
 __global__ void k_hyp_write(DevParams p, DevState s)
 {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= p.G) return;
-    const int cnt = s.grp_count[g], off = s.grp_offset[g];
+    const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= p.G * kMaxSols) return;
+    const int g = gi / kMaxSols, i = gi % kMaxSols;
+    if (i >= s.grp_count[g]) return;
+    const int h = s.grp_offset[g] + i;
+    if (h >= p.S) return;
     const double q = p.fyd / p.fxd;
     const double sc[3] = {1.0, q, 1.0};
-    for (int i = 0; i < cnt; ++i) {
-        const int h = off + i;
-        if (h >= p.S) break;
-        const double* Rt = s.grp_sols + ((size_t)g * kMaxSols + i) * 12;
-        double* oR = s.hyp_Rt + (size_t)h * 12;
-        for (int r = 0; r < 3; ++r) {
-            for (int c = 0; c < 3; ++c) oR[r * 3 + c] = Rt[r * 4 + c];
-            oR[9 + r] = Rt[r * 4 + 3];
-        }
-        float* f = s.hyp_f32 + (size_t)h * 12;
-        for (int r = 0; r < 3; ++r) {
-            for (int c = 0; c < 3; ++c) f[r * 3 + c] = (float)(sc[r] * (Rt[r * 4 + c] - (r == c ? 1.0 : 0.0)) / sc[c]);
-            f[9 + r] = (float)(sc[r] * Rt[r * 4 + 3]);
-        }
-        se3_log_quat(Rt, s.hyp_p + (size_t)h * 6);
-        s.hyp_w[h] = s.grp_weight[g];
-        s.hyp_info[(size_t)h * 2 + 0] = g;
-        s.hyp_info[(size_t)h * 2 + 1] = i;
+    const double* Rt = s.grp_sols + ((size_t)g * kMaxSols + i) * 12;
+    double* oR = s.hyp_Rt + (size_t)h * 12;
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) oR[r * 3 + c] = Rt[r * 4 + c];
+        oR[9 + r] = Rt[r * 4 + 3];
     }
+    float* f = s.hyp_f32 + (size_t)h * 12;
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) f[r * 3 + c] = (float)(sc[r] * (Rt[r * 4 + c] - (r == c ? 1.0 : 0.0)) / sc[c]);
+        f[9 + r] = (float)(sc[r] * Rt[r * 4 + 3]);
+    }
+    se3_log_quat(Rt, s.hyp_p + (size_t)h * 6);
+    s.hyp_w[h] = s.grp_weight[g];
+    s.hyp_info[(size_t)h * 2 + 0] = g;
+    s.hyp_info[(size_t)h * 2 + 1] = i;
 }
 
 void launch_hyp_collect(const DevParams& p, const DevState& s, cudaStream_t st)
 {
     k_hyp_scan<<<1, 1024, 0, st>>>(p, s);
-    k_hyp_write<<<(p.G + 127) / 128, 128, 0, st>>>(p, s);
+    k_hyp_write<<<(p.G * kMaxSols + 63) / 64, 64, 0, st>>>(p, s);
 }
 
 // Scoring form of caller-given hypotheses already copied to hyp_Rt.
@@ -517,6 +518,7 @@ k_meanshift(DevParams p, DevState s, int t)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
     __shared__ double wred[32][8];
     __shared__ double part[2][8];
+    __shared__ double gath[kMeanshiftCtas * 7];
     __shared__ double xs[8];
     __shared__ double seedp[6];
     __shared__ double bval[32];
@@ -597,12 +599,15 @@ k_meanshift(DevParams p, DevState s, int t)
             part[buf][tid] = v;
         }
         cluster.sync();
+        // the CTAs' partial sums, fetched in parallel from distributed shared
+        // memory, then added in rank order by one thread
+        if (tid < kMeanshiftCtas * 7)
+            gath[tid] = *cluster.map_shared_rank(&part[buf][tid % 7], (unsigned)(tid / 7));
+        __syncthreads();
         if (tid == 0) {
             double tot[7] = {0, 0, 0, 0, 0, 0, 0};
-            for (unsigned r = 0; r < kMeanshiftCtas; ++r) {
-                const double* pr = cluster.map_shared_rank(&part[buf][0], r);
-                for (int c = 0; c < 7; ++c) tot[c] += pr[c];
-            }
+            for (unsigned r = 0; r < kMeanshiftCtas; ++r)
+                for (int c = 0; c < 7; ++c) tot[c] += gath[r * 7 + c];
             if (!(tot[0] > 0.0)) {
                 flag = (it == 0) ? 2 : 1;
             } else {
