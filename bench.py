@@ -245,9 +245,6 @@ def run_ours(args):
     torch.cuda.synchronize()
     win = voldor.Window(dev_flows, w.K, params, stream=stream)
     T1 = w.poses[0]
-    # the library's dense-scoring shape autotuner, as a user runs it (not timed)
-    win.bootstrap(T1)
-    hpt, chunks, _ = win.autotune()
     win.enable_timing(True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local_rank}")
 
@@ -289,7 +286,6 @@ def run_ours(args):
     if not args.no_e2e:
         pinned = torch.from_numpy(flows16).pin_memory()
         host_win = voldor.Window(pinned, w.K, params, stream=stream)
-        host_win.set_score_shape(hpt, chunks)
         P = np.zeros((w.T, 4, 4))
         for i in range(args.warmup + args.steps):
             if i == args.warmup:
@@ -335,7 +331,6 @@ def run_ours(args):
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
 
     cfg = config_dict(w, args, world)
-    cfg["score_shape"] = f"{hpt} hypotheses/thread x {chunks} pixel chunks (autotuned)"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
