@@ -447,7 +447,7 @@ int score_chunks_for(int S, int N, int hpt, int waves)
     return chunks < 1 ? 1 : chunks;
 }
 
-int score_chunks(int S, int N) { return score_chunks_for(S, N, kScoreHypsPerThread, 4); }
+int score_chunks(int S, int N) { return score_chunks_for(S, N, kScoreDefaultHpt, kScoreDefaultWaves); }
 
 int score_chunks_max(int S, int N)
 {

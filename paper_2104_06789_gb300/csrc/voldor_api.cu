@@ -159,7 +159,7 @@ size_t layout(voldor_ctx& c, char* base)
     s.fb_fwd = (float*)take(T * N * 8);
     s.score_log = (long long*)take((size_t)kScoreLogMax * 2 * 8);
     s.n_chunks = chunks;
-    s.score_hpt = kScoreHypsPerThread;
+    s.score_hpt = kScoreDefaultHpt;
     return off;
 }
 

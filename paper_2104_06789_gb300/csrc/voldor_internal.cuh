@@ -15,7 +15,9 @@ namespace vd {
 constexpr int kMaxT = 16;
 constexpr int kMaxSols = 4;            // P3P has at most four solutions
 constexpr int kScoreThreads = 256;     // dense scoring block
-constexpr int kScoreHypsPerThread = 8;   // independent hypotheses per thread (ILP)
+constexpr int kScoreHypsPerThread = 8;   // hypotheses per thread of the allocation-free scoring (ILP)
+constexpr int kScoreDefaultHpt = 4;      // a window's dense-scoring shape until autotuned: 4 hypotheses
+constexpr int kScoreDefaultWaves = 8;    // per thread, two blocks per SM, pixel chunks for 8 waves
 constexpr int kScoreBlocksPerSM = 1;
 constexpr int kScoreHypsPerBlock = kScoreThreads * kScoreHypsPerThread;
 constexpr int kMeanshiftCtas = 8;      // thread-block cluster of the meanshift
