@@ -413,14 +413,28 @@ __global__ void __launch_bounds__(kScoreThreads, MINB) k_score(DevParams p, DevS
     }
 }
 
-// L_h = sum over chunks, in chunk order (partials are in natural-log units).
-__global__ void k_score_reduce(DevParams p, DevState s)
+// L_h = sum over the chunks' partials (natural-log units) in a fixed order:
+// 8 threads per hypothesis each add a contiguous range of chunks in chunk
+// order, then their 8 sums are added in range order (deterministic).
+constexpr int kReduceSplit = 8;
+
+__global__ void __launch_bounds__(256) k_score_reduce(DevParams p, DevState s)
 {
-    const int h = blockIdx.x * blockDim.x + threadIdx.x;
-    if (h >= *s.n_hyp) return;
+    __shared__ double part[kReduceSplit][32];
+    const int hl = threadIdx.x & 31, q = threadIdx.x >> 5;
+    const int h = blockIdx.x * 32 + hl;
+    const int n_hyp = *s.n_hyp, nc = s.n_chunks;
+    const int c0 = nc * q / kReduceSplit, c1 = nc * (q + 1) / kReduceSplit;
     double v = 0.0;
-    for (int c = 0; c < s.n_chunks; ++c) v += s.partial[(size_t)c * p.S + h];
-    s.scores[h] = v;
+    if (h < n_hyp)
+        for (int c = c0; c < c1; ++c) v += s.partial[(size_t)c * p.S + h];
+    part[q][hl] = v;
+    __syncthreads();
+    if (q == 0 && h < n_hyp) {
+        double t = 0.0;
+        for (int r = 0; r < kReduceSplit; ++r) t += part[r][hl];
+        s.scores[h] = t;
+    }
 }
 
 static int g_num_sms = 0;
@@ -478,7 +492,7 @@ void launch_score(const DevParams& p, const DevState& s, int log_idx, cudaStream
 
 void launch_score_reduce(const DevParams& p, const DevState& s, cudaStream_t st)
 {
-    k_score_reduce<<<(p.S + 255) / 256, 256, 0, st>>>(p, s);
+    k_score_reduce<<<(p.S + 31) / 32, 32 * kReduceSplit, 0, st>>>(p, s);
 }
 
 
