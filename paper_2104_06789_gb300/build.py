@@ -1,7 +1,8 @@
 """Builds libvoldor.so (sm_103a) in-tree with nvcc.
 
-The four translation units compile in parallel; the per-pixel one without
-FMA contraction (its comparisons need bit-identical scores of equal depths).
+The translation units compile in parallel; the MIE sweep's (k_pixel.cu)
+without FMA contraction (its comparisons need bit-identical scores of equal
+depths).
 """
 from __future__ import annotations
 
@@ -22,6 +23,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE
           "--expt-relaxed-constexpr"]
 UNITS = {
     "k_pixel.cu": ["--fmad=false"],
+    "k_geom.cu": [],
     "k_pose.cu": [],
     "k_score.cu": [],
     "voldor_api.cu": [],

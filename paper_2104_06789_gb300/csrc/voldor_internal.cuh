@@ -241,6 +241,21 @@ __device__ __forceinline__ bool geom_prev_valid(const DevParams& p, const double
     return u >= 0.0 && u <= (double)(p.W - 1) && v >= 0.0 && v <= (double)(p.H - 1);
 }
 
+// Stages C_{t-1} and T_t of every frame in shared memory.
+struct FramesD {
+    double C[kMaxT][12];
+    double Tt[kMaxT][12];
+};
+
+__device__ __forceinline__ void load_frames(const DevParams& p, const DevState& s, FramesD& f)
+{
+    for (int i = threadIdx.x; i < p.T * 12; i += blockDim.x) {
+        f.C[i / 12][i % 12] = s.cum[i];
+        f.Tt[i / 12][i % 12] = s.poses[i];
+    }
+    __syncthreads();
+}
+
 // Fisk quantities of an observed flow of magnitude n (Eqs. 5-7), FP32:
 // beta, log2(alpha), and mu / beta written as ys / (x_mu (1 + ys)^2) with
 // x_mu = lambda^2 n^2 and ys = 2^-|beta log2(x_mu / alpha)|.
