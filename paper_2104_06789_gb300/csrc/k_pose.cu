@@ -504,7 +504,7 @@ void score_hyps_from_host(const DevParams& p, const DevState& s, int n, cudaStre
 // below ms_tol, when a step below 1e-7 no longer contracts (the FP32 noise
 // floor of the kernel weights), or after ms_max_iter steps.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double warp_sum_d(double v)
+__device__ __forceinline__ float warp_sum_f(float v)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -587,10 +587,12 @@ k_meanshift(DevParams p, DevState s, int t)
             acc[1] = fmaf(kw, q0.x, acc[1]); acc[2] = fmaf(kw, q0.y, acc[2]); acc[3] = fmaf(kw, q0.z, acc[3]);
             acc[4] = fmaf(kw, q0.w, acc[4]); acc[5] = fmaf(kw, q1.x, acc[5]); acc[6] = fmaf(kw, q1.y, acc[6]);
         }
-        double accd[7];
-        for (int c = 0; c < 7; ++c) accd[c] = warp_sum_d((double)acc[c]);
+        // warp sums in FP32 (each lane holds at most 4 terms; a warp-wide FP64 add
+        // costs this GPU's FP64 pipe ~16 cycles), the rest of the reduction in FP64
+        float accw[7];
+        for (int c = 0; c < 7; ++c) accw[c] = warp_sum_f(acc[c]);
         if (lane == 0)
-            for (int c = 0; c < 7; ++c) wred[warp][c] = accd[c];
+            for (int c = 0; c < 7; ++c) wred[warp][c] = (double)accw[c];
         __syncthreads();
         const int buf = it & 1;
         if (tid < 7) {
@@ -612,8 +614,9 @@ k_meanshift(DevParams p, DevState s, int t)
                 flag = (it == 0) ? 2 : 1;
             } else {
                 double step = 0.0;
+                const double inv = 1.0 / tot[0];
                 for (int c = 0; c < 6; ++c) {
-                    const double xn = seedp[c] + tot[1 + c] / tot[0];
+                    const double xn = seedp[c] + tot[1 + c] * inv;
                     step += (xn - xs[c]) * (xn - xs[c]);
                     xs[c] = xn;
                 }
