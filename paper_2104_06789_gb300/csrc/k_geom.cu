@@ -2,8 +2,8 @@
 // scoring's per-pixel records), the E-step emissions (also the unsmoothed
 // rigidness update) and forward-backward smoothing of the rigidness.
 //
-// Geometry is FP64 and likelihood arithmetic FP32 (geom_prev, k_emissions,
-// neg_ell). Unlike the MIE sweep's translation unit this one is compiled with
+// Geometry is FP64 and likelihood arithmetic FP32 (k_prep_count/k_prep_write,
+// k_emissions, neg_ell). Unlike the MIE sweep's translation unit this one is compiled with
 // FMA contraction: none of its results is compared bit for bit with another
 // kernel's, and fused FP64 multiply-adds halve the FP64 instructions of the
 // geometry (this GPU's FP64 rate is a small fraction of its FP32 rate).
@@ -13,7 +13,12 @@ namespace vd {
 
 // ---------------------------------------------------------------------------
 // Pose preparation of frame t: one record per pixel whose pi_{t-1} is valid,
-// compacted in pixel order (count pass, then write pass with block offsets).
+// compacted in pixel order. The count pass computes each pixel's point in
+// camera t-1, P = C_{t-1} theta K^-1 [x y 1] (FP64), its reciprocal depth and
+// pi_{t-1}, stores them (SoA, pix_geo[6][N]) and counts the valid pixels per
+// block; the write pass reads them back (valid iff P_z > 0 and pi_{t-1} inside
+// the image, the same test on the same values), samples the flow at pi_{t-1}
+// bilinearly (FP64) and writes the records at block offsets.
 // ---------------------------------------------------------------------------
 __global__ void k_prep_count(DevParams p, DevState s, int t)
 {
@@ -21,17 +26,42 @@ __global__ void k_prep_count(DevParams p, DevState s, int t)
     if (threadIdx.x < 12) C[threadIdx.x] = s.cum[12 * (t - 1) + threadIdx.x];
     __syncthreads();
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = j < p.N && geom_prev_valid(p, C, t, j % p.W, j / p.W, s.theta[j]);
+    bool valid = false;
+    if (j < p.N) {
+        const int x = j % p.W, y = j / p.W;
+        const double th = (double)s.theta[j];
+        const double dx = ((double)x - p.cxd) * p.inv_fxd, dy = ((double)y - p.cyd) * p.inv_fyd;
+        double Px = th * dx, Py = th * dy, Pz = th, u = (double)x, v = (double)y, iz = 0.0;
+        if (t > 1) {
+            const double X = Px, Y = Py, Z = Pz;
+            Px = C[0] * X + C[1] * Y + C[2] * Z + C[3];
+            Py = C[4] * X + C[5] * Y + C[6] * Z + C[7];
+            Pz = C[8] * X + C[9] * Y + C[10] * Z + C[11];
+        }
+        if (Pz > 0.0) {
+            iz = rcp64(Pz);
+            if (t > 1) {
+                u = p.fxd * Px * iz + p.cxd;
+                v = p.fyd * Py * iz + p.cyd;
+            }
+        }
+        valid = Pz > 0.0 && u >= 0.0 && u <= (double)(p.W - 1) && v >= 0.0 && v <= (double)(p.H - 1);
+        const size_t N = (size_t)p.N;
+        s.pix_geo[j] = Px;
+        s.pix_geo[N + j] = Py;
+        s.pix_geo[2 * N + j] = Pz;
+        s.pix_geo[3 * N + j] = u;
+        s.pix_geo[4 * N + j] = v;
+        s.pix_geo[5 * N + j] = iz;
+    }
     const int cnt = __syncthreads_count(valid);
     if (threadIdx.x == 0) s.pix_block_count[blockIdx.x] = cnt;
 }
 
 __global__ void k_prep_write(DevParams p, DevState s, int t)
 {
-    __shared__ double C[12];
     __shared__ int warp_sum[kPixThreads / 32];
     __shared__ int base;
-    if (threadIdx.x < 12) C[threadIdx.x] = s.cum[12 * (t - 1) + threadIdx.x];
     // offset of this block: sum of the counts of all earlier blocks
     int acc = 0;
     for (int b = threadIdx.x; b < (int)blockIdx.x; b += blockDim.x) acc += s.pix_block_count[b];
@@ -45,9 +75,18 @@ __global__ void k_prep_write(DevParams p, DevState s, int t)
     }
     __syncthreads();
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t N = (size_t)p.N;
     bool valid = false;
-    GeomD g;
-    if (j < p.N) valid = geom_prev(p, C, s.flows, t, j % p.W, j / p.W, s.theta[j], g);
+    double Px = 0.0, Py = 0.0, iz = 0.0, u = 0.0, v = 0.0;
+    if (j < p.N) {
+        Px = s.pix_geo[j];
+        Py = s.pix_geo[N + j];
+        const double Pz = s.pix_geo[2 * N + j];
+        u = s.pix_geo[3 * N + j];
+        v = s.pix_geo[4 * N + j];
+        iz = s.pix_geo[5 * N + j];
+        valid = Pz > 0.0 && u >= 0.0 && u <= (double)(p.W - 1) && v >= 0.0 && v <= (double)(p.H - 1);
+    }
     const unsigned bal = __ballot_sync(0xffffffffu, valid);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __syncthreads();
@@ -56,20 +95,28 @@ __global__ void k_prep_write(DevParams p, DevState s, int t)
     int rank = __popc(bal & ((1u << lane) - 1u));
     for (int w = 0; w < warp; ++w) rank += warp_sum[w];
     if (valid) {
-        const float n = sqrtf((float)(g.fu * g.fu + g.fv * g.fv));
-        const double iz = rcp64(g.Pz);
+        const int x0 = min((int)floor(u), p.W - 2), y0 = min((int)floor(v), p.H - 2);
+        const double ax = u - x0, ay = v - y0;
+        const size_t fb = (size_t)(t - 1) * N + (size_t)y0 * p.W + x0;
+        const float2 f00 = load_flow(s.flows, p.flow_f16, fb), f10 = load_flow(s.flows, p.flow_f16, fb + 1);
+        const float2 f01 = load_flow(s.flows, p.flow_f16, fb + p.W);
+        const float2 f11 = load_flow(s.flows, p.flow_f16, fb + p.W + 1);
+        const double w00 = (1.0 - ax) * (1.0 - ay), w10 = ax * (1.0 - ay), w01 = (1.0 - ax) * ay, w11 = ax * ay;
+        const double fu = w00 * f00.x + w10 * f10.x + w01 * f01.x + w11 * f11.x;
+        const double fv = w00 * f00.y + w10 * f10.y + w01 * f01.y + w11 * f11.y;
+        const float n = sqrtf((float)(fu * fu + fv * fv));
         PixRec r;
-        r.a = make_float4((float)(g.Px * iz), (float)(p.fy_over_fx_d * g.Py * iz), (float)iz, (float)(g.fu * p.inv_fxd));
+        r.a = make_float4((float)(Px * iz), (float)(p.fy_over_fx_d * Py * iz), (float)iz, (float)(fu * p.inv_fxd));
         if (p.residual == VOLDOR_RESIDUAL_GAUSSIAN) {
             const GaussConst gc = gauss_const(p, n);
-            r.b = make_float4((float)(g.fv * p.inv_fxd), (float)(p.fxd * p.fxd) * gc.inv_alpha, -gc.x_mu * gc.inv_alpha,
+            r.b = make_float4((float)(fv * p.inv_fxd), (float)(p.fxd * p.fxd) * gc.inv_alpha, -gc.x_mu * gc.inv_alpha,
                               0.f);
         } else {
             const FiskConst fc = fisk_const(p, n);
-            r.b = make_float4((float)(g.fv * p.inv_fxd), fc.beta, fc.beta * (p.log2_fx2 - fc.log2_alpha),
+            r.b = make_float4((float)(fv * p.inv_fxd), fc.beta, fc.beta * (p.log2_fx2 - fc.log2_alpha),
                               (float)(p.fxd * p.fxd) * fc.mu_over_beta);
         }
-        r.c = make_float4(s.wmap[(size_t)(t - 1) * p.N + j], 0.f, 0.f, 0.f);
+        r.c = make_float4(s.wmap[(size_t)(t - 1) * N + j], 0.f, 0.f, 0.f);
         s.pix[base + rank] = r;
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {

@@ -74,6 +74,7 @@ struct DevState {
     // dense scoring scratch
     PixRec* pix;              // [N] compacted valid pixels of the current frame
     int* pix_block_count;     // [ceil(N / kPixThreads)]
+    double* pix_geo;          // [6][N] P_x, P_y, P_z in camera t-1, pi_{t-1} (u, v), 1 / P_z of the frame being prepared
     int* pix_count;           // [1]
     // P3P
     double* grp_sols;         // [G][4][12]
@@ -160,19 +161,10 @@ __device__ __forceinline__ bool flow_bilinear(const DevParams& p, const void* fl
 }
 
 // ---------------------------------------------------------------------------
-// Per-pixel geometry of frame t (1-based) at depth `depth`, in FP64: the point
-// P in camera t-1 (Eq. 1 with C_{t-1}), pi_{t-1}, and the observed flow
-// X_t(pi_{t-1}) by bilinear interpolation. The per-pixel passes keep the
-// geometry in FP64 because the rigid flow (tens of px) cancels against the
-// observed flow down to residuals of a tenth of a pixel; the likelihood
-// arithmetic that follows is FP32. False if P_z <= 0 or pi_{t-1} leaves
-// [0, W-1] x [0, H-1].
+// Per-pixel geometry (Eq. 1) is FP64 in the per-pixel passes because the rigid
+// flow (tens of px) cancels against the observed flow down to residuals of a
+// tenth of a pixel; the likelihood arithmetic that follows is FP32.
 // ---------------------------------------------------------------------------
-struct GeomD {
-    double Px, Py, Pz;    // point in camera t-1
-    double u, v;          // pi_{t-1}
-    double fu, fv;        // observed flow X_t(pi_{t-1})
-};
 
 // 1/d in FP64 from the SFU reciprocal and two Newton steps (full double
 // precision for normal d; falls back to division outside [1e-30, 1e30]).
@@ -185,60 +177,6 @@ __device__ __forceinline__ double rcp64(double d)
     r = fma(r, e, r);
     e = fma(-d, r, 1.0);
     return fma(r, e, r);
-}
-
-__device__ __forceinline__ bool geom_prev(const DevParams& p, const double* C, const void* flows, int t, int x, int y,
-                                          float depth, GeomD& g)
-{
-    const double th = (double)depth;
-    const double dx = ((double)x - p.cxd) * p.inv_fxd, dy = ((double)y - p.cyd) * p.inv_fyd;
-    if (t == 1) {
-        g.Px = th * dx; g.Py = th * dy; g.Pz = th;
-        g.u = (double)x; g.v = (double)y;
-        if (!(th > 0.0)) return false;
-    } else {
-        const double X = th * dx, Y = th * dy, Z = th;
-        g.Px = C[0] * X + C[1] * Y + C[2] * Z + C[3];
-        g.Py = C[4] * X + C[5] * Y + C[6] * Z + C[7];
-        g.Pz = C[8] * X + C[9] * Y + C[10] * Z + C[11];
-        if (!(g.Pz > 0.0)) return false;
-        const double iz = rcp64(g.Pz);
-        g.u = p.fxd * g.Px * iz + p.cxd;
-        g.v = p.fyd * g.Py * iz + p.cyd;
-    }
-    if (!(g.u >= 0.0 && g.u <= (double)(p.W - 1) && g.v >= 0.0 && g.v <= (double)(p.H - 1))) return false;
-    const int x0 = min((int)floor(g.u), p.W - 2), y0 = min((int)floor(g.v), p.H - 2);
-    const double ax = g.u - x0, ay = g.v - y0;
-    const size_t base = (size_t)(t - 1) * p.N + (size_t)y0 * p.W + x0;
-    const float2 f00 = load_flow(flows, p.flow_f16, base), f10 = load_flow(flows, p.flow_f16, base + 1);
-    const float2 f01 = load_flow(flows, p.flow_f16, base + p.W), f11 = load_flow(flows, p.flow_f16, base + p.W + 1);
-    const double w00 = (1.0 - ax) * (1.0 - ay), w10 = ax * (1.0 - ay), w01 = (1.0 - ax) * ay, w11 = ax * ay;
-    g.fu = w00 * f00.x + w10 * f10.x + w01 * f01.x + w11 * f11.x;
-    g.fv = w00 * f00.y + w10 * f10.y + w01 * f01.y + w11 * f11.y;
-    return true;
-}
-
-// Whether (t, j) has an observation at pi_{t-1}: geom_prev's test without the
-// flow sample (same arithmetic, so the same decision).
-__device__ __forceinline__ bool geom_prev_valid(const DevParams& p, const double* C, int t, int x, int y, float depth)
-{
-    const double th = (double)depth;
-    const double dx = ((double)x - p.cxd) * p.inv_fxd, dy = ((double)y - p.cyd) * p.inv_fyd;
-    double u, v;
-    if (t == 1) {
-        if (!(th > 0.0)) return false;
-        u = (double)x; v = (double)y;
-    } else {
-        const double X = th * dx, Y = th * dy, Z = th;
-        const double Px = C[0] * X + C[1] * Y + C[2] * Z + C[3];
-        const double Py = C[4] * X + C[5] * Y + C[6] * Z + C[7];
-        const double Pz = C[8] * X + C[9] * Y + C[10] * Z + C[11];
-        if (!(Pz > 0.0)) return false;
-        const double iz = rcp64(Pz);
-        u = p.fxd * Px * iz + p.cxd;
-        v = p.fyd * Py * iz + p.cyd;
-    }
-    return u >= 0.0 && u <= (double)(p.W - 1) && v >= 0.0 && v <= (double)(p.H - 1);
 }
 
 // Stages C_{t-1} and T_t of every frame in shared memory.
