@@ -3,10 +3,11 @@
 // rigidness update) and forward-backward smoothing of the rigidness.
 //
 // Geometry is FP64 and likelihood arithmetic FP32 (k_prep_count/k_prep_write,
-// k_emissions, neg_ell). Unlike the MIE sweep's translation unit this one is compiled with
-// FMA contraction: none of its results is compared bit for bit with another
-// kernel's, and fused FP64 multiply-adds halve the FP64 instructions of the
-// geometry (this GPU's FP64 rate is a small fraction of its FP32 rate).
+// k_emissions, neg_ell). Unlike the MIE sweep's translation unit this one is
+// compiled with FMA contraction: none of its results is compared bit for bit
+// with another kernel's, and fused FP64 multiply-adds cut the FP64
+// instructions of the geometry (this GPU's FP64 rate is a small fraction of
+// its FP32 rate).
 #include "voldor_internal.cuh"
 
 namespace vd {
