@@ -17,9 +17,10 @@ namespace vd {
 // compacted in pixel order. The count pass computes each pixel's point in
 // camera t-1, P = C_{t-1} theta K^-1 [x y 1] (FP64), its reciprocal depth and
 // pi_{t-1}, stores them (SoA, pix_geo[6][N]) and counts the valid pixels per
-// block; the write pass reads them back (valid iff P_z > 0 and pi_{t-1} inside
-// the image, the same test on the same values), samples the flow at pi_{t-1}
-// bilinearly (FP64) and writes the records at block offsets.
+// block, and its last block to finish scans the counts into block offsets;
+// the write pass reads them back (valid iff P_z > 0 and pi_{t-1} inside the
+// image, the same test on the same values), samples the flow at pi_{t-1}
+// bilinearly (FP64) and writes the records at its block's offset.
 // ---------------------------------------------------------------------------
 __global__ void k_prep_count(DevParams p, DevState s, int t)
 {
@@ -56,25 +57,49 @@ __global__ void k_prep_count(DevParams p, DevState s, int t)
         s.pix_geo[5 * N + j] = iz;
     }
     const int cnt = __syncthreads_count(valid);
-    if (threadIdx.x == 0) s.pix_block_count[blockIdx.x] = cnt;
+    // the last block to finish turns the block counts into block offsets
+    // (exclusive scan, in place) and sets the record count; no block waits
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        s.pix_block_count[blockIdx.x] = cnt;
+        __threadfence();
+        last = atomicAdd(s.prep_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int nb = gridDim.x, per = (nb + blockDim.x - 1) / blockDim.x;
+    const int b0 = min((int)threadIdx.x * per, nb), b1 = min(b0 + per, nb);
+    volatile int* counts = s.pix_block_count;
+    int local = 0;
+    for (int b = b0; b < b1; ++b) local += counts[b];
+    __shared__ int wsum[kPixThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    int off = before + incl - local;
+    for (int b = b0; b < b1; ++b) {
+        const int c = counts[b];
+        counts[b] = off;
+        off += c;
+    }
+    if (threadIdx.x == blockDim.x - 1) {
+        *s.pix_count = off;
+        *s.prep_done = 0u;
+    }
 }
 
 __global__ void k_prep_write(DevParams p, DevState s, int t)
 {
     __shared__ int warp_sum[kPixThreads / 32];
-    __shared__ int base;
-    // offset of this block: sum of the counts of all earlier blocks
-    int acc = 0;
-    for (int b = threadIdx.x; b < (int)blockIdx.x; b += blockDim.x) acc += s.pix_block_count[b];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int tot = 0;
-        for (int w = 0; w < kPixThreads / 32; ++w) tot += warp_sum[w];
-        base = tot;
-    }
-    __syncthreads();
+    const int base = s.pix_block_count[blockIdx.x];      // this block's offset (set by the count pass)
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const size_t N = (size_t)p.N;
     bool valid = false;
@@ -119,11 +144,6 @@ __global__ void k_prep_write(DevParams p, DevState s, int t)
         }
         r.c = make_float4(s.wmap[(size_t)(t - 1) * N + j], 0.f, 0.f, 0.f);
         s.pix[base + rank] = r;
-    }
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
-        int tot = base;
-        for (int w = 0; w < kPixThreads / 32; ++w) tot += warp_sum[w];
-        *s.pix_count = tot;
     }
 }
 

@@ -138,6 +138,7 @@ size_t layout(voldor_ctx& c, char* base)
     s.pix = (PixRec*)take(N * sizeof(PixRec));
     s.pix_block_count = (int*)take(((N + kPixThreads - 1) / kPixThreads) * 4);
     s.pix_geo = (double*)take(6 * N * sizeof(double));
+    s.prep_done = (unsigned*)take(4);
     s.pix_count = (int*)take(4);
     s.grp_sols = (double*)take(G * kMaxSols * 12 * 8);
     s.grp_weight = (double*)take(G * 8);

@@ -73,7 +73,8 @@ struct DevState {
     int* status;              // [4] n_hyp, seed, meanshift steps, status bits
     // dense scoring scratch
     PixRec* pix;              // [N] compacted valid pixels of the current frame
-    int* pix_block_count;     // [ceil(N / kPixThreads)]
+    int* pix_block_count;     // [ceil(N / kPixThreads)] valid pixels per block, then the blocks' record offsets
+    unsigned* prep_done;      // [1] blocks of the count pass finished (0 between launches)
     double* pix_geo;          // [6][N] P_x, P_y, P_z in camera t-1, pi_{t-1} (u, v), 1 / P_z of the frame being prepared
     int* pix_count;           // [1]
     // P3P
