@@ -50,7 +50,7 @@ typedef enum {
 } voldor_status;
 
 enum { VOLDOR_FLOW_F32 = 0, VOLDOR_FLOW_F16 = 1 };
-enum { VOLDOR_BOOT_GIVEN_POSE = 0 };
+enum { VOLDOR_BOOT_GIVEN_POSE = 0, VOLDOR_BOOT_EPIPOLAR = 2 };
 
 typedef struct { double fx, fy, cx, cy; } voldor_intrinsics;
 
@@ -106,12 +106,18 @@ voldor_status voldor_init_window(voldor_ctx** out, int width, int height, int T,
 voldor_status voldor_set_flows(voldor_ctx* ctx, const void* flows, int flows_on_device);
 
 /* Bootstrap (Table 1, first three lines): W := 1 everywhere; T_1 := the given
- * pose (mode VOLDOR_BOOT_GIVEN_POSE, Sec. 5.3 "from previous estimates");
+ * pose (mode VOLDOR_BOOT_GIVEN_POSE, Sec. 5.3 "from previous estimates"), or
+ * (mode VOLDOR_BOOT_EPIPOLAR, T1_rowmajor_4x4 ignored and may be NULL) the
+ * epipolar estimate of voldor_bootstrap_epipolar with 512 samples and
+ * |t_1| = 1 (the monocular scale convention of that mode); the learned
+ * bootstrap is voldor_bootstrap_learned (it needs the network);
  * T_t := T_1 for t >= 2 (used only when a frame has no weighted hypothesis);
  * theta by two-view triangulation of x_j + X_1^j along the ray of pixel j
  * (least squares over the two projection equations, inverse depth clamped to
  * [inv_depth_min, inv_depth_max], non-positive depth sent to the far end).
- * Resets the iteration counter k to 0. T1_rowmajor_4x4: host, 16 doubles. */
+ * Resets the iteration counter k to 0. T1_rowmajor_4x4: host, 16 doubles.
+ * Errors: INVALID_ARG (unknown mode, NULL or non-finite T_1 for GIVEN_POSE),
+ * CUDA; with EPIPOLAR also those of voldor_bootstrap_epipolar. */
 voldor_status voldor_bootstrap(voldor_ctx* ctx, int mode, const double* T1_rowmajor_4x4);
 
 /* Epipolar bootstrap (Sec. 5.3 and Table 1, second line: T_1 from the

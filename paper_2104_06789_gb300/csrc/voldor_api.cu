@@ -429,6 +429,7 @@ voldor_status voldor_bootstrap(voldor_ctx* c, int mode, const double* T1)
 {
     if (!c) return VOLDOR_ERR_INVALID_ARG;
     if (c->poisoned) return kCuda;
+    if (mode == VOLDOR_BOOT_EPIPOLAR) return voldor_bootstrap_epipolar(c, 512, 1.0, nullptr);
     if (mode != VOLDOR_BOOT_GIVEN_POSE || !T1) return VOLDOR_ERR_INVALID_ARG;
     for (int i = 0; i < 12; ++i)
         if (!std::isfinite(T1[i])) return VOLDOR_ERR_INVALID_ARG;

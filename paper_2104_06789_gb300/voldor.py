@@ -20,7 +20,7 @@ FLOW_F32, FLOW_F16 = 0, 1
 LEARNED_DEPTH, LEARNED_RIGIDNESS = 1, 2
 CRITERION_MIE, CRITERION_MLE = 0, 1
 RESIDUAL_FISK, RESIDUAL_GAUSSIAN = 0, 1
-BOOT_GIVEN_POSE = 0
+BOOT_GIVEN_POSE, BOOT_EPIPOLAR = 0, 2
 (BUF_SMOOTHED, BUF_LABELS, BUF_HYPS, BUF_HYP_INFO, BUF_HYP_WEIGHT, BUF_SCORES, BUF_POSE_INFO,
  BUF_DEPTH_SAMPLES, BUF_HYPS_F32, BUF_EPI_E, BUF_EPI_MEDIANS, BUF_EPI_VALID, BUF_EPI_INFO,
  BUF_EPI_REFINED) = range(14)

@@ -127,3 +127,22 @@ def test_invalid_arguments(vd):
     for n, b in [(0, 1.0), (vd.EPI_MAX_SAMPLES + 1, 1.0), (8, 0.0), (8, float("nan")), (8, -1.0)]:
         assert L.voldor_bootstrap_epipolar(g._h, n, b, None) == vd.ERR_INVALID_ARG
     g.destroy()
+
+
+def test_bootstrap_mode_epipolar_equals_the_epipolar_call(vd):
+    """voldor_bootstrap(ctx, VOLDOR_BOOT_EPIPOLAR, NULL) is the epipolar
+    bootstrap with 512 samples and |t_1| = 1: same poses, depth and state."""
+    w = synthetic.driving(seed=3001, W=414, H=125, f=239.3, T=3)
+    p = vd.default_params(inv_depth_min=w.inv_depth_range[0], inv_depth_max=w.inv_depth_range[1],
+                          hyps_per_frame=64, groups_per_frame=128)
+    a = vd.Window(w.flows.astype(np.float32), w.K, p)
+    b = vd.Window(w.flows.astype(np.float32), w.K, p)
+    T1 = a.bootstrap_epipolar(512, 1.0)
+    assert vd.lib().voldor_bootstrap(b._h, vd.BOOT_EPIPOLAR, None) == vd.OK
+    Pa, Da, Wa = a.get_pose_depth_rigidness()
+    Pb, Db, Wb = b.get_pose_depth_rigidness()
+    assert np.array_equal(Pa, Pb) and np.array_equal(Da, Db) and np.array_equal(Wa, Wb)
+    assert np.linalg.norm(T1[:3, 3]) == pytest.approx(1.0, rel=1e-12)
+    assert vd.lib().voldor_bootstrap(b._h, 1, None) == vd.ERR_INVALID_ARG      # the learned mode needs the network
+    a.destroy()
+    b.destroy()
