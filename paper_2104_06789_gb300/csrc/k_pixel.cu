@@ -184,7 +184,7 @@ __device__ __forceinline__ float depth_ell_fast(const DevParams& p, const float*
 //   resolve  per chain: follow r -> end of run from the chain start; a run
 //            that reached the cap is continued on the fly.
 // ---------------------------------------------------------------------------
-constexpr int kRunCap = 32;
+constexpr int kRunCap = 8;
 
 __device__ __forceinline__ float nan_to_ninf(float v) { return isnan(v) ? -INFINITY : v; }
 
