@@ -35,7 +35,12 @@ sys.path.insert(0, ROOT)
 METRIC = "Mpixel·frame EM updates/s at 1242x375 T=8; learned vs plain time-to-equal-pose-error"
 UNIT = "Mpixel*frame/s"
 MUFU_PER_SM_PER_CLK = 16          # 4 SFU lanes per SM sub-partition, 4 sub-partitions
-ALGO_MUFU_PER_PAIR = 4            # rcp (projection), lg2 + ex2 ((x/alpha)^beta), lg2 (log(1+mu/rho))
+# algorithmic SFU operations per hypothesis-pixel pair, (rcp, lg2, ex2), by
+# (criterion, residual model): the projection's reciprocal; Fisk: lg2 + ex2 for
+# (x/alpha)^beta and lg2 of 1 + mu/rho (MIE) or of mu/rho (MLE); Gaussian:
+# log2(mu/rho) is linear in x, MIE adds ex2 + lg2 for log2(1 + 2^-|s|)
+ALGO_MUFU_MIX = {("mie", "fisk"): (1, 2, 1), ("mle", "fisk"): (1, 2, 1),
+                 ("mie", "gaussian"): (1, 1, 1), ("mle", "gaussian"): (1, 0, 0)}
 NOMINAL_SMS, NOMINAL_MAX_MHZ = 152, 2070.0
 
 
@@ -47,6 +52,10 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--iters", type=int, default=5)
     ap.add_argument("--hyps", type=int, default=8192)
+    ap.add_argument("--criterion", choices=["mie", "mle"], default="mie",
+                    help="depth and pose criterion (MLE: the ablation variant)")
+    ap.add_argument("--residual", choices=["fisk", "gaussian"], default="fisk",
+                    help="flow residual model (Gaussian: the ablation variant)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch", type=int, default=0,
@@ -93,7 +102,8 @@ def config_dict(w, args, world):
     return {"workload": w.name, "width": w.W, "height": w.H, "T": w.T, "em_iters": args.iters,
             "hyps_per_frame": args.hyps, "groups_per_frame": 2 * args.hyps, "flows": "fp16",
             "focal_px": w.K[0], "windows_per_rank": 1, "parallelism": f"replicas x{world}",
-            "l2": "flushed between timed steps (256 MiB write)"}
+            "l2": "flushed between timed steps (256 MiB write)",
+            "criterion": args.criterion, "residual": args.residual}
 
 
 # ---------------------------------------------------------------------------
@@ -153,7 +163,13 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle on a bounded sample of the same window
 # ---------------------------------------------------------------------------
-def oracle_sample(w, S, iters, n_score_hyps=4, n_groups=64):
+def variant_overrides(args):
+    """Oracle parameters of the variant `args` selects (criterion 1 = MLE,
+    residual 1 = Gaussian; 0 the paper's MIE and Fisk model)."""
+    return {"criterion": int(args.criterion == "mle"), "residual": int(args.residual == "gaussian")}
+
+
+def oracle_sample(w, S, iters, n_score_hyps=4, n_groups=64, variant=None):
     """Times the FP64 oracle on parts of one EM iteration of window `w` and
     scales each part linearly to the full configuration: dense scoring of
     n_score_hyps hypotheses per frame (cost linear in S), collection of
@@ -164,7 +180,7 @@ def oracle_sample(w, S, iters, n_score_hyps=4, n_groups=64):
     oracle.build()
     flows = w.flows.astype(np.float16).astype(np.float64)
     ow = oracle.OracleWindow(flows, w.K, S=n_groups * 4, G=n_groups, inv_depth_min=w.inv_depth_range[0],
-                             inv_depth_max=w.inv_depth_range[1])
+                             inv_depth_max=w.inv_depth_range[1], **(variant or {}))
     ow.bootstrap(w.poses[0])
     t0 = time.perf_counter()
     for t in range(1, w.T + 1):
@@ -195,11 +211,11 @@ def _oracle_piece(args):
     """One process's share of the parallel oracle sample: dense scoring of the
     sampled hypotheses and the sampled group collection, for frame t.
     Returns (scoring seconds, groups seconds)."""
-    flows16, K, poses, inv_range, t, n_score_hyps, n_groups = args
+    flows16, K, poses, inv_range, t, n_score_hyps, n_groups, variant = args
     import oracle
     flows = flows16.astype(np.float64)
     ow = oracle.OracleWindow(flows, K, S=n_groups * 4, G=n_groups, inv_depth_min=inv_range[0],
-                             inv_depth_max=inv_range[1])
+                             inv_depth_max=inv_range[1], **variant)
     ow.bootstrap(poses[0])
     R = np.tile(poses[t - 1][:3, :3], (n_score_hyps, 1, 1))
     tv = np.tile(poses[t - 1][:3, 3], (n_score_hyps, 1))
@@ -211,7 +227,7 @@ def _oracle_piece(args):
     return t_score, time.perf_counter() - t0
 
 
-def oracle_sample_parallel(w, S, iters, workers, n_score_hyps=4, n_groups=64):
+def oracle_sample_parallel(w, S, iters, workers, n_score_hyps=4, n_groups=64, variant=None):
     """The same sample as oracle_sample with its independent pieces (the
     frames' dense scoring and group collection) spread over `workers` spawned
     processes, each running the unchanged single-threaded oracle; the
@@ -221,7 +237,8 @@ def oracle_sample_parallel(w, S, iters, workers, n_score_hyps=4, n_groups=64):
     import oracle
     oracle.build()
     f16 = w.flows.astype(np.float16)
-    jobs = [(f16, w.K, w.poses, w.inv_depth_range, t, n_score_hyps, n_groups) for t in range(1, w.T + 1)]
+    jobs = [(f16, w.K, w.poses, w.inv_depth_range, t, n_score_hyps, n_groups, variant or {})
+            for t in range(1, w.T + 1)]
     keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
     saved = {k: os.environ.get(k) for k in keys}
     os.environ.update({k: "1" for k in keys})
@@ -245,7 +262,7 @@ def oracle_sample_parallel(w, S, iters, workers, n_score_hyps=4, n_groups=64):
     n_proc = min(workers, len(jobs))
     flows = f16.astype(np.float64)
     ow = oracle.OracleWindow(flows, w.K, S=n_groups * 4, G=n_groups, inv_depth_min=w.inv_depth_range[0],
-                             inv_depth_max=w.inv_depth_range[1])
+                             inv_depth_max=w.inv_depth_range[1], **(variant or {}))
     ow.bootstrap(w.poses[0])
     t0 = time.perf_counter()
     em = ow.emissions()
@@ -281,7 +298,7 @@ def run_reference(args):
     desc, n_proc = "", 1
     for i in range(args.warmup + args.steps):
         v, secs, desc, n_proc = oracle_sample_parallel(w, args.hyps, args.iters, os.cpu_count() or 1,
-                                                       n_score_hyps=2, n_groups=32)
+                                                       n_score_hyps=2, n_groups=32, variant=variant_overrides(args))
         if i >= args.warmup:
             steps.append(v)
     value = float(np.mean(steps))
@@ -319,7 +336,10 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     params = voldor.default_params(hyps_per_frame=args.hyps, groups_per_frame=2 * args.hyps,
                                    inv_depth_min=w.inv_depth_range[0], inv_depth_max=w.inv_depth_range[1],
-                                   seed=0, window_id=rank)
+                                   seed=0, window_id=rank,
+                                   criterion={"mie": voldor.CRITERION_MIE, "mle": voldor.CRITERION_MLE}[args.criterion],
+                                   residual={"fisk": voldor.RESIDUAL_FISK,
+                                             "gaussian": voldor.RESIDUAL_GAUSSIAN}[args.residual])
     dev_flows = torch.from_numpy(flows16).to(f"cuda:{local_rank}")
     torch.cuda.synchronize()
     win = voldor.Window(dev_flows, w.K, params, stream=stream)
@@ -387,28 +407,32 @@ def run_ours(args):
 
     props = torch.cuda.get_device_properties(local_rank)
     sms = props.multi_processor_count
-    # SFU results per SM clock, measured on this GPU (exp2, log2, reciprocal);
-    # the algorithmic mix per pair is 1 rcp + 2 lg2 + 1 ex2
+    # SFU results per SM clock, measured on this GPU (exp2, log2, reciprocal),
+    # combined over the variant's algorithmic mix per pair
     rates = {name: voldor.probe_sfu_rate(op) for op, name in enumerate(("ex2", "lg2", "rcp"))}
-    per_clk = ALGO_MUFU_PER_PAIR / (1.0 / rates["rcp"] + 2.0 / rates["lg2"] + 1.0 / rates["ex2"])
+    mix = dict(zip(("rcp", "lg2", "ex2"), ALGO_MUFU_MIX[(args.criterion, args.residual)]))
+    ops_per_pair = sum(mix.values())
+    per_clk = ops_per_pair / sum(n / rates[op] for op, n in mix.items())
     peak = sms * per_clk * NOMINAL_MAX_MHZ * 1e6 / 1e12                # T SFU-ops/s
     score_ms = np.array(score_ms)
     score_pairs = np.array(score_pairs, dtype=np.float64)
-    achieved = float(np.mean(ALGO_MUFU_PER_PAIR * score_pairs / (score_ms * 1e-3)) / 1e12) if len(score_ms) else None
+    achieved = float(np.mean(ops_per_pair * score_pairs / (score_ms * 1e-3)) / 1e12) if len(score_ms) else None
+    mix_txt = " + ".join(f"{n} {op}" for op, n in mix.items() if n)
     roofline = {"kernel": "k_score (dense hypothesis scoring)", "bound": "alu", "achieved": achieved,
-                "peak": peak, "unit": "T SFU-op/s (4 algorithmic SFU ops per hypothesis-pixel pair)",
+                "peak": peak, "unit": f"T SFU-op/s ({ops_per_pair} algorithmic SFU ops per hypothesis-pixel pair)",
                 "frac": achieved / peak if achieved else None, "traffic": None,
                 "peak_source": (f"{sms} SMs x {per_clk:.2f} SFU results/clk/SM (measured: ex2 {rates['ex2']:.2f}, "
-                                f"lg2 {rates['lg2']:.2f}, rcp {rates['rcp']:.2f}; mix 1 rcp + 2 lg2 + 1 ex2) x "
+                                f"lg2 {rates['lg2']:.2f}, rcp {rates['rcp']:.2f}; mix {mix_txt}) x "
                                 f"{NOMINAL_MAX_MHZ:.0f} MHz; nominal table value 16/clk/SM"),
                 "launches_timed": int(len(score_ms)), "mean_launch_ms": float(score_ms.mean()) if len(score_ms) else None,
                 "share_of_step": float(score_ms.sum() / total_ms) if len(score_ms) else None}
 
     cpu = cpu_par = None
     if world == 1 and not args.no_cpu:
-        v, secs, desc = oracle_sample(w, args.hyps, args.iters)
+        v, secs, desc = oracle_sample(w, args.hyps, args.iters, variant=variant_overrides(args))
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
-        vp, secs_p, desc_p, n_proc = oracle_sample_parallel(w, args.hyps, args.iters, os.cpu_count() or 1)
+        vp, secs_p, desc_p, n_proc = oracle_sample_parallel(w, args.hyps, args.iters, os.cpu_count() or 1,
+                                                            variant=variant_overrides(args))
         cpu_par = {"value": vp, "unit": UNIT, "cores": n_proc, "kind": "oracle", "sample": desc_p}
 
     cfg = config_dict(w, args, world)

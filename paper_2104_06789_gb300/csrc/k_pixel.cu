@@ -13,29 +13,51 @@ namespace vd {
 // Frame setup: C_{t-1} = T_{t-1} ... T_1 for every t (FP64), the product of
 // Eq. 1 with T_t the motion from t-1 to t.
 // ---------------------------------------------------------------------------
+// One warp: the poses are staged in shared memory, then thread c < 4 carries
+// column c of C (O = A C is column by column: O[:, c] = A[:, :3] C[:, c], plus
+// A's translation for c = 3), each element added in the same order as the
+// row-by-row product.
 __global__ void k_frame_setup(DevParams p, DevState s)
 {
-    if (threadIdx.x != 0) return;
-    double C[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
+    __shared__ double A[kMaxT * 12];
+    for (int i = threadIdx.x; i < p.T * 12; i += blockDim.x) A[i] = s.poses[i];
+    __syncthreads();
+    const int c = threadIdx.x;
+    if (c >= 4) return;
+    double C0 = c == 0 ? 1.0 : 0.0, C1 = c == 1 ? 1.0 : 0.0, C2 = c == 2 ? 1.0 : 0.0;
     for (int t = 1; t <= p.T; ++t) {
-        for (int q = 0; q < 12; ++q) s.cum[12 * (t - 1) + q] = C[q];
-        const double* A = s.poses + 12 * (t - 1);
+        double* cum = s.cum + 12 * (t - 1);
+        cum[c] = C0;
+        cum[4 + c] = C1;
+        cum[8 + c] = C2;
+        const double* At = A + 12 * (t - 1);
         float* f = s.frames32 + 24 * (t - 1);     // E_c = R_c - I, t_c, E_t = R_t - I, t_t
-        for (int r = 0; r < 3; ++r) {
-            for (int c = 0; c < 3; ++c) {
-                f[r * 3 + c] = (float)(C[r * 4 + c] - (r == c ? 1.0 : 0.0));
-                f[12 + r * 3 + c] = (float)(A[r * 4 + c] - (r == c ? 1.0 : 0.0));
-            }
-            f[9 + r] = (float)C[r * 4 + 3];
-            f[21 + r] = (float)A[r * 4 + 3];
+        if (c < 3) {
+            f[c] = (float)(C0 - (c == 0 ? 1.0 : 0.0));
+            f[3 + c] = (float)(C1 - (c == 1 ? 1.0 : 0.0));
+            f[6 + c] = (float)(C2 - (c == 2 ? 1.0 : 0.0));
+            f[12 + c] = (float)(At[c] - (c == 0 ? 1.0 : 0.0));
+            f[15 + c] = (float)(At[4 + c] - (c == 1 ? 1.0 : 0.0));
+            f[18 + c] = (float)(At[8 + c] - (c == 2 ? 1.0 : 0.0));
+        } else {
+            f[9] = (float)C0;
+            f[10] = (float)C1;
+            f[11] = (float)C2;
+            f[21] = (float)At[3];
+            f[22] = (float)At[7];
+            f[23] = (float)At[11];
         }
-        double O[12];
-        for (int r = 0; r < 3; ++r) {
-            for (int c = 0; c < 3; ++c)
-                O[r * 4 + c] = A[r * 4 + 0] * C[c] + A[r * 4 + 1] * C[4 + c] + A[r * 4 + 2] * C[8 + c];
-            O[r * 4 + 3] = A[r * 4 + 0] * C[3] + A[r * 4 + 1] * C[7] + A[r * 4 + 2] * C[11] + A[r * 4 + 3];
+        double n0 = At[0] * C0 + At[1] * C1 + At[2] * C2;
+        double n1 = At[4] * C0 + At[5] * C1 + At[6] * C2;
+        double n2 = At[8] * C0 + At[9] * C1 + At[10] * C2;
+        if (c == 3) {
+            n0 = n0 + At[3];
+            n1 = n1 + At[7];
+            n2 = n2 + At[11];
         }
-        for (int q = 0; q < 12; ++q) C[q] = O[q];
+        C0 = n0;
+        C1 = n1;
+        C2 = n2;
     }
 }
 

@@ -504,6 +504,8 @@ void score_hyps_from_host(const DevParams& p, const DevState& s, int n, cudaStre
 // below ms_tol, when a step below 1e-7 no longer contracts (the FP32 noise
 // floor of the kernel weights), or after ms_max_iter steps.
 // ---------------------------------------------------------------------------
+constexpr int kMsCached = 4;     // hypotheses per thread held in registers (all of them up to S = 8192)
+
 __device__ __forceinline__ float warp_sum_f(float v)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -557,14 +559,27 @@ k_meanshift(DevParams p, DevState s, int t)
     }
     __syncthreads();
     const int seed = bidx[0];
-    // FP32 offsets of this CTA's hypotheses from the seed
-    const int stride = kMeanshiftCtas * blockDim.x;
-    for (int h = rank * blockDim.x + tid; h < n; h += stride) {
-        float4* o = reinterpret_cast<float4*>(s.hyp_dp + (size_t)h * 8);
+    // FP32 offsets of this CTA's hypotheses from the seed: a thread's first
+    // kMsCached stay in registers, the rest (S above kMsCached x the cluster's
+    // threads) go to global memory
+    const int stride = kMeanshiftCtas * blockDim.x, h0 = rank * blockDim.x + tid;
+    float4 r0[kMsCached], r1[kMsCached];
+#pragma unroll
+    for (int k = 0; k < kMsCached; ++k) { r0[k] = make_float4(0.f, 0.f, 0.f, 0.f); r1[k] = r0[k]; }
+    for (int h = h0, k = 0; h < n; h += stride, ++k) {
         const double* ph = s.hyp_p + (size_t)h * 6;
-        o[0] = make_float4((float)(ph[0] - seedp[0]), (float)(ph[1] - seedp[1]), (float)(ph[2] - seedp[2]),
-                           (float)(ph[3] - seedp[3]));
-        o[1] = make_float4((float)(ph[4] - seedp[4]), (float)(ph[5] - seedp[5]), (float)s.hyp_w[h], 0.f);
+        const float4 o0 = make_float4((float)(ph[0] - seedp[0]), (float)(ph[1] - seedp[1]),
+                                      (float)(ph[2] - seedp[2]), (float)(ph[3] - seedp[3]));
+        const float4 o1 = make_float4((float)(ph[4] - seedp[4]), (float)(ph[5] - seedp[5]), (float)s.hyp_w[h], 0.f);
+        if (k < kMsCached) {
+#pragma unroll
+            for (int i = 0; i < kMsCached; ++i)
+                if (i == k) { r0[i] = o0; r1[i] = o1; }
+        } else {
+            float4* o = reinterpret_cast<float4*>(s.hyp_dp + (size_t)h * 8);
+            o[0] = o0;
+            o[1] = o1;
+        }
     }
     const float ivt = (float)(1.0 / p.sigma_t), ivr = (float)(1.0 / p.sigma_r);
     const float mlog2e = -0.5f * 1.4426950408889634f;
@@ -575,17 +590,23 @@ k_meanshift(DevParams p, DevState s, int t)
         float dx[6];
         for (int c = 0; c < 6; ++c) dx[c] = (float)(xs[c] - seedp[c]);
         float acc[7] = {0, 0, 0, 0, 0, 0, 0};
-        for (int h = rank * blockDim.x + tid; h < n; h += stride) {
-            const float4* o = reinterpret_cast<const float4*>(s.hyp_dp + (size_t)h * 8);
-            const float4 q0 = o[0], q1 = o[1];
+        // hypotheses in increasing h (the registers' first, then global memory)
+        auto add = [&](const float4 q0, const float4 q1) {
             const float d0 = dx[0] - q0.x, d1 = dx[1] - q0.y, d2 = dx[2] - q0.z;
             const float d3 = dx[3] - q0.w, d4 = dx[4] - q1.x, d5 = dx[5] - q1.y;
             const float m = fmaf(d0 * d0 + d1 * d1 + d2 * d2, ivt, (d3 * d3 + d4 * d4 + d5 * d5) * ivr);
             const float kw = q1.z * exp2f(mlog2e * m);
-            if (!(kw > 0.f)) continue;     // zero weight (or a non-finite hypothesis) adds nothing
+            if (!(kw > 0.f)) return;       // zero weight (or a non-finite hypothesis) adds nothing
             acc[0] += kw;
             acc[1] = fmaf(kw, q0.x, acc[1]); acc[2] = fmaf(kw, q0.y, acc[2]); acc[3] = fmaf(kw, q0.z, acc[3]);
             acc[4] = fmaf(kw, q0.w, acc[4]); acc[5] = fmaf(kw, q1.x, acc[5]); acc[6] = fmaf(kw, q1.y, acc[6]);
+        };
+#pragma unroll
+        for (int k = 0; k < kMsCached; ++k)
+            if (h0 + k * stride < n) add(r0[k], r1[k]);
+        for (int h = h0 + kMsCached * stride; h < n; h += stride) {
+            const float4* o = reinterpret_cast<const float4*>(s.hyp_dp + (size_t)h * 8);
+            add(o[0], o[1]);
         }
         // warp sums in FP32 (each lane holds at most 4 terms; a warp-wide FP64 add
         // costs this GPU's FP64 pipe ~16 cycles), the rest of the reduction in FP64
