@@ -416,7 +416,10 @@ def run_ours(args):
     peak = sms * per_clk * NOMINAL_MAX_MHZ * 1e6 / 1e12                # T SFU-ops/s
     score_ms = np.array(score_ms)
     score_pairs = np.array(score_pairs, dtype=np.float64)
-    achieved = float(np.mean(ops_per_pair * score_pairs / (score_ms * 1e-3)) / 1e12) if len(score_ms) else None
+    # algorithmic work per launch over the mean launch duration (= all timed
+    # launches' work over their summed time)
+    achieved = (float(ops_per_pair * score_pairs.sum() / (score_ms.sum() * 1e-3)) / 1e12
+                if len(score_ms) else None)
     mix_txt = " + ".join(f"{n} {op}" for op, n in mix.items() if n)
     roofline = {"kernel": "k_score (dense hypothesis scoring)", "bound": "alu", "achieved": achieved,
                 "peak": peak, "unit": f"T SFU-op/s ({ops_per_pair} algorithmic SFU ops per hypothesis-pixel pair)",

@@ -25,6 +25,7 @@
 // FP64.
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "voldor_internal.cuh"
@@ -217,9 +218,6 @@ struct PixX2 {
 static_assert(sizeof(PixX2) == 80, "PixX2 is five 16-byte words");
 
 
-// log2(1 + r) (MIE) or log2(r) (MLE) for two hypotheses against one pixel;
-// the packed form of pair_term2<false, MLE>, with the residual's sign flipped
-// (it is squared).
 // log2(1 + r) (MIE) or log2(r) (MLE), r = mu / rho, of two hypotheses against
 // one pixel, with the checks of pair_term2<true>; the residual's sign is
 // flipped (it is squared). kGauss: the Gaussian residual model, r = 2^s with
@@ -288,15 +286,24 @@ __device__ __forceinline__ void score_tile(const HypX2* hy, const PixX2* xt, int
     }
 }
 
-// SLOTS hypothesis pairs per thread (the hypothesis side of the tile is
-// 2 * SLOTS * 256 per block: pair k holds hypotheses tile0 + 2k * 256 + tid and
-// tile0 + (2k + 1) * 256 + tid); MINB resident blocks per SM. Pairs wholly past
-// the frame's hypothesis count are skipped (block-uniform), so a partial tile
-// costs at most 511 idle hypotheses. The autotuner picks among the instances.
+// SLOTS hypothesis pairs per thread; MINB resident blocks per SM. A block
+// scores a tile of 2 * SLOTS * 256 hypotheses against one chunk of the pixel
+// records. The tile is cut into groups of 64 consecutive hypotheses, and warp
+// slot k of a warp holds one group, lane l taking hypotheses 2l and 2l + 1 of
+// it. A full tile needs every warp slot (16 groups for SLOTS = 2): warp w holds
+// groups w * SLOTS .. w * SLOTS + SLOTS - 1 and scores every pixel of the
+// chunk. The last, partial tile of a frame needs only u = ceil(m / 64) groups
+// for its m hypotheses, i.e. wpg = ceil(u / SLOTS) warps; the block's warps
+// then form P = 8 / wpg teams of wpg warps, team j scoring the same groups on
+// the j-th of P equal parts of every pixel tile, and the teams' sums are added
+// in team order at the end. So a partial tile costs about m / 1024 of a full
+// one instead of a whole 512-hypothesis slot per started slot. The autotuner
+// picks among the instances.
 template <int SLOTS, int MINB, bool MLE, bool GAUSS>
 __global__ void __launch_bounds__(kScoreThreads, MINB) k_score(DevParams p, DevState s, int log_idx)
 {
     constexpr int HPT = 2 * SLOTS;
+    constexpr int kWarps = kScoreThreads / 32;
     const int n_hyp = *s.n_hyp;
     const int n_pix = *s.pix_count;
     if (log_idx >= 0 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
@@ -312,6 +319,15 @@ __global__ void __launch_bounds__(kScoreThreads, MINB) k_score(DevParams p, DevS
     const long long lo = (long long)n_pix * chunk / n_chunks;
     const long long hi = (long long)n_pix * (chunk + 1) / n_chunks;
     const int n_tiles = (int)((hi - lo + kTilePix - 1) / kTilePix);
+
+    // work split (block-uniform; warp-uniform per warp)
+    const int m = min(n_hyp - tile0, kScoreThreads * HPT);
+    const int u = (m + 63) / 64;                       // hypothesis groups of this tile
+    const int wpg = (u + SLOTS - 1) / SLOTS;           // warps per team
+    const int P = kWarps / wpg;                        // teams
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int team = warp / wpg, wg = warp - team * wpg;
+    const int nsw = team < P ? max(0, min(SLOTS, u - wg * SLOTS)) : 0;   // this warp's groups
 
     __shared__ __align__(128) float4 tile[kStages][kTilePix * 3];
     __shared__ __align__(16) PixX2 xt[kTilePix];
@@ -335,16 +351,18 @@ __global__ void __launch_bounds__(kScoreThreads, MINB) k_score(DevParams p, DevS
     if (threadIdx.x == 0)
         for (int i = 0; i < kStages && i < n_tiles; ++i) issue(i);
 
+    // hypothesis of slot k, lane half v: tile0 + (wg * SLOTS + k) * 64 + 2 * lane + v
+    const int hbase = tile0 + wg * SLOTS * 64 + 2 * lane;
     HypX2 hy[SLOTS];
     {
 #pragma unroll
         for (int k = 0; k < SLOTS; ++k) {
             HypF a[2];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int h = tile0 + (2 * k + u) * kScoreThreads + threadIdx.x;
+            for (int v = 0; v < 2; ++v) {
+                const int h = hbase + k * 64 + v;
                 const float* f = s.hyp_f32 + (size_t)min(h, n_hyp - 1) * 12;
-                a[u] = HypF{f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7], f[8], f[9], f[10], f[11]};
+                a[v] = HypF{f[0], f[1], f[2], f[3], f[4], f[5], f[6], f[7], f[8], f[9], f[10], f[11]};
             }
             hy[k] = HypX2{f2_pack(-a[0].e0, -a[1].e0), f2_pack(-a[0].e1, -a[1].e1), f2_pack(-a[0].e2, -a[1].e2),
                           f2_pack(-a[0].t0, -a[1].t0), f2_pack(-a[0].e3, -a[1].e3), f2_pack(-a[0].e4, -a[1].e4),
@@ -356,46 +374,54 @@ __global__ void __launch_bounds__(kScoreThreads, MINB) k_score(DevParams p, DevS
 #pragma unroll
     for (int i = 0; i < HPT; ++i) acc[i] = 0.0;
     const float xs_min = p.xs_min, xs_max = p.xs_max;
-    const int ns = min(SLOTS, (n_hyp - tile0 + 2 * kScoreThreads - 1) / (2 * kScoreThreads));
 
+    // the tile loop; TEAMS = false is the full-tile case (one team, every
+    // pixel), kept as its own copy so that it carries no team state
     int it = 0;
-    for (; it < n_tiles; ++it) {
-        const int slot = it % kStages;
-        if (!mbar_wait_bounded(&full[slot], (uint32_t)((it / kStages) & 1))) atomicExch(&timed_out, 1);
-        const int cnt = (int)min((long long)kTilePix, hi - (lo + (long long)it * kTilePix));
-        if ((int)threadIdx.x < cnt) {
-            // expand record threadIdx.x into both lanes (a timed-out tile's
-            // contents are never used)
-            const float4* r = &tile[slot][3 * threadIdx.x];
-            const float4 a = r[0], b = r[1];
-            const float wq = r[2].x;
-            float4* x = reinterpret_cast<float4*>(&xt[threadIdx.x]);
-            x[0] = make_float4(a.x, a.x, a.y, a.y);
-            x[1] = make_float4(a.z, a.z, a.w, a.w);
-            x[2] = make_float4(b.x, b.x, b.y, b.y);
-            x[3] = make_float4(b.z, b.z, b.w, b.w);
-            x[4] = make_float4(wq, wq, 0.f, 0.f);
-        }
-        __syncthreads();                       // tile expanded; the raw slot is free
-        if (timed_out) break;
-        if (threadIdx.x == 0 && it + kStages < n_tiles) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(it + kStages);
-        }
-        f2 facc[SLOTS];
+    auto run = [&](auto teams) {
+        constexpr bool TEAMS = decltype(teams)::value;
+        for (; it < n_tiles; ++it) {
+            const int slot = it % kStages;
+            if (!mbar_wait_bounded(&full[slot], (uint32_t)((it / kStages) & 1))) atomicExch(&timed_out, 1);
+            const int cnt = (int)min((long long)kTilePix, hi - (lo + (long long)it * kTilePix));
+            if ((int)threadIdx.x < cnt) {
+                // expand record threadIdx.x into both lanes (a timed-out tile's
+                // contents are never used)
+                const float4* r = &tile[slot][3 * threadIdx.x];
+                const float4 a = r[0], b = r[1];
+                const float wq = r[2].x;
+                float4* x = reinterpret_cast<float4*>(&xt[threadIdx.x]);
+                x[0] = make_float4(a.x, a.x, a.y, a.y);
+                x[1] = make_float4(a.z, a.z, a.w, a.w);
+                x[2] = make_float4(b.x, b.x, b.y, b.y);
+                x[3] = make_float4(b.z, b.z, b.w, b.w);
+                x[4] = make_float4(wq, wq, 0.f, 0.f);
+            }
+            __syncthreads();                       // tile expanded; the raw slot is free
+            if (timed_out) break;
+            if (threadIdx.x == 0 && it + kStages < n_tiles) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(it + kStages);
+            }
+            // this team's part of the tile
+            const int q0 = TEAMS ? cnt * team / P : 0, q1 = TEAMS ? cnt * (team + 1) / P : cnt;
+            f2 facc[SLOTS];
 #pragma unroll
-        for (int k = 0; k < SLOTS; ++k) facc[k] = 0ull;
-        if (ns >= SLOTS) score_tile<SLOTS, MLE, GAUSS>(hy, xt, cnt, xs_min, xs_max, facc);
-        else if (SLOTS > 3 && ns == 3) score_tile<(SLOTS > 3 ? 3 : 1), MLE, GAUSS>(hy, xt, cnt, xs_min, xs_max, facc);
-        else if (SLOTS > 2 && ns == 2) score_tile<(SLOTS > 2 ? 2 : 1), MLE, GAUSS>(hy, xt, cnt, xs_min, xs_max, facc);
-        else score_tile<1, MLE, GAUSS>(hy, xt, cnt, xs_min, xs_max, facc);
+            for (int k = 0; k < SLOTS; ++k) facc[k] = 0ull;
+            if (nsw >= SLOTS) score_tile<SLOTS, MLE, GAUSS>(hy, xt + q0, q1 - q0, xs_min, xs_max, facc);
+            else if (SLOTS > 3 && nsw == 3) score_tile<(SLOTS > 3 ? 3 : 1), MLE, GAUSS>(hy, xt + q0, q1 - q0, xs_min, xs_max, facc);
+            else if (SLOTS > 2 && nsw == 2) score_tile<(SLOTS > 2 ? 2 : 1), MLE, GAUSS>(hy, xt + q0, q1 - q0, xs_min, xs_max, facc);
+            else if (nsw == 1) score_tile<1, MLE, GAUSS>(hy, xt + q0, q1 - q0, xs_min, xs_max, facc);
 #pragma unroll
-        for (int k = 0; k < SLOTS; ++k) {
-            acc[2 * k] += (double)f2_lo(facc[k]);
-            acc[2 * k + 1] += (double)f2_hi(facc[k]);
+            for (int k = 0; k < SLOTS; ++k) {
+                acc[2 * k] += (double)f2_lo(facc[k]);
+                acc[2 * k + 1] += (double)f2_hi(facc[k]);
+            }
+            __syncthreads();                       // every thread is done with the expanded tile
         }
-        __syncthreads();                       // every thread is done with the expanded tile
-    }
+    };
+    if (P == 1) run(std::false_type{});
+    else run(std::true_type{});
     if (timed_out) {
         // drain the copies this block issued (bounded) before leaving
         if (threadIdx.x == 0) {
@@ -406,10 +432,31 @@ __global__ void __launch_bounds__(kScoreThreads, MINB) k_score(DevParams p, DevS
         return;
     }
     const int S = p.S;
+    if (P == 1) {
+        if (team == 0) {                               // warps past the one team scored nothing
 #pragma unroll
-    for (int i = 0; i < HPT; ++i) {
-        const int h = tile0 + i * kScoreThreads + threadIdx.x;
-        if (h < n_hyp) s.partial[(size_t)chunk * S + h] = -acc[i] * 0.69314718055994531;
+            for (int i = 0; i < HPT; ++i) {
+                const int h = hbase + (i >> 1) * 64 + (i & 1);
+                if (h < n_hyp) s.partial[(size_t)chunk * S + h] = -acc[i] * 0.69314718055994531;
+            }
+        }
+        return;
+    }
+    // teams: sums per (team, hypothesis of the tile) in the expanded-tile
+    // buffer (free after the loop's last barrier; P * wpg * SLOTS * 64 <=
+    // 8 * SLOTS * 64 doubles fit in it), then added in team order
+    double* red = reinterpret_cast<double*>(xt);
+    const int span = wpg * SLOTS * 64;                 // hypotheses a team covers (>= m)
+    static_assert(kWarps * SLOTS * 64 * sizeof(double) <= sizeof(PixX2) * kTilePix, "team sums fit");
+    if (team < P) {
+#pragma unroll
+        for (int i = 0; i < HPT; ++i) red[team * span + (hbase - tile0) + (i >> 1) * 64 + (i & 1)] = acc[i];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += kScoreThreads) {
+        double t = 0.0;
+        for (int j = 0; j < P; ++j) t += red[j * span + i];
+        s.partial[(size_t)chunk * S + tile0 + i] = -t * 0.69314718055994531;
     }
 }
 

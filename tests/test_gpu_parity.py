@@ -50,15 +50,18 @@ def test_bootstrap(vd, oracle_lib, scene):
     assert rel.max() < 1e-6          # FP64 triangulation, FP32 storage
 
 
-@pytest.mark.parametrize("t", [1, 2, 3])
-def test_dense_scores(vd, oracle_lib, scene, t):
+# hypothesis counts: 64 and 200 leave one partial tile that the block's warps
+# split into 8 and 2 teams over the pixels; 1100 is a full 1024-hypothesis tile
+# plus a ragged 76-hypothesis one
+@pytest.mark.parametrize("t,n", [(1, 64), (2, 64), (3, 64), (1, 200), (2, 1100), (3, 1100)])
+def test_dense_scores(vd, oracle_lib, scene, t, n):
     w = scene
     rng = np.random.default_rng(10 + t)
     depth, rig = f32_state(rng, w)
-    g = _gpu_window(vd, w)
+    g = _gpu_window(vd, w, S=max(256, n))
     g.set_state(poses=w.poses, depth=depth, rigidness=rig, iteration=0)
     ow = oracle_window(oracle_lib, w, w.flows.astype(np.float32).astype(np.float64), 256, depth, rig, w.poses)
-    R, tv = f32_hypotheses(rng, w.poses[t - 1][:3, :3], w.poses[t - 1][:3, 3], 64)
+    R, tv = f32_hypotheses(rng, w.poses[t - 1][:3, :3], w.poses[t - 1][:3, 3], n)
     L_gpu = g.score_hypotheses(t, R, tv)
     L_ref = ow.score(t, R, tv)
     rel = np.abs(L_gpu - L_ref) / np.abs(L_ref)
