@@ -42,6 +42,13 @@ MUFU_PER_SM_PER_CLK = 16          # 4 SFU lanes per SM sub-partition, 4 sub-part
 ALGO_MUFU_MIX = {("mie", "fisk"): (1, 2, 1), ("mle", "fisk"): (1, 2, 1),
                  ("mie", "gaussian"): (1, 1, 1), ("mle", "gaussian"): (1, 0, 0)}
 NOMINAL_SMS, NOMINAL_MAX_MHZ = 152, 2070.0
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per k_score launch,
+# mean over the 40 launches of one driving-window step (S = 8192, 5 iterations),
+# from one ncu capture of the current default MIE / Fisk kernel (cold L2 at each
+# launch: 13.58 MB read, < 1 KB written; the first frame's launch reads 22.82 MB
+# against 22.75 MB of records and hypotheses). The other variants and hypothesis
+# counts were not captured: their traffic is reported as null.
+SCORE_TRAFFIC_BYTES = {("mie", "fisk", 8192): 13.58e6}
 
 
 def parse_args():
@@ -423,7 +430,9 @@ def run_ours(args):
     mix_txt = " + ".join(f"{n} {op}" for op, n in mix.items() if n)
     roofline = {"kernel": "k_score (dense hypothesis scoring)", "bound": "alu", "achieved": achieved,
                 "peak": peak, "unit": f"T SFU-op/s ({ops_per_pair} algorithmic SFU ops per hypothesis-pixel pair)",
-                "frac": achieved / peak if achieved else None, "traffic": None,
+                "frac": achieved / peak if achieved else None,
+                "traffic": SCORE_TRAFFIC_BYTES.get((args.criterion, args.residual, args.hyps)),
+                "traffic_unit": "DRAM bytes per launch (ncu)",
                 "peak_source": (f"{sms} SMs x {per_clk:.2f} SFU results/clk/SM (measured: ex2 {rates['ex2']:.2f}, "
                                 f"lg2 {rates['lg2']:.2f}, rcp {rates['rcp']:.2f}; mix {mix_txt}) x "
                                 f"{NOMINAL_MAX_MHZ:.0f} MHz; nominal table value 16/clk/SM"),

@@ -1,12 +1,13 @@
 """Parity at the benchmark's full size and launch configuration: the
 1242x375, T = 8 driving window with FP16 flows, S = 8192 hypotheses per frame
-(the dense scoring's default 8-hypotheses-per-thread shape and pixel-chunk
-count, as bench.py times it), teacher-forced as the small-window tests are.
+(the dense scoring's default shape -- 4 hypotheses per thread, two blocks per
+SM -- and pixel-chunk count, as bench.py times it), teacher-forced as the small-window tests are.
 
 - dense scores: sampled hypotheses recomputed by the oracle over all 465,750
-  pixels, 1e-5 relative; one launch with a full last tile (8192 hypotheses)
-  and one whose last tile is partial (6844: two of its four hypothesis pairs
-  skipped, one half-filled);
+  pixels, 1e-5 relative; one launch with a full last tile (8192 hypotheses:
+  eight 1024-hypothesis tiles) and two whose last tile is partial (6844: 700
+  hypotheses on six of the block's eight warps; 6400: 256 hypotheses scored by
+  four teams of two warps, each on a quarter of every pixel tile);
 - per-pixel log-likelihoods (unsmoothed rigidness) at every (t, j): 1e-5
   relative;
 - smoothed rigidness (forward-backward) at every (t, j): 2e-5 absolute;
@@ -46,7 +47,7 @@ def _pair(vd, oracle_lib, drive, rng):
     return g, ow, depth, rig
 
 
-@pytest.mark.parametrize("t,n", [(1, 8192), (5, 6844)])
+@pytest.mark.parametrize("t,n", [(1, 8192), (5, 6844), (7, 6400)])
 def test_dense_scores_full_size(vd, oracle_lib, drive, t, n):
     w = drive[0]
     rng = np.random.default_rng(300 + t)
@@ -54,7 +55,7 @@ def test_dense_scores_full_size(vd, oracle_lib, drive, t, n):
     g.set_state(poses=w.poses, depth=depth, rigidness=rig, iteration=0)
     R, tv = f32_hypotheses(rng, w.poses[t - 1][:3, :3], w.poses[t - 1][:3, 3], n)
     L_gpu = g.score_hypotheses(t, R, tv)
-    idx = np.array(sorted({0, 1, 255, 256, 2047, 2048, 4095, 6143, 6144, 6655, 6656, 6843, n - 1} & set(range(n))))
+    idx = np.array(sorted({0, 1, 255, 256, 2047, 2048, 4095, 6143, 6144, 6145, 6271, 6338, 6655, 6656, 6843, n - 1} & set(range(n))))
     L_ref = ow.score(t, R[idx], tv[idx])
     rel = np.abs(L_gpu[idx] - L_ref) / np.abs(L_ref)
     assert rel.max() < 1e-5, (rel.max(), idx[np.argmax(rel)])

@@ -50,10 +50,10 @@ def test_bootstrap(vd, oracle_lib, scene):
     assert rel.max() < 1e-6          # FP64 triangulation, FP32 storage
 
 
-# hypothesis counts: 64 and 200 leave one partial tile that the block's warps
-# split into 8 and 2 teams over the pixels; 1100 is a full 1024-hypothesis tile
-# plus a ragged 76-hypothesis one
-@pytest.mark.parametrize("t,n", [(1, 64), (2, 64), (3, 64), (1, 200), (2, 1100), (3, 1100)])
+# hypothesis counts: 1, 64 and 200 leave one partial tile that the block's
+# warps split into 8, 8 and 2 teams over the pixels; 1100 is a full
+# 1024-hypothesis tile plus a ragged 76-hypothesis one
+@pytest.mark.parametrize("t,n", [(1, 1), (1, 64), (2, 64), (3, 64), (1, 200), (2, 1100), (3, 1100)])
 def test_dense_scores(vd, oracle_lib, scene, t, n):
     w = scene
     rng = np.random.default_rng(10 + t)
