@@ -178,7 +178,7 @@ voldor_status voldor_set_state(voldor_ctx* ctx, const double* poses, const float
  * argmax L_h. Results stay readable through voldor_get_buffer. */
 voldor_status voldor_pose_update(voldor_ctx* ctx, int k, int t);
 
-/* Dense scoring alone (the spec kernel): scores n caller-given
+/* Dense scoring alone (the step that dominates the EM): scores n caller-given
  * hypotheses of frame t against every valid pixel under the current state.
  *  R: n*9 doubles row-major, tv: n*3 doubles (host); L: n doubles (host).
  *  L_h = sum_j [pi_{t-1}(theta_j) valid] W_t^j log(rho/(rho+mu)), the Eq. 10

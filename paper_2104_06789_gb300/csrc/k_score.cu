@@ -223,10 +223,19 @@ static_assert(sizeof(PixX2) == 80, "PixX2 is five 16-byte words");
 // flipped (it is squared). kGauss: the Gaussian residual model, r = 2^s with
 // s = xs fx^2 / alpha - x_mu / alpha (record fields beta, beta_k), and
 // log2(1 + 2^s) = max(s, 0) + log2(1 + 2^-|s|).
-template <bool kMLE, bool kGauss>
-__device__ __forceinline__ f2 pair_x2(const HypX2& h, const PixX2& q, float xs_min, float xs_max)
+//
+// The term is computed in two halves so that the tile loop can overlap the
+// second half of one pixel with the first half of the next: the front
+// (projection, reciprocal, squared residual and, under the Fisk model, its
+// log2) leaves u = Cp xs, s and -(1 + a_z); the back (the exponentials, the
+// log1p and the selects) finishes the term.
+struct PairMid {
+    f2 u, s, nden;
+};
+
+template <bool kGauss>
+__device__ __forceinline__ PairMid pair_front(const HypX2& h, const PixX2& q, float xs_min, float xs_max)
 {
-    const f2 ONE = f2_pack(1.f, 1.f), TWO = f2_pack(2.f, 2.f);
     const f2 nax = f2_fma(h.x0, q.xb, f2_fma(h.x1, q.yb2, f2_fma(h.xt, q.w, h.x2)));   // -a_x
     const f2 nay = f2_fma(h.y0, q.xb, f2_fma(h.y1, q.yb2, f2_fma(h.yt, q.w, h.y2)));   // -a_y
     const f2 az = f2_fma(h.z0, q.xb, f2_fma(h.z1, q.yb2, f2_fma(h.zt, q.w, h.z2)));
@@ -238,10 +247,18 @@ __device__ __forceinline__ f2 pair_x2(const HypX2& h, const PixX2& q, float xs_m
     const f2 rv = f2_fma(mv, rd, q.vt);
     f2 xs = f2_fma(ru, ru, f2_mul(rv, rv));
     xs = f2_pack(fminf(fmaxf(f2_lo(xs), xs_min), xs_max), fminf(fmaxf(f2_hi(xs), xs_min), xs_max));
+    if (kGauss) return PairMid{xs, f2_fma(q.beta, xs, q.beta_k), nden};       // s = log2(mu / rho)
+    return PairMid{f2_mul(q.Cp, xs), f2_fma(q.beta, f2_lg2(xs), q.beta_k), nden};
+}
+
+template <bool kMLE, bool kGauss>
+__device__ __forceinline__ f2 pair_back(const PairMid& m)
+{
+    const f2 ONE = f2_pack(1.f, 1.f), TWO = f2_pack(2.f, 2.f);
+    const f2 nden = m.nden;
     const float behind = kMLE ? 0.f : 1.f;       // 1 + a_z <= 0: rho := mu
     if (kGauss) {
-        const f2 sq = f2_fma(q.beta, xs, q.beta_k);                      // log2(mu / rho)
-        const float g0 = f2_lo(sq), g1 = f2_hi(sq);
+        const float g0 = f2_lo(m.s), g1 = f2_hi(m.s);
         if (kMLE) return f2_pack(slct(behind, g0, f2_lo(nden)), slct(behind, g1, f2_hi(nden)));
         const f2 e = f2_pack(mufu_ex2(-fabsf(g0)), mufu_ex2(-fabsf(g1)));
         f2 ps = f2_fma(e, f2_pack(1.784831882e-01f, 1.784831882e-01f), f2_pack(-3.390570283e-01f, -3.390570283e-01f));
@@ -255,10 +272,9 @@ __device__ __forceinline__ f2 pair_x2(const HypX2& h, const PixX2& q, float xs_m
         const float v1 = fmaxf(g1, 0.f) + slct(f2_hi(big), f2_hi(small), f2_hi(d));
         return f2_pack(slct(behind, v0, f2_lo(nden)), slct(behind, v1, f2_hi(nden)));
     }
-    const f2 sg = f2_fma(q.beta, f2_lg2(xs), q.beta_k);
-    const float s0 = f2_lo(sg), s1 = f2_hi(sg);
+    const float s0 = f2_lo(m.s), s1 = f2_hi(m.s);
     const f2 ep = f2_pack(mufu_ex2(s0), mufu_ex2(s1)), en = f2_pack(mufu_ex2(-s0), mufu_ex2(-s1));
-    const f2 r = f2_mul(f2_mul(q.Cp, xs), f2_add(ep, f2_add(en, TWO)));
+    const f2 r = f2_mul(m.u, f2_add(ep, f2_add(en, TWO)));
     if (kMLE) {
         const f2 v = f2_lg2(r);
         return f2_pack(slct(behind, f2_lo(v), f2_lo(nden)), slct(behind, f2_hi(v), f2_hi(nden)));
@@ -274,16 +290,33 @@ __device__ __forceinline__ f2 pair_x2(const HypX2& h, const PixX2& q, float xs_m
     return f2_pack(slct(behind, v0, f2_lo(nden)), slct(behind, v1, f2_hi(nden)));
 }
 
-// One shared-memory tile against the first NS hypothesis pairs of the thread.
+// One shared-memory tile against the first NS hypothesis pairs of the thread,
+// software-pipelined over the pixels: the front half of pixel q is issued
+// beside the back half of pixel q - 1 (independent chains), and each pixel's
+// term is added to the accumulator in pixel order as before.
 template <int NS, bool MLE, bool GAUSS>
 __device__ __forceinline__ void score_tile(const HypX2* hy, const PixX2* xt, int cnt, float xs_min, float xs_max,
                                            f2* facc)
 {
-    for (int q = 0; q < cnt; ++q) {
-        const PixX2 px = xt[q];
+    if (cnt <= 0) return;
+    PairMid m[NS];
+    f2 wq = xt[0].wq;
 #pragma unroll
-        for (int k = 0; k < NS; ++k) facc[k] = f2_fma(px.wq, pair_x2<MLE, GAUSS>(hy[k], px, xs_min, xs_max), facc[k]);
+    for (int k = 0; k < NS; ++k) m[k] = pair_front<GAUSS>(hy[k], xt[0], xs_min, xs_max);
+    for (int q = 1; q < cnt; ++q) {
+        const PixX2 px = xt[q];
+        PairMid n[NS];
+#pragma unroll
+        for (int k = 0; k < NS; ++k) n[k] = pair_front<GAUSS>(hy[k], px, xs_min, xs_max);
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            facc[k] = f2_fma(wq, pair_back<MLE, GAUSS>(m[k]), facc[k]);
+            m[k] = n[k];
+        }
+        wq = px.wq;
     }
+#pragma unroll
+    for (int k = 0; k < NS; ++k) facc[k] = f2_fma(wq, pair_back<MLE, GAUSS>(m[k]), facc[k]);
 }
 
 // SLOTS hypothesis pairs per thread; MINB resident blocks per SM. A block

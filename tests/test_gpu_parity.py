@@ -2,7 +2,7 @@
 sides get the same FP32-representable state and run one sub-step).
 
 Tolerances (derived in the design notes from the FP32 arithmetic):
-  - dense scores L_h: 1e-5 relative (the north-star tolerance);
+  - dense scores L_h: 1e-5 relative;
   - per-pixel log-likelihood terms and rigidness maps: absolute 2e-5 on
     quantities in [0, 1], relative 1e-5 on sums;
   - P3P hypotheses: identical group indices and slots, poses to 1e-9;
