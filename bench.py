@@ -45,10 +45,10 @@ NOMINAL_SMS, NOMINAL_MAX_MHZ = 152, 2070.0
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per k_score launch,
 # mean over the 40 launches of one driving-window step (S = 8192, 5 iterations),
 # from one ncu capture of the current default MIE / Fisk kernel (cold L2 at each
-# launch: 13.58 MB read, < 1 KB written; the first frame's launch reads 22.82 MB
+# launch: 13.59 MB read, < 1 KB written; the first frame's launch reads 22.82 MB
 # against 22.75 MB of records and hypotheses). The other variants and hypothesis
 # counts were not captured: their traffic is reported as null.
-SCORE_TRAFFIC_BYTES = {("mie", "fisk", 8192): 13.58e6}
+SCORE_TRAFFIC_BYTES = {("mie", "fisk", 8192): 13.59e6}
 
 
 def parse_args():
