@@ -335,8 +335,16 @@ __global__ void k_hyp_scan(DevParams p, DevState s)
     const int tid = threadIdx.x, nt = blockDim.x;
     const int seg = (p.G + nt - 1) / nt;
     const int g0 = min(tid * seg, p.G), g1 = min(g0 + seg, p.G);
+    // segments of a multiple of 4 counts start 16-byte aligned (the arrays are
+    // 256-byte aligned): read and write them four at a time
+    const bool vec = (seg & 3) == 0;
+    const int gv = vec ? g0 + ((g1 - g0) & ~3) : g0;
     int local = 0;
-    for (int g = g0; g < g1; ++g) local += s.grp_count[g];
+    for (int g = g0; g < gv; g += 4) {
+        const int4 c = *reinterpret_cast<const int4*>(s.grp_count + g);
+        local += c.x + c.y + c.z + c.w;
+    }
+    for (int g = gv; g < g1; ++g) local += s.grp_count[g];
     // block exclusive scan of `local`
     const int lane = tid & 31, warp = tid >> 5;
     int incl = local;
@@ -357,7 +365,14 @@ __global__ void k_hyp_scan(DevParams p, DevState s)
     }
     __syncthreads();
     int off = incl - local + (warp > 0 ? wsum[warp - 1] : 0);
-    for (int g = g0; g < g1; ++g) {
+    for (int g = g0; g < gv; g += 4) {
+        const int4 c = *reinterpret_cast<const int4*>(s.grp_count + g);
+        int4 o;
+        o.x = off; o.y = o.x + c.x; o.z = o.y + c.y; o.w = o.z + c.z;
+        *reinterpret_cast<int4*>(s.grp_offset + g) = o;
+        off = o.w + c.w;
+    }
+    for (int g = gv; g < g1; ++g) {
         s.grp_offset[g] = off;
         off += s.grp_count[g];
     }
@@ -366,7 +381,9 @@ __global__ void k_hyp_scan(DevParams p, DevState s)
 
 // se(3) logarithm through the unit quaternion of R (Shepperd's selection):
 // phi = 2 atan2(|v|, w) v/|v|, rho = V^-1 t with
-// V^-1 = I - Phi/2 + (1 - (th/2) cot(th/2)) / th^2 Phi^2.
+// V^-1 = I - Phi/2 + (1 - (th/2) cot(th/2)) / th^2 Phi^2, where
+// cot(th/2) = w / |v| (w = cos(th/2), |v| = sin(th/2), w >= 0): no FP64
+// sine or cosine, which are long serial routines on this GPU's FP64 pipe.
 __device__ void se3_log_quat(const double* Rt, double* p6)
 {
     const double R00 = Rt[0], R01 = Rt[1], R02 = Rt[2];
@@ -398,7 +415,7 @@ __device__ void se3_log_quat(const double* Rt, double* p6)
     const double phi[3] = {scale * x, scale * y, scale * z};
     double c2;
     if (th < 1e-4) c2 = 1.0 / 12.0 + th * th / 720.0;
-    else c2 = (1.0 - 0.5 * th * cos(0.5 * th) / sin(0.5 * th)) / (th * th);
+    else c2 = (1.0 - 0.5 * th * w / vn) / (th * th);
     const double t[3] = {Rt[3], Rt[7], Rt[11]};
     double a[3], b[3];
     d3cross(phi, t, a);
