@@ -18,11 +18,12 @@
 // The FP32 add / mul / fma work runs on packed pairs: two hypotheses share a
 // 64-bit register pair and one .f32x2 instruction does both lanes, which
 // halves the issue slots of the FMA-pipe work (the pipe still does 128 lane
-// operations per SM clock, and it is what bounds this kernel). Each thread
-// carries 4 pairs (8 hypotheses, instruction-level parallelism over
-// occupancy); pixel records are bulk-copied into shared memory tile by tile
-// and expanded there into both lanes; sums are FP32 per 256-pixel tile, then
-// FP64.
+// operations per SM clock: after the SFU it is this kernel's second limit).
+// Each thread carries 2 pairs (4 hypotheses, two 256-thread blocks per SM:
+// the default shape) or 4 pairs (8 hypotheses, one block per SM); the pixel
+// loop is software-pipelined over two consecutive pixels; pixel records are
+// bulk-copied into shared memory tile by tile and expanded there into both
+// lanes; sums are FP32 per 256-pixel tile, then FP64.
 #include <cmath>
 #include <mutex>
 #include <type_traits>
