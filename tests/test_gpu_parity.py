@@ -68,6 +68,26 @@ def test_dense_scores(vd, oracle_lib, scene, t, n):
     assert rel.max() < 1e-5, rel.max()
 
 
+# tiny images (108 and 231 pixels): the pixel chunks hold one or a few
+# records, so pixel tiles of a single pixel (the pipelined pixel loop's first
+# and last stage only) and warp teams with an empty share of a tile occur
+@pytest.mark.parametrize("shape,n", [((12, 9), 1), ((12, 9), 300), ((33, 7), 64), ((33, 7), 1100)])
+def test_dense_scores_tiny_images(vd, oracle_lib, shape, n):
+    W, H = shape
+    w = small_window(seed=1100 + W, W=W, H=H, f=W * 0.75)
+    rng = np.random.default_rng(W + n)
+    depth, rig = f32_state(rng, w)
+    g = _gpu_window(vd, w, S=max(256, n))
+    g.set_state(poses=w.poses, depth=depth, rigidness=rig, iteration=0)
+    ow = oracle_window(oracle_lib, w, w.flows.astype(np.float32).astype(np.float64), 256, depth, rig, w.poses)
+    R, tv = f32_hypotheses(rng, w.poses[0][:3, :3], w.poses[0][:3, 3], n)
+    L_gpu = g.score_hypotheses(1, R, tv)
+    L_ref = ow.score(1, R, tv)
+    rel = np.abs(L_gpu - L_ref) / np.abs(L_ref)
+    assert rel.max() < 1e-5, rel.max()
+    g.destroy()
+
+
 @pytest.mark.parametrize("t", [1, 3])
 def test_pose_update(vd, oracle_lib, scene, t):
     w = scene
