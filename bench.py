@@ -107,7 +107,7 @@ def whole_job_rate(world, units_per_rank, max_seconds):
 
 def config_dict(w, args, world):
     return {"workload": w.name, "width": w.W, "height": w.H, "T": w.T, "em_iters": args.iters,
-            "hyps_per_frame": args.hyps, "groups_per_frame": 2 * args.hyps, "flows": "fp16",
+            "hyps_per_frame": args.hyps, "groups_per_frame": 4 * args.hyps, "flows": "fp16",
             "focal_px": w.K[0], "windows_per_rank": 1, "parallelism": f"replicas x{world}",
             "l2": "flushed between timed steps (256 MiB write)",
             "criterion": args.criterion, "residual": args.residual}
@@ -341,7 +341,7 @@ def run_ours(args):
     w = workload(rank)
     flows16 = np.ascontiguousarray(w.flows.astype(np.float16))
     stream = torch.cuda.Stream()
-    params = voldor.default_params(hyps_per_frame=args.hyps, groups_per_frame=2 * args.hyps,
+    params = voldor.default_params(hyps_per_frame=args.hyps,
                                    inv_depth_min=w.inv_depth_range[0], inv_depth_max=w.inv_depth_range[1],
                                    seed=0, window_id=rank,
                                    criterion={"mie": voldor.CRITERION_MIE, "mle": voldor.CRITERION_MLE}[args.criterion],
@@ -507,11 +507,11 @@ def run_batch(args):
         wins, shapes, hyps = [], {}, {}
         for i, (b, T) in enumerate(wl):
             flows = np.ascontiguousarray(b.flows[:T].astype(np.float16))
-            p = voldor.default_params(hyps_per_frame=S, groups_per_frame=2 * S, inv_depth_min=b.inv_depth_range[0],
+            p = voldor.default_params(hyps_per_frame=S, inv_depth_min=b.inv_depth_range[0],
                                       inv_depth_max=b.inv_depth_range[1], window_id=i)
             if tune_hyps:
                 s_win, _, _ = tuning.autotune_hyps(flows, b.K, p, b.poses[0], iters=args.iters)
-                p.hyps_per_frame, p.groups_per_frame = s_win, 2 * s_win
+                p.hyps_per_frame, p.groups_per_frame = s_win, 4 * s_win
             hyps[p.hyps_per_frame] = hyps.get(p.hyps_per_frame, 0) + 1
             g = voldor.Window(flows, b.K, p)
             g.bootstrap(b.poses[0])

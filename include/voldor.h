@@ -68,7 +68,11 @@ typedef struct {
     double beta_min;              /* floor of the Fisk shape B */
     double ms_tol;                /* meanshift stops when |dx| < ms_tol */
     int hyps_per_frame;           /* S: P3P pose hypotheses kept per frame (<= 65536) */
-    int groups_per_frame;         /* G: minimal groups drawn per frame (>= 1, <= 262144) */
+    int groups_per_frame;         /* G: budget of minimal groups per frame (>= 1, <= 262144). Groups
+                                     are drawn over the frame's pixels with a 3D-2D correspondence
+                                     and solved in order until S hypotheses exist or G groups are
+                                     spent; 4 S (the default's ratio) reaches S on every frame of
+                                     the driving and handheld workloads */
     int ms_max_iter;              /* meanshift iteration cap */
     int criterion;                /* VOLDOR_CRITERION_MIE (Eq. 10, default) or _MLE (Eq. 9) for the
                                      depth update and the dense pose scores; the E-step posterior

@@ -76,7 +76,8 @@ def lib():
             "or_bilinear": (i, [W, i, d, d, P(d)]),
             "or_bootstrap": (None, [W, P(d)]),
             "or_p3p": (i, [P(d), P(d), P(d), P(d), P(d)]),
-            "or_draw_group": (i, [W, i, i, C.c_int64, P(C.c_int64)]),
+            "or_valid_pixels": (C.c_int64, [W, i, P(C.c_int64)]),
+            "or_draw_group": (i, [W, i, i, C.c_int64, P(C.c_int64), C.c_int64, P(C.c_int64)]),
             "or_collect_hypotheses": (i, [W, i, i, P(d), P(d), P(d), P(C.c_int64), P(i)]),
             "or_score_hypotheses": (None, [W, i, i, P(d), P(d), P(d)]),
             "or_se3_exp": (None, [P(d), P(d), P(d)]),
@@ -134,7 +135,7 @@ class OracleWindow:
         self.poses = np.tile(np.eye(4), (self.T, 1, 1)).astype(np.float64)
         prm = dict(PAPER_DEFAULTS)
         prm.update(inv_depth_min=inv_depth_min, inv_depth_max=inv_depth_max,
-                   hyps_per_frame=S, groups_per_frame=2 * S if G is None else G,
+                   hyps_per_frame=S, groups_per_frame=4 * S if G is None else G,
                    seed=seed, window_id=window_id)
         prm.update(overrides)
         self.params = Params(**prm)
@@ -204,6 +205,19 @@ class OracleWindow:
         out = np.zeros(12)
         v = lib().or_frame_eval(self.ref, t, j, depth, _dp(out))
         return v, out
+
+    def valid_pixels(self, t):
+        """Pixels with a 3D-2D correspondence at frame t, in pixel order."""
+        out = np.zeros(self.H * self.W, dtype=np.int64)
+        n = lib().or_valid_pixels(self.ref, t, ptr(out, C.c_int64))
+        return out[:n]
+
+    def draw_group(self, k, t, g, valid):
+        """(distinct, the group's three pixels) drawn from the list `valid`."""
+        valid = np.ascontiguousarray(valid, dtype=np.int64)
+        j = np.zeros(3, dtype=np.int64)
+        ok = lib().or_draw_group(self.ref, k, t, g, ptr(valid, C.c_int64), valid.size, ptr(j, C.c_int64))
+        return bool(ok), j
 
     def collect_hypotheses(self, k, t):
         S = self.params.hyps_per_frame

@@ -623,19 +623,43 @@ int or_p3p(const double P[9], const double b[9], double Rs[36], double ts[12], d
 }
 
 // ---------------------------------------------------------------------------
-// Monte-Carlo minimal groups (Eqs. 15-17, 19). Reading: group g of frame t at
-// iteration k draws Philox(index g, t, k, POSE) and takes j_i = hi64(r_i * N)
-// for i = 0, 1, 2; a group with repeated or invalid pixels yields nothing.
-// Groups g = 0 .. G-1 are solved in order and their solutions (sorted by s1)
-// are kept until S hypotheses are collected. The weight of a hypothesis is the
-// product of the unsmoothed W_t of its three pixels (Eq. 19).
+// Monte-Carlo minimal groups (Sec. 5.2, Eqs. 15-17, 19). The paper forms a
+// group around a depth-map position that has a 3D-2D correspondence at frame t
+// and two further distinct positions; Fig. 6 ties every correspondence to a
+// minimal instance. Reading: the positions with a correspondence at frame t
+// (pi_{t-1} inside I_{t-1} and P_z > 0 in camera t-1) are listed in pixel
+// order, V_t = (v_0 < ... < v_{n-1}); group g of frame t at iteration k draws
+// Philox(index g, t, k, POSE) and takes j_i = V_t[hi64(r_i * n)] for
+// i = 0, 1, 2; a group with a repeated position yields nothing. Groups
+// g = 0, 1, ... are solved in order and their solutions (sorted by s1) are
+// appended until S hypotheses exist, drawing at most G groups (the budget).
+// The weight of a hypothesis is the product of the unsmoothed W_t of its
+// three pixels (Eq. 19).
 // ---------------------------------------------------------------------------
-int or_draw_group(const or_window* w, int k, int t, int64_t g, int64_t j_out[3])
+static bool has_correspondence(const or_window* w, const double Cprev[12], const double Tt[12], int t, int64_t j)
 {
+    return eval_frame(w, Cprev, Tt, t, (int)j, w->theta[j]).valid_prev;
+}
+
+// Writes V_t (pixel indices in increasing order) into out (room for H*W
+// entries) and returns n.
+int64_t or_valid_pixels(const or_window* w, int t, int64_t* out)
+{
+    double C[12], Tt[12];
+    frame_poses(w, t, C, Tt);
+    int64_t N = (int64_t)w->width * w->height, n = 0;
+    for (int64_t j = 0; j < N; ++j)
+        if (has_correspondence(w, C, Tt, t, j)) out[n++] = j;
+    return n;
+}
+
+int or_draw_group(const or_window* w, int k, int t, int64_t g, const int64_t* valid, int64_t n_valid,
+                  int64_t j_out[3])
+{
+    if (n_valid < 1) return 0;
     uint64_t r[4];
     draw(w, (uint64_t)g, (uint64_t)t, (uint64_t)k, STREAM_POSE, r);
-    uint64_t N = (uint64_t)w->width * w->height;
-    for (int i = 0; i < 3; ++i) j_out[i] = (int64_t)scale_index(r[i], N);
+    for (int i = 0; i < 3; ++i) j_out[i] = valid[scale_index(r[i], (uint64_t)n_valid)];
     return (j_out[0] != j_out[1] && j_out[0] != j_out[2] && j_out[1] != j_out[2]) ? 1 : 0;
 }
 
@@ -665,11 +689,13 @@ int or_collect_hypotheses(const or_window* w, int k, int t, double* R, double* t
 {
     double C[12], Tt[12];
     frame_poses(w, t, C, Tt);
+    std::vector<int64_t> valid((size_t)w->width * w->height);
+    const int64_t n_valid = or_valid_pixels(w, t, valid.data());
     int S = w->p.hyps_per_frame, G = w->p.groups_per_frame;
     int n = 0;
     for (int64_t g = 0; g < G && n < S; ++g) {
         int64_t j[3];
-        if (!or_draw_group(w, k, t, g, j)) continue;
+        if (!or_draw_group(w, k, t, g, valid.data(), n_valid, j)) continue;
         double P[9], b[9], wt;
         if (!group_instance(w, C, Tt, t, j, P, b, &wt)) continue;
         double Rs[36], ts[12], s1[4];

@@ -56,9 +56,14 @@ __global__ void k_prep_count(DevParams p, DevState s, int t)
         s.pix_geo[4 * N + j] = v;
         s.pix_geo[5 * N + j] = iz;
     }
+    // per-warp ballots of the valid pixels: with the block offsets they map
+    // the i-th valid pixel (pixel order) to its index for the minimal groups
+    const unsigned bal = __ballot_sync(0xffffffffu, valid);
+    if ((threadIdx.x & 31) == 0) s.pix_vmask[j >> 5] = bal;
     const int cnt = __syncthreads_count(valid);
     // the last block to finish turns the block counts into block offsets
-    // (exclusive scan, in place) and sets the record count; no block waits
+    // (exclusive scan, in place), sets the record count and clears the P3P
+    // claim counters of the frame; no block waits
     __shared__ bool last;
     if (threadIdx.x == 0) {
         s.pix_block_count[blockIdx.x] = cnt;
@@ -93,6 +98,8 @@ __global__ void k_prep_count(DevParams p, DevState s, int t)
     if (threadIdx.x == blockDim.x - 1) {
         *s.pix_count = off;
         *s.prep_done = 0u;
+        *s.p3p_claims = 0;
+        *s.p3p_done = 0ull;
     }
 }
 
@@ -147,11 +154,22 @@ __global__ void k_prep_write(DevParams p, DevState s, int t)
     }
 }
 
-void launch_pose_prep(const DevParams& p, const DevState& s, int t, cudaStream_t st)
+void launch_prep_count(const DevParams& p, const DevState& s, int t, cudaStream_t st)
 {
     const int nb = (p.N + kPixThreads - 1) / kPixThreads;
     k_prep_count<<<nb, kPixThreads, 0, st>>>(p, s, t);
+}
+
+void launch_prep_write(const DevParams& p, const DevState& s, int t, cudaStream_t st)
+{
+    const int nb = (p.N + kPixThreads - 1) / kPixThreads;
     k_prep_write<<<nb, kPixThreads, 0, st>>>(p, s, t);
+}
+
+void launch_pose_prep(const DevParams& p, const DevState& s, int t, cudaStream_t st)
+{
+    launch_prep_count(p, s, t, st);
+    launch_prep_write(p, s, t, st);
 }
 
 // Emissions rho/(rho+mu) of every (t, j) at the current depth (E-step input)

@@ -2,6 +2,8 @@
 // Philox4x64-10, FP64 P3P per group (Eq. 17), order-preserving hypothesis
 // collection with se(3) logarithms, and the weighted Gaussian meanshift of
 // Eqs. 18-19 on a thread-block cluster.
+#include <algorithm>
+
 #include <cooperative_groups.h>
 
 #include "voldor_internal.cuh"
@@ -247,32 +249,52 @@ __device__ int p3p_solve(const double P[3][3], const double b[3][3], P3PSol* out
 }
 
 // ---------------------------------------------------------------------------
-// Groups of frame t at iteration k: Philox(index g, t, k, POSE) gives
-// j_i = hi64(r_i * N); P3P on the 3D points in camera t-1 and the bearings of
-// the flow targets pi_{t-1} + X_t in camera t, all in FP64.
+// Minimal groups of frame t at iteration k (Sec. 5.2): the pixels with a 3D-2D
+// correspondence (pi_{t-1} valid), in pixel order, form the list V_t of n
+// entries; Philox(index g, t, k, POSE) gives j_i = V_t[hi64(r_i * n)] and a
+// group with a repeated pixel yields nothing. P3P (Eq. 17) takes the points in
+// camera t-1 and the bearings of the flow targets pi_{t-1} + X_t in camera t,
+// all in FP64.
 // ---------------------------------------------------------------------------
-__device__ bool group_point(const DevParams& p, const DevState& s, const double* C, int t, long long j, double* P,
-                            double* bear)
+
+// The i-th valid pixel of the frame (0 <= i < n): the block whose record
+// offset is the last one <= i (the count pass's exclusive scan), then the
+// (i - offset)-th set bit of that block's per-warp ballots.
+__device__ int valid_pixel_at(const DevState& s, int nb, int i)
 {
-    const int x = (int)(j % p.W), y = (int)(j / p.W);
-    const double th = (double)s.theta[j];
-    const double d[3] = {((double)x - p.cxd) / p.fxd, ((double)y - p.cyd) / p.fyd, 1.0};
-    double u, v;
-    if (t == 1) {
-        P[0] = th * d[0]; P[1] = th * d[1]; P[2] = th;
-        u = x; v = y;
-        if (!(P[2] > 0.0)) return false;
-    } else {
-        const double X = th * d[0], Y = th * d[1], Z = th;
-        for (int r = 0; r < 3; ++r) P[r] = C[r * 4 + 0] * X + C[r * 4 + 1] * Y + C[r * 4 + 2] * Z + C[r * 4 + 3];
-        if (!(P[2] > 0.0)) return false;
-        u = p.fxd * P[0] / P[2] + p.cxd;
-        v = p.fyd * P[1] / P[2] + p.cyd;
+    int lo = 0, hi = nb - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s.pix_block_count[mid] <= i) lo = mid;
+        else hi = mid - 1;
     }
-    if (!(u >= 0.0 && u <= (double)(p.W - 1) && v >= 0.0 && v <= (double)(p.H - 1))) return false;
+    int r = i - s.pix_block_count[lo];
+    const unsigned* m = s.pix_vmask + (size_t)lo * (kPixThreads / 32);
+    for (int w = 0; w < kPixThreads / 32; ++w) {
+        unsigned mw = m[w];
+        const int c = __popc(mw);
+        if (r < c) {
+            for (int q = 0; q < r; ++q) mw &= mw - 1u;
+            return lo * kPixThreads + w * 32 + (__ffs(mw) - 1);
+        }
+        r -= c;
+    }
+    return -1;
+}
+
+// Point in camera t-1 and bearing of the flow target of valid pixel j, from
+// the FP64 geometry the count pass stored (pix_geo) and an FP64 bilinear
+// sample of X_t at pi_{t-1}.
+__device__ bool group_point(const DevParams& p, const DevState& s, int t, int j, double* P, double* bear)
+{
+    const size_t N = (size_t)p.N;
+    P[0] = s.pix_geo[j];
+    P[1] = s.pix_geo[N + j];
+    P[2] = s.pix_geo[2 * N + j];
+    const double u = s.pix_geo[3 * N + j], v = s.pix_geo[4 * N + j];
     const int x0 = min((int)floor(u), p.W - 2), y0 = min((int)floor(v), p.H - 2);
     const double ax = u - x0, ay = v - y0;
-    const size_t base = (size_t)(t - 1) * p.N + (size_t)y0 * p.W + x0;
+    const size_t base = (size_t)(t - 1) * N + (size_t)y0 * p.W + x0;
     const float2 f00 = load_flow(s.flows, p.flow_f16, base), f10 = load_flow(s.flows, p.flow_f16, base + 1);
     const float2 f01 = load_flow(s.flows, p.flow_f16, base + p.W), f11 = load_flow(s.flows, p.flow_f16, base + p.W + 1);
     const double w00 = (1 - ax) * (1 - ay), w10 = ax * (1 - ay), w01 = (1 - ax) * ay, w11 = ax * ay;
@@ -284,44 +306,94 @@ __device__ bool group_point(const DevParams& p, const DevState& s, const double*
     return d3unit(bear);
 }
 
-__global__ void k_p3p_groups(DevParams p, DevState s, int t)
+// Solves group g; returns its solution count and weight.
+__device__ int solve_group(const DevParams& p, const DevState& s, int t, int k, int g, int n_valid, int nb,
+                           P3PSol* sols, double* weight_out)
 {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= p.G) return;
-    const int k = *s.iter;
+    *weight_out = 0.0;
     const U64x4 r = philox4x64_10((uint64_t)g, (uint64_t)t, (uint64_t)k, (uint64_t)kStreamPose, p.seed, p.window_id);
-    long long j[3];
-    for (int i = 0; i < 3; ++i) j[i] = (long long)__umul64hi(r.v[i], (uint64_t)p.N);
-    int n = 0;
-    double weight = 0.0;
-    P3PSol sols[kMaxSols];
-    if (j[0] != j[1] && j[0] != j[2] && j[1] != j[2]) {
-        const double* C = s.cum + 12 * (t - 1);
-        double P[3][3], b[3][3];
-        bool ok = true;
-        weight = 1.0;
-        for (int i = 0; i < 3 && ok; ++i) {
-            ok = group_point(p, s, C, t, j[i], P[i], b[i]);
-            weight *= (double)s.wmap[(size_t)(t - 1) * p.N + j[i]];
-        }
-        if (ok) n = p3p_solve(P, b, sols);
-        if (!ok) weight = 0.0;
+    int idx[3];
+    for (int i = 0; i < 3; ++i) idx[i] = (int)__umul64hi(r.v[i], (uint64_t)n_valid);
+    if (idx[0] == idx[1] || idx[0] == idx[2] || idx[1] == idx[2]) return 0;
+    double P[3][3], b[3][3];
+    double weight = 1.0;
+    for (int i = 0; i < 3; ++i) {
+        const int j = valid_pixel_at(s, nb, idx[i]);
+        if (j < 0 || !group_point(p, s, t, j, P[i], b[i])) return 0;
+        weight *= (double)s.wmap[(size_t)(t - 1) * p.N + j];
     }
-    s.grp_count[g] = n;
-    s.grp_weight[g] = weight;
-    double* o = s.grp_sols + (size_t)g * kMaxSols * 12;
-    for (int i = 0; i < n; ++i)
-        for (int q = 0; q < 12; ++q) o[i * 12 + q] = sols[i].Rt[q];
+    *weight_out = weight;
+    return p3p_solve(P, b, sols);
 }
 
-// All G groups in one launch: one thread per group, one warp per block so
-// that the FP64 solves spread over every SM. The solve is bound by FP64
-// latency with a few warps per SM, so solving the groups past the first S
-// solutions costs little time, and the collection keeps the first S
-// solutions in group order either way.
+// Groups are solved in order in chunks of 32 (one warp each) until the frame
+// has S solutions or the budget of G groups is spent. A warp claims chunks
+// with an atomic counter, so the claimed chunks are always 0, 1, ..., c - 1,
+// and every claimed chunk is solved: the solved groups form a prefix of the
+// group order. After its first chunk a warp claims another only while the
+// solutions found so far plus the chunks still in flight, at the yield
+// observed so far, fall short of S; the warp that completes the last chunk
+// in flight sees exact counts, so the run ends with at least S solutions in
+// the prefix (or the whole budget solved), and the first S solutions in
+// group order are the same whatever the timing.
+__global__ void __launch_bounds__(32) k_p3p_groups(DevParams p, DevState s, int t)
+{
+    const int lane = threadIdx.x;
+    const int n_valid = *s.pix_count;
+    if (n_valid < 3) return;                              // every group repeats a pixel
+    const int k = *s.iter;
+    const int nb = (p.N + kPixThreads - 1) / kPixThreads;
+    const int n_chunks = (p.G + 31) / 32;
+    bool first = true;
+    for (;;) {
+        int c = -1;
+        if (lane == 0) {
+            bool claim = first;
+            if (!first) {
+                const unsigned long long d = atomicAdd(s.p3p_done, 0ull);
+                const long long done = (long long)(d >> 32), sols = (long long)(d & 0xffffffffull);
+                const long long inflight = max(0LL, (long long)atomicAdd(s.p3p_claims, 0) - done);
+                claim = sols + (done > 0 ? inflight * sols / done : inflight) < (long long)p.S;
+            }
+            if (claim) c = atomicAdd(s.p3p_claims, 1);
+        }
+        first = false;
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c < 0 || c >= n_chunks) break;
+        const int g = c * 32 + lane;
+        int n = 0;
+        if (g < p.G) {
+            P3PSol sols[kMaxSols];
+            double weight;
+            n = solve_group(p, s, t, k, g, n_valid, nb, sols, &weight);
+            s.grp_count[g] = n;
+            s.grp_weight[g] = weight;
+            double* o = s.grp_sols + (size_t)g * kMaxSols * 12;
+            for (int i = 0; i < n; ++i)
+                for (int q = 0; q < 12; ++q) o[i * 12 + q] = sols[i].Rt[q];
+        }
+        int tot = n;
+        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        __threadfence();
+        if (lane == 0) atomicAdd(s.p3p_done, (1ull << 32) | (unsigned long long)tot);
+    }
+}
+
+// Groups solved for the current frame (a prefix of the group order).
+__device__ __forceinline__ int groups_solved(const DevParams& p, const DevState& s)
+{
+    const int n_chunks = (p.G + 31) / 32;
+    return min(min(*s.p3p_claims, n_chunks) * 32, p.G);
+}
+
+// One warp per block spreads the FP64 solves over the SMs. The first wave
+// is sized for about 1.1 S solutions at the yield of driving-like windows
+// (1.4-1.5 solutions per group); further chunks are claimed as needed.
 void launch_p3p_groups(const DevParams& p, const DevState& s, int t, cudaStream_t st)
 {
-    k_p3p_groups<<<(p.G + 31) / 32, 32, 0, st>>>(p, s, t);
+    const int n_chunks = (p.G + 31) / 32;
+    const int wave = std::max(1, std::min(n_chunks, (3 * p.S + 127) / 128));
+    k_p3p_groups<<<wave, 32, 0, st>>>(p, s, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -333,8 +405,9 @@ __global__ void k_hyp_scan(DevParams p, DevState s)
 {
     __shared__ int wsum[32];
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int seg = (p.G + nt - 1) / nt;
-    const int g0 = min(tid * seg, p.G), g1 = min(g0 + seg, p.G);
+    const int G = groups_solved(p, s);
+    const int seg = (G + nt - 1) / nt;
+    const int g0 = min(tid * seg, G), g1 = min(g0 + seg, G);
     // segments of a multiple of 4 counts start 16-byte aligned (the arrays are
     // 256-byte aligned): read and write them four at a time
     const bool vec = (seg & 3) == 0;
@@ -458,7 +531,7 @@ __device__ void se3_exp_vec(const double* p6, double* Rt)
 __global__ void k_hyp_write(DevParams p, DevState s)
 {
     const int gi = blockIdx.x * blockDim.x + threadIdx.x;
-    if (gi >= p.G * kMaxSols) return;
+    if (gi >= groups_solved(p, s) * kMaxSols) return;
     const int g = gi / kMaxSols, i = gi % kMaxSols;
     if (i >= s.grp_count[g]) return;
     const int h = s.grp_offset[g] + i;
@@ -485,7 +558,8 @@ __global__ void k_hyp_write(DevParams p, DevState s)
 void launch_hyp_collect(const DevParams& p, const DevState& s, cudaStream_t st)
 {
     k_hyp_scan<<<1, 1024, 0, st>>>(p, s);
-    k_hyp_write<<<(p.G * kMaxSols + 63) / 64, 64, 0, st>>>(p, s);
+    // sized for the budget; threads past the solved prefix return at once
+    k_hyp_write<<<(p.G * kMaxSols + 127) / 128, 128, 0, st>>>(p, s);
 }
 
 // Scoring form of caller-given hypotheses already copied to hyp_Rt.

@@ -140,6 +140,9 @@ size_t layout(voldor_ctx& c, char* base)
     s.pix_geo = (double*)take(6 * N * sizeof(double));
     s.prep_done = (unsigned*)take(4);
     s.pix_count = (int*)take(4);
+    s.pix_vmask = (unsigned*)take(((N + kPixThreads - 1) / kPixThreads) * (kPixThreads / 32) * 4);
+    s.p3p_claims = (int*)take(4);
+    s.p3p_done = (unsigned long long*)take(8);
     s.grp_sols = (double*)take(G * kMaxSols * 12 * 8);
     s.grp_weight = (double*)take(G * 8);
     s.grp_count = (int*)take(G * 4);
@@ -200,12 +203,14 @@ bool enqueue_pose_update(voldor_ctx* c, int t, cudaEvent_t ev0, cudaEvent_t ev1,
     const DevState& s = c->ds;
     cudaStream_t st = c->stream;
     launch_frame_setup(p, s, st);
-    // the minimal groups and P3P (FP64) run beside the pixel records
+    launch_prep_count(p, s, t, st);
+    // the minimal groups (drawn from the valid pixels the count pass listed)
+    // and their P3P (FP64) run beside the write of the pixel records
     if (!cuda_ok(c, cudaEventRecord(c->ev_fork, st))) return false;
     if (!cuda_ok(c, cudaStreamWaitEvent(c->aux, c->ev_fork, 0))) return false;
     launch_p3p_groups(p, s, t, c->aux);
     if (!cuda_ok(c, cudaEventRecord(c->ev_join, c->aux))) return false;
-    launch_pose_prep(p, s, t, st);
+    launch_prep_write(p, s, t, st);
     if (!cuda_ok(c, cudaStreamWaitEvent(st, c->ev_join, 0))) return false;
     launch_hyp_collect(p, s, st);
     // External records become event-record nodes when the stream is captured
@@ -353,7 +358,7 @@ void voldor_default_params(voldor_params* p)
     p->inv_depth_min = 1.0 / 40.0; p->inv_depth_max = 1.0;
     p->x_min = 1e-6; p->x_max = 1e12; p->beta_min = 0.05;
     p->ms_tol = 1e-10;
-    p->hyps_per_frame = 256; p->groups_per_frame = 512; p->ms_max_iter = 100;
+    p->hyps_per_frame = 256; p->groups_per_frame = 1024; p->ms_max_iter = 100;
     p->criterion = VOLDOR_CRITERION_MIE;
     p->residual = VOLDOR_RESIDUAL_FISK;
     p->seed = 0; p->window_id = 0;
@@ -787,8 +792,8 @@ voldor_status voldor_autotune(voldor_ctx* c, int* hpt_out, int* chunks_out, floa
     if (!cuda_ok(c, cudaMemcpyAsync(&k_saved, c->ds.iter, 4, cudaMemcpyDeviceToHost, c->stream))) return kCuda;
     if (!cuda_ok(c, cudaStreamSynchronize(c->stream))) return kCuda;
     launch_frame_setup(c->dp, c->ds, c->stream);
-    launch_p3p_groups(c->dp, c->ds, 1, c->stream);
     launch_pose_prep(c->dp, c->ds, 1, c->stream);
+    launch_p3p_groups(c->dp, c->ds, 1, c->stream);
     launch_hyp_collect(c->dp, c->ds, c->stream);
     if (!launched(c)) return kCuda;
     cudaEvent_t e0, e1;

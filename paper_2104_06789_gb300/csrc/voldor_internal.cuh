@@ -77,7 +77,10 @@ struct DevState {
     unsigned* prep_done;      // [1] blocks of the count pass finished (0 between launches)
     double* pix_geo;          // [6][N] P_x, P_y, P_z in camera t-1, pi_{t-1} (u, v), 1 / P_z of the frame being prepared
     int* pix_count;           // [1]
+    unsigned* pix_vmask;      // [ceil(N / kPixThreads) * kPixThreads / 32] per-warp ballots of the valid pixels
     // P3P
+    int* p3p_claims;          // [1] 32-group chunks claimed by the P3P warps of the current frame
+    unsigned long long* p3p_done;   // [1] chunks solved (high 32 bits) and their solutions (low 32 bits)
     double* grp_sols;         // [G][4][12]
     double* grp_weight;       // [G]
     int* grp_count;           // [G]
@@ -256,6 +259,8 @@ __device__ __forceinline__ float neg_ell(const DevParams& p, float x, float n, b
 void launch_frame_setup(const DevParams& p, const DevState& s, cudaStream_t st);
 void launch_bootstrap(const DevParams& p, const DevState& s, const double* T1, cudaStream_t st);
 void launch_pose_prep(const DevParams& p, const DevState& s, int t, cudaStream_t st);
+void launch_prep_count(const DevParams& p, const DevState& s, int t, cudaStream_t st);
+void launch_prep_write(const DevParams& p, const DevState& s, int t, cudaStream_t st);
 void launch_p3p_groups(const DevParams& p, const DevState& s, int t, cudaStream_t st);
 void launch_hyp_collect(const DevParams& p, const DevState& s, cudaStream_t st);
 void launch_score(const DevParams& p, const DevState& s, int log_idx, cudaStream_t st);

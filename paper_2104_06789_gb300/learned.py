@@ -106,8 +106,7 @@ class Dataset:
 
 
 def make_params(inv_range, S):
-    return voldor.default_params(inv_depth_min=inv_range[0], inv_depth_max=inv_range[1], hyps_per_frame=S,
-                                 groups_per_frame=2 * S)
+    return voldor.default_params(inv_depth_min=inv_range[0], inv_depth_max=inv_range[1], hyps_per_frame=S)
 
 
 def init_weights(T, seed=0, width=32):

@@ -137,8 +137,12 @@ def _f32(a):
 
 
 def default_params(**overrides) -> Params:
+    """The library's defaults with overrides; the group budget follows S
+    (4 S) unless it is given."""
     p = Params()
     lib().voldor_default_params(C.byref(p))
+    if "hyps_per_frame" in overrides and "groups_per_frame" not in overrides:
+        overrides = dict(overrides, groups_per_frame=4 * int(overrides["hyps_per_frame"]))
     for k, v in overrides.items():
         setattr(p, k, v)
     return p

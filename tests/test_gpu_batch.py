@@ -23,7 +23,7 @@ def _windows():
 
 
 def _make(vd, w, i):
-    p = vd.default_params(hyps_per_frame=128, groups_per_frame=256, inv_depth_min=w.inv_depth_range[0],
+    p = vd.default_params(hyps_per_frame=128, inv_depth_min=w.inv_depth_range[0],
                           inv_depth_max=w.inv_depth_range[1], window_id=i)
     g = vd.Window(w.flows.astype(np.float16), w.K, p)
     g.bootstrap(w.poses[0])
@@ -62,7 +62,7 @@ def test_batch_rejects_bad_input(vd):
     g = _make(vd, w, 0)
     with pytest.raises(vd.VoldorError):
         vd.Batch([g, g], 1)
-    p = vd.default_params(hyps_per_frame=64, groups_per_frame=128)
+    p = vd.default_params(hyps_per_frame=64, )
     raw = vd.Window(w.flows.astype(np.float32), w.K, p)           # not bootstrapped
     with pytest.raises(vd.VoldorError) as e:
         vd.Batch([g, raw], 1)
@@ -93,7 +93,7 @@ def test_autotune_hyps_on_a_window(vd):
     smallest candidate, and the chosen count's window runs."""
     from paper_2104_06789_gb300 import synthetic, tuning
     w = synthetic.small_planes(seed=1003)
-    p = vd.default_params(hyps_per_frame=256, groups_per_frame=512, inv_depth_min=w.inv_depth_range[0],
+    p = vd.default_params(hyps_per_frame=256, inv_depth_min=w.inv_depth_range[0],
                           inv_depth_max=w.inv_depth_range[1])
     flows = w.flows.astype(np.float32)
     S, tried, _ = tuning.autotune_hyps(flows, w.K, p, w.poses[0], rot_tol=-1.0, trans_tol=-1.0)

@@ -18,7 +18,7 @@ def vd():
 def _run_window(vd):
     from paper_2104_06789_gb300 import synthetic
     w = synthetic.small_planes(seed=1000)
-    p = vd.default_params(hyps_per_frame=128, groups_per_frame=256, inv_depth_min=w.inv_depth_range[0],
+    p = vd.default_params(hyps_per_frame=128, inv_depth_min=w.inv_depth_range[0],
                           inv_depth_max=w.inv_depth_range[1])
     g = vd.Window(w.flows.astype(np.float32), w.K, p)
     g.bootstrap(w.poses[0])

@@ -40,7 +40,7 @@ def drive():
 def _pair(vd, oracle_lib, drive, rng):
     w, f16, f64 = drive
     depth, rig = f32_state(rng, w)
-    p = vd.default_params(hyps_per_frame=8192, groups_per_frame=16384, inv_depth_min=w.inv_depth_range[0],
+    p = vd.default_params(hyps_per_frame=8192, inv_depth_min=w.inv_depth_range[0],
                           inv_depth_max=w.inv_depth_range[1], seed=0, window_id=0)
     g = vd.Window(f16, w.K, p)
     ow = oracle_window(oracle_lib, w, f64, 8192, depth, rig, w.poses)
@@ -59,6 +59,34 @@ def test_dense_scores_full_size(vd, oracle_lib, drive, t, n):
     L_ref = ow.score(t, R[idx], tv[idx])
     rel = np.abs(L_gpu[idx] - L_ref) / np.abs(L_ref)
     assert rel.max() < 1e-5, (rel.max(), idx[np.argmax(rel)])
+    g.destroy()
+
+
+@pytest.mark.parametrize("t", [1, 5, 8])
+def test_hypotheses_full_size(vd, oracle_lib, drive, t):
+    """Minimal groups drawn over the frame's valid pixels, P3P and the
+    collection at S = 8192 in the benchmark's launch shape: exactly S
+    hypotheses, the same groups, slots and weights as the oracle, poses to
+    1e-9."""
+    w = drive[0]
+    rng = np.random.default_rng(310 + t)
+    g, ow, depth, rig = _pair(vd, oracle_lib, drive, rng)
+    rig = (0.5 + 0.5 * rig).astype(np.float32)
+    ow.wmap[:] = rig.astype(np.float64)
+    g.set_state(poses=w.poses, depth=depth, rigidness=rig, iteration=1)
+    g.pose_update(1, t)
+    hg = g.hypotheses()
+    R, tv, wts, grp, slot = ow.collect_hypotheses(1, t)
+    assert len(R) == 8192 and len(hg["R"]) == 8192
+    assert np.array_equal(hg["group"], grp) and np.array_equal(hg["slot"], slot)
+    assert np.array_equal(hg["weight"], wts)
+    # translations to 1e-9 relative to their size: spurious roots of far,
+    # thin triangles reach hundreds of metres, and P3P magnifies the FP64
+    # rounding of its inputs there (the two sides form K^-1 [x y 1] with a
+    # reciprocal and with a division)
+    assert np.abs(hg["R"] - R).max() < 1e-9
+    dt = np.linalg.norm(hg["t"] - tv, axis=1) / np.maximum(np.linalg.norm(tv, axis=1), 1.0)
+    assert dt.max() < 1e-9, dt.max()
     g.destroy()
 
 
@@ -100,7 +128,7 @@ def test_depth_sweep_full_size(vd, oracle_lib, drive):
 
 def test_em_step_full_size_tracks_the_ground_truth(vd, drive):
     w, f16, _ = drive
-    p = vd.default_params(hyps_per_frame=8192, groups_per_frame=16384, inv_depth_min=w.inv_depth_range[0],
+    p = vd.default_params(hyps_per_frame=8192, inv_depth_min=w.inv_depth_range[0],
                           inv_depth_max=w.inv_depth_range[1], seed=0, window_id=0)
     g = vd.Window(f16, w.K, p)
     g.bootstrap(w.poses[0])

@@ -25,7 +25,7 @@ def scene():
 
 def _pair(vd, oracle_lib, w, rng, S=256):
     depth, rig = f32_state(rng, w)
-    p = vd.default_params(hyps_per_frame=S, groups_per_frame=2 * S, inv_depth_min=w.inv_depth_range[0],
+    p = vd.default_params(hyps_per_frame=S, inv_depth_min=w.inv_depth_range[0],
                           inv_depth_max=w.inv_depth_range[1], criterion=vd.CRITERION_MLE)
     g = vd.Window(w.flows.astype(np.float32), w.K, p)
     ow = oracle_window(oracle_lib, w, w.flows.astype(np.float32).astype(np.float64), S, depth, rig, w.poses,
@@ -71,7 +71,7 @@ def test_mle_noiseless_window_keeps_its_truth(vd):
     at its true T_1 stays at its true poses under MLE."""
     from paper_2104_06789_gb300 import synthetic
     w = synthetic.small_planes(seed=1000, noise=False, nonrigid=False)
-    p = vd.default_params(hyps_per_frame=256, groups_per_frame=512, inv_depth_min=w.inv_depth_range[0],
+    p = vd.default_params(hyps_per_frame=256, inv_depth_min=w.inv_depth_range[0],
                           inv_depth_max=w.inv_depth_range[1], criterion=vd.CRITERION_MLE,
                           sigma_t=1e-8, sigma_r=1e-10)
     g = vd.Window(w.flows.astype(np.float32), w.K, p)

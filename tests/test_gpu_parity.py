@@ -31,8 +31,7 @@ def scene():
 
 def _gpu_window(vd, w, S=256, flows=None, **kw):
     flows = w.flows.astype(np.float32) if flows is None else flows
-    p = vd.default_params(hyps_per_frame=S, groups_per_frame=2 * S,
-                          inv_depth_min=w.inv_depth_range[0], inv_depth_max=w.inv_depth_range[1], **kw)
+    p = vd.default_params(hyps_per_frame=S, inv_depth_min=w.inv_depth_range[0], inv_depth_max=w.inv_depth_range[1], **kw)
     return vd.Window(flows, w.K, p)
 
 
@@ -101,7 +100,8 @@ def test_pose_update(vd, oracle_lib, scene, t):
     g.pose_update(k, t)
     hg = g.hypotheses()
     R, tv, wts, grp, slot = ow.collect_hypotheses(k, t)
-    assert len(hg["R"]) == len(R)
+    assert len(R) == 256 and len(hg["R"]) == len(R)        # exactly S
+    assert grp[-1] < 4 * 256
     assert np.array_equal(hg["group"], grp) and np.array_equal(hg["slot"], slot)
     assert np.array_equal(hg["weight"], wts)
     assert np.abs(hg["R"] - R).max() < 1e-9 and np.abs(hg["t"] - tv).max() < 1e-9

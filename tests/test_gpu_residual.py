@@ -27,7 +27,7 @@ def scene():
 
 def _pair(vd, oracle_lib, w, rng, criterion, S=256):
     depth, rig = f32_state(rng, w)
-    p = vd.default_params(hyps_per_frame=S, groups_per_frame=2 * S, inv_depth_min=w.inv_depth_range[0],
+    p = vd.default_params(hyps_per_frame=S, inv_depth_min=w.inv_depth_range[0],
                           inv_depth_max=w.inv_depth_range[1], criterion=criterion,
                           residual=vd.RESIDUAL_GAUSSIAN)
     g = vd.Window(w.flows.astype(np.float32), w.K, p)
@@ -96,7 +96,7 @@ def test_gaussian_noiseless_window_keeps_its_truth(vd):
     instead of saturating as the Fisk model's does.)"""
     from conftest import fronto_parallel_window
     flows, K, poses, depth = fronto_parallel_window(W=48, H=36, T=3, f=40.0)
-    p = vd.default_params(hyps_per_frame=256, groups_per_frame=512, inv_depth_min=1 / 40.0, inv_depth_max=1.0,
+    p = vd.default_params(hyps_per_frame=256, inv_depth_min=1 / 40.0, inv_depth_max=1.0,
                           residual=vd.RESIDUAL_GAUSSIAN, sigma_t=1e-8, sigma_r=1e-10)
     g = vd.Window(flows.astype(np.float32), K, p)
     g.bootstrap(poses[0])

@@ -25,7 +25,7 @@ def _centres(traj):
 
 def test_noiseless_sequence_is_followed(vd):
     w = synthetic.small_planes(seed=1000, T=10, noise=False, nonrigid=False)
-    p = vd.default_params(hyps_per_frame=1024, groups_per_frame=2048, inv_depth_min=w.inv_depth_range[0],
+    p = vd.default_params(hyps_per_frame=1024, inv_depth_min=w.inv_depth_range[0],
                           inv_depth_max=w.inv_depth_range[1], sigma_t=1e-8, sigma_r=1e-10)
     r = vo.SlidingWindowVO(w.K, T=4, stride=2, n_iters=3, params=p).run(w.flows.astype(np.float32), T1=w.poses[0])
     assert r["starts"] == [0, 2, 4, 6]
@@ -37,7 +37,7 @@ def test_noiseless_sequence_is_followed(vd):
 
 def test_noisy_driving_sequence_from_the_epipolar_start(vd):
     w = synthetic.driving(seed=3001, W=414, H=125, f=239.3, T=12)
-    p = vd.default_params(hyps_per_frame=1024, groups_per_frame=2048, inv_depth_min=w.inv_depth_range[0],
+    p = vd.default_params(hyps_per_frame=1024, inv_depth_min=w.inv_depth_range[0],
                           inv_depth_max=w.inv_depth_range[1])
     r = vo.SlidingWindowVO(w.K, T=6, stride=3, n_iters=5, params=p).run(
         w.flows.astype(np.float16).astype(np.float32), T1=None, baseline=float(np.linalg.norm(w.poses[0][:3, 3])))
@@ -48,7 +48,7 @@ def test_noisy_driving_sequence_from_the_epipolar_start(vd):
 
 def test_ground_plane_fixes_a_wrong_initial_scale(vd):
     w = synthetic.driving(seed=3001, W=414, H=125, f=239.3, T=12)
-    p = vd.default_params(hyps_per_frame=1024, groups_per_frame=2048, inv_depth_min=w.inv_depth_range[0],
+    p = vd.default_params(hyps_per_frame=1024, inv_depth_min=w.inv_depth_range[0],
                           inv_depth_max=w.inv_depth_range[1])
     d = vo.SlidingWindowVO(w.K, T=6, stride=3, n_iters=5, params=p)
     flows = w.flows.astype(np.float16).astype(np.float32)

@@ -7,6 +7,8 @@ enumeration, or a noiseless synthetic scene whose answer is known exactly.
 import itertools
 import math
 
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -361,18 +363,69 @@ def test_depth_samples_uniform_in_inverse_depth(oracle_lib):
 
 
 def test_group_draws_uniform(oracle_lib):
-    import ctypes
+    """Group pixels are uniform over the list handed to the draw and distinct
+    with the birthday probability of three draws from n."""
     from scipy import stats
     flows, K, poses, depth = fronto_parallel_window(W=10, H=10, T=1)
     ow = oracle_lib.OracleWindow(flows, K, S=8)
+    valid = np.arange(3, 100, 2, dtype=np.int64)          # any increasing list
+    n = valid.size
     counts = np.zeros(100)
-    j = np.zeros(3, dtype=np.int64)
     distinct = 0
     for g in range(5000):
-        distinct += oracle_lib.lib().or_draw_group(ow.ref, 2, 1, g, j.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+        ok, j = ow.draw_group(2, 1, g, valid)
+        distinct += ok
         counts[j] += 1
-    assert stats.chisquare(counts).pvalue > 1e-3
-    assert distinct == pytest.approx(5000 * 0.99 * 0.98, rel=0.02)
+    assert counts[np.setdiff1d(np.arange(100), valid)].sum() == 0
+    assert stats.chisquare(counts[valid]).pvalue > 1e-3
+    assert distinct == pytest.approx(5000 * (1 - 1 / n) * (1 - 2 / n), rel=0.02)
+    ok, _ = ow.draw_group(2, 1, 0, np.zeros(0, dtype=np.int64))
+    assert not ok
+
+
+def test_valid_pixels_are_the_correspondences(oracle_lib):
+    """V_t lists, in pixel order, exactly the pixels whose pi_{t-1} lies inside
+    I_{t-1} in front of camera t-1 (checked per pixel through or_frame_ell's
+    validity report); from frame 2 on the pixels that the earlier motion
+    carries out of the image drop out of the list."""
+    flows, K, poses, depth = fronto_parallel_window(W=24, H=18, T=3)
+    ow = oracle_lib.OracleWindow(flows, K, S=8)
+    ow.theta[:] = depth
+    ow.poses[:] = poses
+    for t in (1, 2, 3):
+        v = ow.valid_pixels(t)
+        assert np.all(np.diff(v) > 0)
+        brute = []
+        for j in range(depth.size):
+            flag = ctypes.c_int(0)
+            oracle_lib.lib().or_frame_ell(ow.ref, t, j, float(ow.theta.flat[j]), ctypes.byref(flag))
+            if flag.value >= 1:
+                brute.append(j)
+        assert np.array_equal(v, np.array(brute, dtype=np.int64))
+    assert ow.valid_pixels(1).size == depth.size            # pi_0 is the pixel itself
+    assert 0 < ow.valid_pixels(2).size < depth.size
+
+
+def test_every_frame_collects_exactly_S(oracle_lib):
+    """With the draws over V_t, every frame of a driving-like window collects
+    exactly S hypotheses within the 4 S group budget, from groups whose three
+    pixels all have a correspondence, in increasing group order."""
+    from paper_2104_06789_gb300 import synthetic as sy
+    w = sy.driving(W=207, H=63, f=119.7, T=8, seed=3000)
+    S = 512
+    ow = oracle_lib.OracleWindow(w.flows, w.K, S=S, inv_depth_min=w.inv_depth_range[0],
+                                 inv_depth_max=w.inv_depth_range[1])
+    ow.bootstrap(w.poses[0])
+    ow.poses[:] = w.poses
+    for t in range(1, w.T + 1):
+        valid = set(ow.valid_pixels(t).tolist())
+        assert len(valid) < w.W * w.H or t == 1
+        R, tv, wt, grp, slot = ow.collect_hypotheses(0, t)
+        assert len(grp) == S, (t, len(grp))
+        assert np.all(np.diff(grp) >= 0) and grp[-1] < 4 * S
+        for g in np.unique(grp)[:20]:
+            ok, j = ow.draw_group(0, t, int(g), ow.valid_pixels(t))
+            assert ok and all(int(x) in valid for x in j)
 
 
 # ---------------------------------------------------------------------------

@@ -48,15 +48,15 @@ def _truth(T=4):
 @pytest.mark.parametrize("err0,expect", [(1e-6, 512), (2e-4, 1024), (6e-4, 2048), (1e-2, 4096)])
 def test_smallest_agreeing_count_is_chosen(err0, expect):
     truth = _truth()
-    params = voldor.Params(hyps_per_frame=4096, groups_per_frame=8192, seed=7)
+    params = voldor.Params(hyps_per_frame=4096, groups_per_frame=16384, seed=7)
     FakeWindow.made = []
     mk = lambda f, K, p: FakeWindow(truth, 4096, err0, p)
     S, tried, tol = tuning.autotune_hyps(None, (1, 1, 0, 0), params, np.eye(4), make_window=mk, rot_tol=1e-3,
                                          trans_tol=1e-3)
     assert S == expect and tol == (1e-3, 1e-3)
     # the reference ran first, with the window's own counts and key; groups scale with S
-    assert FakeWindow.made[0] == (4096, 8192, 7)
-    assert all(g == 2 * h and sd == 7 for h, g, sd in FakeWindow.made)
+    assert FakeWindow.made[0] == (4096, 16384, 7)
+    assert all(g == 4 * h and sd == 7 for h, g, sd in FakeWindow.made)
     assert [s for s, _, _ in tried] == [512, 1024, 2048][:len(tried)]
     assert params.hyps_per_frame == 4096            # the caller's parameters are untouched
 
@@ -67,12 +67,12 @@ def test_default_bound_is_the_reference_spread(err0, expect):
     key sets them; a candidate is accepted when no farther from the reference
     than that run."""
     truth = _truth()
-    params = voldor.Params(hyps_per_frame=4096, groups_per_frame=8192, seed=7)
+    params = voldor.Params(hyps_per_frame=4096, groups_per_frame=16384, seed=7)
     FakeWindow.made = []
     mk = lambda f, K, p: FakeWindow(truth, 4096, err0, p, spread=1e-3)
     S, tried, (rt, tt) = tuning.autotune_hyps(None, (1, 1, 0, 0), params, np.eye(4), make_window=mk)
     assert S == expect
-    assert FakeWindow.made[1] == (4096, 8192, 8)                  # the spread run
+    assert FakeWindow.made[1] == (4096, 16384, 8)                  # the spread run
     assert rt == pytest.approx(1e-3, rel=1e-6) and tt == pytest.approx(1e-3, rel=1e-6)
 
 

@@ -66,7 +66,7 @@ def test_noalloc_scores_match_the_context_entry_point():
     w = small_window(seed=1000)
     rng = np.random.default_rng(77)
     depth, rig = f32_state(rng, w)
-    p = voldor.default_params(hyps_per_frame=256, groups_per_frame=512, inv_depth_min=w.inv_depth_range[0],
+    p = voldor.default_params(hyps_per_frame=256, inv_depth_min=w.inv_depth_range[0],
                               inv_depth_max=w.inv_depth_range[1])
     g = voldor.Window(w.flows.astype(np.float32), w.K, p)
     g.set_state(poses=w.poses, depth=depth, rigidness=rig, iteration=0)
