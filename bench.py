@@ -74,6 +74,8 @@ def parse_args():
     ap.add_argument("--workers", type=int, default=0, help="scene-generator processes (0: cpu count - 1)")
     ap.add_argument("--save-weights", default="")
     ap.add_argument("--weights", default="", help="with --learned: evaluate these weights instead of training")
+    ap.add_argument("--probe-sfu", action="store_true",
+                    help="print the SFU probe's results per SM clock (exp2, log2, rcp) and exit")
     ap.add_argument("--net", type=int, default=0,
                     help="time the proposal network instead: forward passes on this many 1242x375 T=8 flow stacks")
     return ap.parse_args()
@@ -176,28 +178,35 @@ def variant_overrides(args):
     return {"criterion": int(args.criterion == "mle"), "residual": int(args.residual == "gaussian")}
 
 
-def oracle_sample(w, S, iters, n_score_hyps=4, n_groups=64, variant=None):
-    """Times the FP64 oracle on parts of one EM iteration of window `w` and
-    scales each part linearly to the full configuration: dense scoring of
-    n_score_hyps hypotheses per frame (cost linear in S), collection of
-    n_groups minimal groups per frame (linear in the 2S groups drawn), and one
-    pass of the per-pixel steps (E-step, MIE sweep, rigidness). Returns
-    (Mpixel*frame/s, seconds of CPU work, description)."""
+def _scored(hyps_scored, T, S):
+    """Hypotheses scored on frames 1..T (the GPU's per-frame counts, S when
+    not given)."""
+    return [S] * T if hyps_scored is None else [float(h) for h in hyps_scored]
+
+
+def oracle_sample(w, S, iters, n_score_hyps=4, variant=None, hyps_scored=None):
+    """Times the FP64 oracle on one EM iteration of window `w`: dense scoring
+    of n_score_hyps hypotheses per frame, scaled linearly (its cost is linear
+    in the count) to the hypotheses the GPU scored on that frame; the minimal
+    groups, P3P and collection of S hypotheses per frame, timed whole; one
+    pass of the per-pixel steps (E-step, MIE sweep, rigidness), timed whole.
+    Returns (Mpixel*frame/s, seconds of CPU work, description)."""
     import oracle
     oracle.build()
     flows = w.flows.astype(np.float16).astype(np.float64)
-    ow = oracle.OracleWindow(flows, w.K, S=n_groups * 4, G=n_groups, inv_depth_min=w.inv_depth_range[0],
+    ow = oracle.OracleWindow(flows, w.K, S=S, G=4 * S, inv_depth_min=w.inv_depth_range[0],
                              inv_depth_max=w.inv_depth_range[1], **(variant or {}))
     ow.bootstrap(w.poses[0])
-    t0 = time.perf_counter()
+    scored = _scored(hyps_scored, w.T, S)
+    t_score = []
     for t in range(1, w.T + 1):
         R = np.tile(w.poses[t - 1][:3, :3], (n_score_hyps, 1, 1))
         tv = np.tile(w.poses[t - 1][:3, 3], (n_score_hyps, 1))
+        t0 = time.perf_counter()
         ow.score(t, R, tv)
-    t_score = time.perf_counter() - t0
+        t_score.append(time.perf_counter() - t0)
     t0 = time.perf_counter()
-    for t in range(1, w.T + 1):
-        ow.collect_hypotheses(0, t)
+    n_col = [len(ow.collect_hypotheses(0, t)[0]) for t in range(1, w.T + 1)]
     t_groups = time.perf_counter() - t0
     t0 = time.perf_counter()
     em = ow.emissions()
@@ -205,24 +214,26 @@ def oracle_sample(w, S, iters, n_score_hyps=4, n_groups=64, variant=None):
     ow.mie_sweep(0, q)
     ow.rigidness()
     t_pixel = time.perf_counter() - t0
-    per_iter = t_score * (S / n_score_hyps) + t_groups * (2 * S / n_groups) + t_pixel
+    score_full = sum(ts * n / n_score_hyps for ts, n in zip(t_score, scored))
+    per_iter = score_full + t_groups + t_pixel
+    measured = sum(t_score) + t_groups + t_pixel
     value = w.H * w.W * w.T / per_iter / 1e6
-    desc = (f"one EM iteration of the same window, scaled: dense scoring timed on {n_score_hyps} hypotheses x "
-            f"{w.T} frames (x{S // n_score_hyps}), minimal groups on {n_groups} per frame "
-            f"(x{2 * S // n_groups}), E-step + MIE sweep + rigidness timed whole; "
-            f"{per_iter:.1f} s/iteration extrapolated from {t_score + t_groups + t_pixel:.1f} s measured")
-    return value, t_score + t_groups + t_pixel, desc
+    desc = (f"one EM iteration of the same window: dense scoring timed on {n_score_hyps} hypotheses x {w.T} "
+            f"frames and scaled to the {sum(scored) / w.T:.0f} hypotheses per frame the GPU scored; minimal groups, "
+            f"P3P and collection timed whole ({min(n_col)}-{max(n_col)} hypotheses per frame); E-step + MIE sweep + "
+            f"rigidness timed whole; {per_iter:.1f} s/iteration extrapolated from {measured:.1f} s measured")
+    return value, measured, desc
 
 
 def _oracle_piece(args):
     """One process's share of the parallel oracle sample: dense scoring of the
-    sampled hypotheses and the sampled group collection, for frame t.
-    Returns (scoring seconds, groups seconds)."""
-    flows16, K, poses, inv_range, t, n_score_hyps, n_groups, variant = args
+    sampled hypotheses and the collection of frame t's S hypotheses.
+    Returns (scoring seconds, collection seconds)."""
+    flows16, K, poses, inv_range, t, n_score_hyps, S, variant = args
     import oracle
     flows = flows16.astype(np.float64)
-    ow = oracle.OracleWindow(flows, K, S=n_groups * 4, G=n_groups, inv_depth_min=inv_range[0],
-                             inv_depth_max=inv_range[1], **variant)
+    ow = oracle.OracleWindow(flows, K, S=S, G=4 * S, inv_depth_min=inv_range[0], inv_depth_max=inv_range[1],
+                             **variant)
     ow.bootstrap(poses[0])
     R = np.tile(poses[t - 1][:3, :3], (n_score_hyps, 1, 1))
     tv = np.tile(poses[t - 1][:3, 3], (n_score_hyps, 1))
@@ -234,17 +245,17 @@ def _oracle_piece(args):
     return t_score, time.perf_counter() - t0
 
 
-def oracle_sample_parallel(w, S, iters, workers, n_score_hyps=4, n_groups=64, variant=None):
-    """The same sample as oracle_sample with its independent pieces (the
-    frames' dense scoring and group collection) spread over `workers` spawned
-    processes, each running the unchanged single-threaded oracle; the
-    per-pixel passes (one sequential pass each) stay on one core. Returns
-    (Mpixel*frame/s, wall seconds, description)."""
+def oracle_sample_parallel(w, S, iters, workers, n_score_hyps=4, variant=None, hyps_scored=None):
+    """The same sample as oracle_sample with its independent pieces (each
+    frame's dense scoring and collection) on `workers` spawned processes,
+    each running the unchanged single-threaded oracle; the per-pixel passes
+    (one sequential pass each) stay on one core. Returns (Mpixel*frame/s,
+    wall seconds, description, processes)."""
     import multiprocessing as mp
     import oracle
     oracle.build()
     f16 = w.flows.astype(np.float16)
-    jobs = [(f16, w.K, w.poses, w.inv_depth_range, t, n_score_hyps, n_groups, variant or {})
+    jobs = [(f16, w.K, w.poses, w.inv_depth_range, t, n_score_hyps, S, variant or {})
             for t in range(1, w.T + 1)]
     keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
     saved = {k: os.environ.get(k) for k in keys}
@@ -262,13 +273,12 @@ def oracle_sample_parallel(w, S, iters, workers, n_score_hyps=4, n_groups=64, va
                 os.environ.pop(k, None)
             else:
                 os.environ[k] = v
-    # scale: every piece is linear in its count; with P processes the scoring
-    # and groups of all frames take max over processes of their pieces
-    t_score = sum(p[0] for p in parts) * (S / n_score_hyps)
-    t_groups = sum(p[1] for p in parts) * (2 * S / n_groups)
+    scored = _scored(hyps_scored, w.T, S)
+    t_score = sum(p[0] * n / n_score_hyps for p, n in zip(parts, scored))
+    t_groups = sum(p[1] for p in parts)
     n_proc = min(workers, len(jobs))
     flows = f16.astype(np.float64)
-    ow = oracle.OracleWindow(flows, w.K, S=n_groups * 4, G=n_groups, inv_depth_min=w.inv_depth_range[0],
+    ow = oracle.OracleWindow(flows, w.K, S=S, G=4 * S, inv_depth_min=w.inv_depth_range[0],
                              inv_depth_max=w.inv_depth_range[1], **(variant or {}))
     ow.bootstrap(w.poses[0])
     t0 = time.perf_counter()
@@ -277,17 +287,99 @@ def oracle_sample_parallel(w, S, iters, workers, n_score_hyps=4, n_groups=64, va
     ow.mie_sweep(0, q)
     ow.rigidness()
     t_pixel = time.perf_counter() - t0
-    # the frames' pieces are independent: with n_proc processes the scoring and
-    # collection of a full iteration split into S / n_score_hyps hypothesis blocks
-    # per frame, spread evenly over the processes
+    # the frames' pieces are independent, and a frame's dense scoring splits
+    # into hypothesis blocks: spread evenly over the processes
     per_iter = (t_score + t_groups) / n_proc + t_pixel
     value = w.H * w.W * w.T / per_iter / 1e6
     desc = (f"one EM iteration of the same window on {n_proc} processes (spawned, one thread each, the unchanged "
-            f"oracle): dense scoring ({n_score_hyps} hypotheses x {w.T} frames measured, x{S // n_score_hyps}) and "
-            f"minimal groups ({n_groups} per frame, x{2 * S // n_groups}) split evenly over the processes, E-step + "
-            f"MIE sweep + rigidness on one core; {per_iter:.1f} s/iteration extrapolated from {t_par + t_pixel:.1f} "
-            f"s measured")
+            f"oracle): dense scoring ({n_score_hyps} hypotheses x {w.T} frames measured, scaled to the "
+            f"{sum(scored) / w.T:.0f} per frame the GPU scored) and the collection of S hypotheses per frame "
+            f"(timed whole) split evenly over the processes, E-step + MIE sweep + rigidness on one core; "
+            f"{per_iter:.1f} s/iteration extrapolated from {t_par + t_pixel:.1f} s measured")
     return value, t_par + t_pixel, desc, n_proc
+
+
+def _f32_hypotheses(rng, R0, t0, n, rot=0.02, trans=0.02):
+    """n hypotheses near (R0, t0) whose scoring form (R - I, t) is exact in
+    FP32, so that both sides score the same poses."""
+    Rs, ts = [], []
+    for i in range(n):
+        ax = rng.normal(size=3)
+        ax /= np.linalg.norm(ax)
+        a = rng.uniform(0, rot) if i else 0.0
+        Kx = np.array([[0, -ax[2], ax[1]], [ax[2], 0, -ax[0]], [-ax[1], ax[0], 0]])
+        R = (np.eye(3) + np.sin(a) * Kx + (1 - np.cos(a)) * Kx @ Kx) @ R0
+        E = (R - np.eye(3)).astype(np.float32).astype(np.float64)
+        Rs.append(np.eye(3) + E)
+        ts.append((t0 + (rng.normal(size=3) * trans if i else 0.0)).astype(np.float32).astype(np.float64))
+    return np.array(Rs), np.array(ts)
+
+
+def error_vs_oracle(win, w, flows16, params, variant, n_hyps=8, k=1):
+    """Per-result error of the GPU against the FP64 oracle on the window's
+    final state (depth, rigidness and poses after the timed steps, read back
+    and handed to the oracle exactly): dense scores L_h of n_hyps hypotheses
+    of the last frame (relative); every per-pixel log-likelihood ell = log W
+    of the rigidness update (relative, with the FP32 storage of W); the depth
+    sweep's labels (agreement); the last frame's pose update (identical
+    hypothesis set, then the oracle's meanshift on the GPU's hypotheses and
+    seed: rotation angle and relative translation of the result)."""
+    import oracle
+    oracle.build()
+    P, D, Wm = win.get_pose_depth_rigidness()
+    ow = oracle.OracleWindow(flows16.astype(np.float64), w.K, S=params.hyps_per_frame, G=params.groups_per_frame,
+                             inv_depth_min=params.inv_depth_min, inv_depth_max=params.inv_depth_max,
+                             seed=params.seed, window_id=params.window_id, **variant)
+    ow.theta[:] = D.astype(np.float64)
+    ow.wmap[:] = Wm.astype(np.float64)
+    ow.poses[:] = P
+    out = {}
+    t = w.T
+    rng = np.random.default_rng(5)
+    R, tv = _f32_hypotheses(rng, P[t - 1][:3, :3], P[t - 1][:3, 3], n_hyps)
+    Lg, Lo = win.score_hypotheses(t, R, tv), ow.score(t, R, tv)
+    out["score_rel_max"] = float(np.max(np.abs(Lg - Lo) / np.abs(Lo)))
+    out["score_hyps"] = n_hyps
+    # rigidness update: log W per (t, j)
+    win.rigidness_update()
+    _, _, W_gpu = win.get_pose_depth_rigidness(poses=False, depth=False)
+    ell_ref = np.log(ow.emissions())
+    ell_gpu = np.log(W_gpu.astype(np.float64))
+    rel = np.abs(ell_gpu - ell_ref) / np.maximum(np.abs(ell_ref), 1e-300)
+    out["ell_rel_max"] = float(rel.max())
+    out["ell_within_bound"] = float(np.mean(np.abs(ell_gpu - ell_ref) <= 1e-5 * np.abs(ell_ref) + 2.0 ** -23))
+    ow.wmap[:] = W_gpu.astype(np.float64)
+    # pose update of the last frame
+    win.pose_update(k, t)
+    hg = win.hypotheses()
+    Ro, to, wo, go, so = ow.collect_hypotheses(k, t)
+    same = len(go) == len(hg["group"]) and np.array_equal(go, hg["group"]) and np.array_equal(so, hg["slot"])
+    out["hyps_identical"] = bool(same and np.array_equal(wo, hg["weight"]))
+    out["hyps_collected"] = int(len(hg["group"]))
+    p6 = np.array([oracle.se3_log(Rh, th) for Rh, th in zip(hg["R"], hg["t"])])
+    it, x = oracle.meanshift(p6, hg["weight"], hg["seed"], params.sigma_t, params.sigma_r, params.ms_max_iter,
+                             params.ms_tol)
+    Rm, tm = oracle.se3_exp(x)
+    Pg, _, _ = win.get_pose_depth_rigidness(depth=False, rigidness=False)
+    c = (np.trace(Pg[t - 1][:3, :3] @ Rm.T) - 1.0) / 2.0
+    out["pose_rot_rad"] = float(np.arccos(np.clip(c, -1.0, 1.0)))
+    out["pose_trans_rel"] = float(np.linalg.norm(Pg[t - 1][:3, 3] - tm) / np.linalg.norm(tm))
+    ow.poses[t - 1] = Pg[t - 1]
+    # depth sweep on a seeded smoothed rigidness
+    q = rng.uniform(0, 1, size=(w.T, w.H, w.W)).astype(np.float32)
+    win.set_buffer(voldor_mod().BUF_SMOOTHED, q)
+    win.depth_update(k)
+    lab_gpu = win.get_buffer(voldor_mod().BUF_LABELS, (w.H, w.W), np.uint8)
+    lab_ref = ow.mie_sweep(k, q.astype(np.float64))
+    out["sweep_labels_identical"] = float(np.mean(lab_gpu == lab_ref))
+    out["tolerances"] = {"score_rel": 1e-5, "ell": "1e-5 |ell| + 2^-23", "labels": 0.999,
+                         "pose_rot_rad": 1e-6, "pose_trans_rel": 1e-6}
+    return out
+
+
+def voldor_mod():
+    from paper_2104_06789_gb300 import voldor
+    return voldor
 
 
 # ---------------------------------------------------------------------------
@@ -305,7 +397,7 @@ def run_reference(args):
     desc, n_proc = "", 1
     for i in range(args.warmup + args.steps):
         v, secs, desc, n_proc = oracle_sample_parallel(w, args.hyps, args.iters, os.cpu_count() or 1,
-                                                       n_score_hyps=2, n_groups=32, variant=variant_overrides(args))
+                                                       n_score_hyps=2, variant=variant_overrides(args))
         if i >= args.warmup:
             steps.append(v)
     value = float(np.mean(steps))
@@ -363,7 +455,7 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    score_ms, score_pairs = [], []
+    score_ms, score_pairs, score_hyps = [], [], []
     launches0 = win.kernel_launches()
     if dist is not None:
         dist.barrier()
@@ -375,9 +467,10 @@ def run_ours(args):
             evs[i][0].record(stream)
             step()
             evs[i][1].record(stream)
-            ms, pairs = win.get_score_times()
+            ms, pairs, nh = win.get_score_times(with_hyps=True)
             score_ms.extend(ms.tolist())
             score_pairs.extend(pairs.tolist())
+            score_hyps.extend(nh.tolist())
         torch.cuda.synchronize()
     launches = win.kernel_launches() - launches0
     total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), dist, f"cuda:{local_rank}")
@@ -412,47 +505,72 @@ def run_ours(args):
             dist.destroy_process_group()
         return
 
+    clocks = clk.summary()
     props = torch.cuda.get_device_properties(local_rank)
     sms = props.multi_processor_count
-    # SFU results per SM clock, measured on this GPU (exp2, log2, reciprocal),
+    # the SM clock of the timed region (median of the samples; the maximum
+    # clock if none were taken) converts per-clock peaks to rates
+    f_mhz = clocks["sm_mhz"] if clocks and clocks.get("sm_mhz") else NOMINAL_MAX_MHZ
+    # SFU results per SM clock, measured on this GPU (exp2, log2, reciprocal;
+    # whole-grid CUDA-event time over the SM clock measured in the probe),
     # combined over the variant's algorithmic mix per pair
-    rates = {name: voldor.probe_sfu_rate(op) for op, name in enumerate(("ex2", "lg2", "rcp"))}
+    probe = {name: voldor.probe_sfu_rate(op, with_clock=True) for op, name in enumerate(("ex2", "lg2", "rcp"))}
+    rates = {name: r for name, (r, _) in probe.items()}
     mix = dict(zip(("rcp", "lg2", "ex2"), ALGO_MUFU_MIX[(args.criterion, args.residual)]))
     ops_per_pair = sum(mix.values())
     per_clk = ops_per_pair / sum(n / rates[op] for op, n in mix.items())
-    peak = sms * per_clk * NOMINAL_MAX_MHZ * 1e6 / 1e12                # T SFU-ops/s
+    peak = sms * per_clk * f_mhz * 1e6 / 1e12                          # T SFU-ops/s
     score_ms = np.array(score_ms)
     score_pairs = np.array(score_pairs, dtype=np.float64)
     # algorithmic work per launch over the mean launch duration (= all timed
     # launches' work over their summed time)
-    achieved = (float(ops_per_pair * score_pairs.sum() / (score_ms.sum() * 1e-3)) / 1e12
-                if len(score_ms) else None)
+    pair_rate = float(score_pairs.sum() / (score_ms.sum() * 1e-3)) if len(score_ms) else None
+    achieved = ops_per_pair * pair_rate / 1e12 if pair_rate else None
     mix_txt = " + ".join(f"{n} {op}" for op, n in mix.items() if n)
+    # the count of the hot-path scope table: 6 MUFU per pair against the
+    # nominal 16 SFU results per SM clock
+    survey_peak = sms * MUFU_PER_SM_PER_CLK * f_mhz * 1e6 / 1e12
+    survey = ({"ops_per_pair": 6, "achieved": 6 * pair_rate / 1e12, "peak": survey_peak,
+               "frac": 6 * pair_rate / 1e12 / survey_peak,
+               "peak_source": f"{sms} SMs x {MUFU_PER_SM_PER_CLK} SFU results/clk/SM (nominal) x {f_mhz:.0f} MHz"}
+              if pair_rate and (args.criterion, args.residual) == ("mie", "fisk") else None)
     roofline = {"kernel": "k_score (dense hypothesis scoring)", "bound": "alu", "achieved": achieved,
                 "peak": peak, "unit": f"T SFU-op/s ({ops_per_pair} algorithmic SFU ops per hypothesis-pixel pair)",
                 "frac": achieved / peak if achieved else None,
                 "traffic": SCORE_TRAFFIC_BYTES.get((args.criterion, args.residual, args.hyps)),
                 "traffic_unit": "DRAM bytes per launch (ncu)",
                 "peak_source": (f"{sms} SMs x {per_clk:.2f} SFU results/clk/SM (measured: ex2 {rates['ex2']:.2f}, "
-                                f"lg2 {rates['lg2']:.2f}, rcp {rates['rcp']:.2f}; mix {mix_txt}) x "
-                                f"{NOMINAL_MAX_MHZ:.0f} MHz; nominal table value 16/clk/SM"),
+                                f"lg2 {rates['lg2']:.2f}, rcp {rates['rcp']:.2f} at a probe clock of "
+                                f"{probe['rcp'][1]:.0f} MHz; mix {mix_txt}) x {f_mhz:.0f} MHz (timed region)"),
+                "survey_count": survey,
                 "launches_timed": int(len(score_ms)), "mean_launch_ms": float(score_ms.mean()) if len(score_ms) else None,
                 "share_of_step": float(score_ms.sum() / total_ms) if len(score_ms) else None}
+    # hypotheses scored per frame (launch i scores frame i mod T + 1)
+    hyps_scored = None
+    if score_hyps:
+        h = np.array(score_hyps, dtype=np.float64)
+        hyps_scored = [float(h[f::w.T].mean()) for f in range(w.T)]
 
     cpu = cpu_par = None
     if world == 1 and not args.no_cpu:
-        v, secs, desc = oracle_sample(w, args.hyps, args.iters, variant=variant_overrides(args))
+        v, secs, desc = oracle_sample(w, args.hyps, args.iters, variant=variant_overrides(args),
+                                      hyps_scored=hyps_scored)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
         vp, secs_p, desc_p, n_proc = oracle_sample_parallel(w, args.hyps, args.iters, os.cpu_count() or 1,
-                                                            variant=variant_overrides(args))
+                                                            variant=variant_overrides(args), hyps_scored=hyps_scored)
         cpu_par = {"value": vp, "unit": UNIT, "cores": n_proc, "kind": "oracle", "sample": desc_p}
+    err = None
+    if world == 1 and not args.no_cpu:
+        err = error_vs_oracle(win, w, flows16, params, variant_overrides(args))
 
     cfg = config_dict(w, args, world)
+    if hyps_scored is not None:
+        cfg["hyps_scored_per_frame"] = hyps_scored
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": cfg, "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_parallel": cpu_par,
-            "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary()}
+            "e2e": e2e, "error_vs_oracle": err, "gpu_launches": int(launches), "clocks": clocks}
     print(json.dumps(line), flush=True)
     win.destroy()
     if dist is not None:
@@ -713,9 +831,26 @@ def run_learned(args):
     net.destroy()
 
 
+def run_probe_sfu():
+    """The SFU probe alone (one launch per op after its warm-up), for an ncu
+    capture of the probe kernel's pipe counters beside its own figures."""
+    import torch
+
+    from paper_2104_06789_gb300 import build, voldor
+    torch.cuda.set_device(0)
+    build.build()
+    out = {}
+    for op, name in enumerate(("ex2", "lg2", "rcp")):
+        r, f = voldor.probe_sfu_rate(op, with_clock=True)
+        out[name] = {"results_per_sm_clock": r, "sm_mhz": f}
+    print(json.dumps({"sfu_probe": out}), flush=True)
+
+
 def main():
     args = parse_args()
-    if args.net:
+    if args.probe_sfu:
+        run_probe_sfu()
+    elif args.net:
         run_net(args)
     elif args.learned:
         run_learned(args)

@@ -227,12 +227,14 @@ voldor_status voldor_set_buffer(voldor_ctx* ctx, int which, const void* host, si
 
 /* Per-launch device times (ms, CUDA events on the context's stream) of the
  * dense-scoring kernel during the last voldor_em_step, in launch order, and
- * (if `pairs` is not NULL) the (hypothesis, pixel) pairs each launch scored.
+ * (if `pairs` is not NULL) the (hypothesis, pixel) pairs each launch scored
+ * and (if `hyps` is not NULL) its hypothesis count.
  * Writes min(count, max) values; *count gets the number recorded. Requires
  * timing to be enabled with voldor_enable_timing(ctx, 1) before the step.
  * Synchronises. */
 voldor_status voldor_enable_timing(voldor_ctx* ctx, int on);
-voldor_status voldor_get_score_times(voldor_ctx* ctx, float* ms, long long* pairs, int max, int* count);
+voldor_status voldor_get_score_times(voldor_ctx* ctx, float* ms, long long* pairs, long long* hyps, int max,
+                                     int* count);
 
 /* Number of library kernels enqueued on this context so far (graph replays
  * count every kernel node of the graph). */
@@ -266,8 +268,9 @@ const char* voldor_last_error_string(const voldor_ctx* ctx);
  *           E = S (R - I) S^-1, tt = S t, S = diag(1, fy/fx, 1).
  *  xs_min, xs_max: floor and cap of the squared residual divided by fx^2.
  *  L:       device, n_hyps doubles, written.
- * Limits: 1 <= n_hyps <= 8192, n_pix >= 0; otherwise INVALID_ARG before any
- * device work. The first call on a device looks up the scratch array's device
+ * Limits: 1 <= n_hyps <= 8192, n_pix >= 0, records 16-byte aligned, hyps
+ * 4-byte aligned, L 8-byte aligned; otherwise INVALID_ARG before any device
+ * work. The first call on a device looks up the scratch array's device
  * address (with that device current); make that first call before any stream
  * capture. Every call writes each scratch cell it later reads, so nothing
  * carries over between calls -- but all calls share the one array, so calls
@@ -278,10 +281,13 @@ voldor_status voldor_score_records_noalloc(const float* records, int n_pix, cons
 
 /* Diagnostic for rooflines (no counterpart in the paper): measures the SFU
  * (special-function unit) throughput of the current GPU in results per SM
- * clock for op 0 = exp2, 1 = log2, 2 = reciprocal (approximate forms), by
- * timing independent chains with the SM cycle counter. Allocates and frees a
- * few KB; synchronises the device. Errors: INVALID_ARG, OOM, CUDA. */
-voldor_status voldor_probe_sfu_rate(int op, double* results_per_sm_clock);
+ * clock for op 0 = exp2, 1 = log2, 2 = reciprocal (approximate forms). One
+ * wave of 4 blocks per SM runs 16 independent chains per thread; the grid is
+ * timed with CUDA events and divided by the SM clock measured during the run
+ * (cycle counter over the global nanosecond timer, median over blocks), which
+ * is returned in *sm_mhz (may be NULL). Allocates and frees a few KB;
+ * synchronises the device. Errors: INVALID_ARG, OOM, CUDA. */
+voldor_status voldor_probe_sfu_rate(int op, double* results_per_sm_clock, double* sm_mhz);
 
 /* Exercises the expiry path of the bounded device-side waits (every mbarrier
  * wait of the library's kernels gives up after a poll limit and the call

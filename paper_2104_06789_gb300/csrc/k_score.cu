@@ -29,6 +29,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <algorithm>
+
 #include "voldor_internal.cuh"
 
 namespace vd {
@@ -689,6 +691,8 @@ extern "C" voldor_status voldor_score_records_noalloc(const float* records, int 
     using namespace vd;
     if (!records || !hyps || !L || n_pix < 0 || n_hyps < 1) return VOLDOR_ERR_INVALID_ARG;
     if (n_hyps > kStaticMaxHyps) return VOLDOR_ERR_INVALID_ARG;
+    // the kernel reads records as float4 and writes L as double
+    if (((uintptr_t)records & 15u) || ((uintptr_t)hyps & 3u) || ((uintptr_t)L & 7u)) return VOLDOR_ERR_INVALID_ARG;
     if (!(xs_min > 0.0) || !(xs_max > xs_min) || !std::isfinite(xs_max)) return VOLDOR_ERR_INVALID_ARG;
     double* partial = nullptr;
     if (static_partials(&partial) != cudaSuccess) {
@@ -706,47 +710,76 @@ extern "C" voldor_status voldor_score_records_noalloc(const float* records, int 
 
 // ---------------------------------------------------------------------------
 // Diagnostic: SFU (MUFU) throughput of this GPU in results per SM clock, for
-// the roofline of the dense scoring. Every thread runs 8 independent chains of
-// one SFU op; each block times itself with clock64, so the figure does not
-// depend on the clock frequency.
+// the roofline of the dense scoring. One wave of blocks (4 per SM, 256
+// threads) runs 16 independent chains of one SFU op per thread; the whole
+// grid is timed with CUDA events, and the SM clock during the run is measured
+// in the kernel (clock64 cycles over globaltimer nanoseconds of each block,
+// median over blocks), so results per SM clock = results / (grid time x SM
+// clock x SMs) holds at whatever clock the GPU ran.
 // ---------------------------------------------------------------------------
 namespace vd {
-__device__ __forceinline__ float sfu_step(int op, float v)
+constexpr int kProbeChains = 16;
+
+// One SFU op per chain step, fixed at compile time: with the op chosen at run
+// time inside the loop the compiler predicates the branches and issues every
+// branch's SFU instruction on each step.
+template <int OP>
+__device__ __forceinline__ float sfu_step(float v)
 {
     float y;
-    if (op == 0) {          // exp2(-|v|): stays in [0.5, 1)
+    if constexpr (OP == 0) {          // exp2(-|v|): stays in [0.5, 1)
         asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-fabsf(v)));
-    } else if (op == 1) {   // log2(v) + 1.5: converges to ~3.2, stays normal
+    } else if constexpr (OP == 1) {   // log2(v) + 1.5: converges to ~3.2, stays normal
         asm volatile("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(v));
         y += 1.5f;
-    } else {                // 1 / (-v): alternates between two normal values
+    } else {                          // 1 / (-v): alternates between two normal values
         asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-v));
     }
     return y;
 }
 
-__global__ void __launch_bounds__(256) k_sfu_probe(int op, int iters, float seed, float* sink, long long* cycles)
+__device__ __forceinline__ unsigned long long global_ns()
 {
-    float v[8];
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <int OP>
+__global__ void __launch_bounds__(256) k_sfu_probe(int iters, float seed, float* sink, long long* clk)
+{
+    float v[kProbeChains];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = seed + 0.001f * (float)((threadIdx.x + i) & 63);
+    for (int i = 0; i < kProbeChains; ++i) v[i] = seed + 0.001f * (float)((threadIdx.x + i) & 63);
     __syncthreads();
-    const long long t0 = clock64();
+    const long long c0 = clock64();
+    const unsigned long long g0 = global_ns();
     for (int it = 0; it < iters; ++it) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = sfu_step(op, v[i]);
+        for (int i = 0; i < kProbeChains; ++i) v[i] = sfu_step<OP>(v[i]);
     }
     __syncthreads();
-    const long long t1 = clock64();
+    const long long c1 = clock64();
+    const unsigned long long g1 = global_ns();
     float acc = 0.f;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) acc += v[i];
+    for (int i = 0; i < kProbeChains; ++i) acc += v[i];
     if (acc == 1234.5f) sink[threadIdx.x] = acc;     // keeps the chains alive
-    if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+    if (threadIdx.x == 0) {
+        clk[2 * blockIdx.x] = c1 - c0;
+        clk[2 * blockIdx.x + 1] = (long long)(g1 - g0);
+    }
+}
+
+void launch_sfu_probe(int op, int blocks, int threads, int iters, float seed, float* sink, long long* clk)
+{
+    if (op == 0) k_sfu_probe<0><<<blocks, threads>>>(iters, seed, sink, clk);
+    else if (op == 1) k_sfu_probe<1><<<blocks, threads>>>(iters, seed, sink, clk);
+    else k_sfu_probe<2><<<blocks, threads>>>(iters, seed, sink, clk);
 }
 }  // namespace vd
 
-extern "C" voldor_status voldor_probe_sfu_rate(int op, double* results_per_sm_clock)
+extern "C" voldor_status voldor_probe_sfu_rate(int op, double* results_per_sm_clock, double* sm_mhz)
 {
     using namespace vd;
     if (!results_per_sm_clock || op < 0 || op > 2) return VOLDOR_ERR_INVALID_ARG;
@@ -755,21 +788,39 @@ extern "C" voldor_status voldor_probe_sfu_rate(int op, double* results_per_sm_cl
         return VOLDOR_ERR_CUDA;
     const int blocks = sms * 4, threads = 256, iters = 4096;
     float* sink = nullptr;
-    long long* cyc = nullptr;
+    long long* clk = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaMalloc(&sink, threads * sizeof(float)) != cudaSuccess) return VOLDOR_ERR_OOM;
-    if (cudaMalloc(&cyc, blocks * sizeof(long long)) != cudaSuccess) { cudaFree(sink); return VOLDOR_ERR_OOM; }
+    if (cudaMalloc(&clk, 2 * blocks * sizeof(long long)) != cudaSuccess) { cudaFree(sink); return VOLDOR_ERR_OOM; }
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
     const float seed = op == 1 ? 1.5f : 0.75f;
-    k_sfu_probe<<<blocks, threads>>>(op, 64, seed, sink, cyc);          // warm-up
-    k_sfu_probe<<<blocks, threads>>>(op, iters, seed, sink, cyc);
-    std::vector<long long> h(blocks);
-    cudaError_t e = cudaMemcpy(h.data(), cyc, blocks * sizeof(long long), cudaMemcpyDeviceToHost);
+    float ms = 0.f;
+    std::vector<long long> h(2 * blocks);
+    if (e == cudaSuccess) {
+        launch_sfu_probe(op, blocks, threads, 256, seed, sink, clk);          // warm-up
+        cudaEventRecord(e0);
+        launch_sfu_probe(op, blocks, threads, iters, seed, sink, clk);
+        cudaEventRecord(e1);
+        e = cudaEventSynchronize(e1);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess) e = cudaMemcpy(h.data(), clk, h.size() * sizeof(long long), cudaMemcpyDeviceToHost);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
     cudaFree(sink);
-    cudaFree(cyc);
-    if (e != cudaSuccess) return VOLDOR_ERR_CUDA;
-    // 4 resident blocks per SM share it: results per SM clock = 4 * per-block ops / cycles
-    double sum = 0.0;
-    for (int b = 0; b < blocks; ++b) sum += 4.0 * (double)threads * 8.0 * iters / (double)h[b];
-    *results_per_sm_clock = sum / blocks;
+    cudaFree(clk);
+    if (e != cudaSuccess || !(ms > 0.f)) return VOLDOR_ERR_CUDA;
+    std::vector<double> mhz;
+    for (int b = 0; b < blocks; ++b)
+        if (h[2 * b + 1] > 0) mhz.push_back(1e3 * (double)h[2 * b] / (double)h[2 * b + 1]);
+    if (mhz.empty()) return VOLDOR_ERR_INTERNAL;
+    std::nth_element(mhz.begin(), mhz.begin() + mhz.size() / 2, mhz.end());
+    const double f = mhz[mhz.size() / 2];                      // MHz
+    const double results = (double)blocks * threads * (double)kProbeChains * iters;
+    *results_per_sm_clock = results / ((double)ms * 1e-3 * f * 1e6 * sms);
+    if (sm_mhz) *sm_mhz = f;
     return VOLDOR_OK;
 }
 

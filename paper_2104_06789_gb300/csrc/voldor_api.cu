@@ -753,7 +753,7 @@ voldor_status voldor_enable_timing(voldor_ctx* c, int on)
     return VOLDOR_OK;
 }
 
-voldor_status voldor_get_score_times(voldor_ctx* c, float* ms, long long* pairs, int max, int* count)
+voldor_status voldor_get_score_times(voldor_ctx* c, float* ms, long long* pairs, long long* hyps, int max, int* count)
 {
     if (!c || !count || (max > 0 && !ms)) return VOLDOR_ERR_INVALID_ARG;
     if (c->poisoned) return kCuda;
@@ -761,12 +761,15 @@ voldor_status voldor_get_score_times(voldor_ctx* c, float* ms, long long* pairs,
     *count = c->last_pairs;
     for (int i = 0; i < c->last_pairs && i < max; ++i)
         if (!cuda_ok(c, cudaEventElapsedTime(&ms[i], c->events[2 * i], c->events[2 * i + 1]))) return kCuda;
-    if (pairs) {
+    if (pairs || hyps) {
         const int n = std::min(std::min(c->last_pairs, max), kScoreLogMax);
         std::vector<long long> log((size_t)2 * (n > 0 ? n : 1));
         if (n > 0) {
             if (!cuda_ok(c, cudaMemcpy(log.data(), c->ds.score_log, (size_t)n * 16, cudaMemcpyDeviceToHost))) return kCuda;
-            for (int i = 0; i < n; ++i) pairs[i] = log[2 * i] * log[2 * i + 1];
+            for (int i = 0; i < n; ++i) {
+                if (pairs) pairs[i] = log[2 * i] * log[2 * i + 1];
+                if (hyps) hyps[i] = log[2 * i];
+            }
         }
     }
     return VOLDOR_OK;

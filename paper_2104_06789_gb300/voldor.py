@@ -81,12 +81,12 @@ def lib():
             "voldor_get_buffer": (i, [vp, i, vp, sz]),
             "voldor_set_buffer": (i, [vp, i, vp, sz]),
             "voldor_enable_timing": (i, [vp, i]),
-            "voldor_get_score_times": (i, [vp, P(C.c_float), P(C.c_longlong), i, P(i)]),
+            "voldor_get_score_times": (i, [vp, P(C.c_float), P(C.c_longlong), P(C.c_longlong), i, P(i)]),
             "voldor_kernel_launches": (C.c_longlong, [vp]),
             "voldor_last_error_string": (C.c_char_p, [vp]),
             "voldor_device_bytes": (sz, [vp]),
             "voldor_score_records_noalloc": (i, [vp, i, vp, i, d, d, vp, vp]),
-            "voldor_probe_sfu_rate": (i, [i, P(d)]),
+            "voldor_probe_sfu_rate": (i, [i, P(d), P(d)]),
             "voldor_probe_bounded_wait": (i, [C.c_longlong, P(C.c_longlong)]),
             "voldor_autotune": (i, [vp, P(i), P(i), P(C.c_float)]),
             "voldor_set_score_shape": (i, [vp, i, i]),
@@ -298,16 +298,19 @@ class Window:
     def enable_timing(self, on=True):
         _check(lib().voldor_enable_timing(self._h, int(bool(on))), "voldor_enable_timing", handle=self._h)
 
-    def get_score_times(self, max_n=1024):
-        """(ms per scoring launch, pairs per launch) of the last timed em_step."""
+    def get_score_times(self, max_n=1024, with_hyps=False):
+        """(ms per scoring launch, pairs per launch[, hypotheses per launch])
+        of the last timed em_step."""
         ms = np.zeros(max_n, np.float32)
         pairs = np.zeros(max_n, np.int64)
+        hyps = np.zeros(max_n, np.int64)
         n = C.c_int(0)
         _check(lib().voldor_get_score_times(self._h, ms.ctypes.data_as(C.POINTER(C.c_float)),
-                                            pairs.ctypes.data_as(C.POINTER(C.c_longlong)), max_n, C.byref(n)),
+                                            pairs.ctypes.data_as(C.POINTER(C.c_longlong)),
+                                            hyps.ctypes.data_as(C.POINTER(C.c_longlong)), max_n, C.byref(n)),
                "voldor_get_score_times", handle=self._h)
         m = min(n.value, max_n)
-        return ms[:m], pairs[:m]
+        return (ms[:m], pairs[:m], hyps[:m]) if with_hyps else (ms[:m], pairs[:m])
 
     def kernel_launches(self):
         return int(lib().voldor_kernel_launches(self._h))
@@ -346,6 +349,15 @@ def score_records_noalloc(records, hyps, L, xs_min, xs_max, stream=None):
     [n_hyps, 12]; L: CUDA float64 tensor [n_hyps], written asynchronously on
     `stream`. Allocates no device memory.
     """
+    import torch
+    for name, x, dt, width in (("records", records, torch.float32, 12), ("hyps", hyps, torch.float32, 12),
+                               ("L", L, torch.float64, None)):
+        if not x.is_cuda or x.dtype != dt or not x.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA {dt} tensor")
+        if width is not None and (x.dim() != 2 or x.shape[1] != width):
+            raise ValueError(f"{name} must have shape [n, {width}]")
+    if L.numel() < hyps.shape[0]:
+        raise ValueError("L needs one entry per hypothesis")
     st = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
     _check(lib().voldor_score_records_noalloc(C.c_void_p(records.data_ptr()), int(records.shape[0]),
                                               C.c_void_p(hyps.data_ptr()), int(hyps.shape[0]), float(xs_min),
@@ -353,11 +365,12 @@ def score_records_noalloc(records, hyps, L, xs_min, xs_max, stream=None):
            "voldor_score_records_noalloc")
 
 
-def probe_sfu_rate(op):
-    """SFU results per SM clock of the current GPU: op 0 exp2, 1 log2, 2 rcp."""
-    v = C.c_double(0.0)
-    _check(lib().voldor_probe_sfu_rate(int(op), C.byref(v)), "voldor_probe_sfu_rate")
-    return v.value
+def probe_sfu_rate(op, with_clock=False):
+    """SFU results per SM clock of the current GPU: op 0 exp2, 1 log2, 2 rcp
+    (with_clock: also the SM clock in MHz measured during the probe)."""
+    v, f = C.c_double(0.0), C.c_double(0.0)
+    _check(lib().voldor_probe_sfu_rate(int(op), C.byref(v), C.byref(f)), "voldor_probe_sfu_rate")
+    return (v.value, f.value) if with_clock else v.value
 
 
 def probe_bounded_wait(polls):

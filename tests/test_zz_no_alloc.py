@@ -97,3 +97,28 @@ def test_noalloc_rejects_sizes_beyond_its_limit():
     with pytest.raises(voldor.VoldorError) as e:
         voldor.score_records_noalloc(rec, hyp, L, 1e-12, 1.0)
     assert e.value.status == voldor.ERR_INVALID_ARG
+
+
+def test_noalloc_rejects_misaligned_pointers_and_bad_tensors():
+    """A records pointer off the 16-byte boundary (a tensor sliced by one
+    float) is refused on the host before any device work; the Python wrapper
+    refuses a wrong dtype, width or a short L."""
+    import ctypes
+    torch = pytest.importorskip("torch")
+    from paper_2104_06789_gb300 import build, voldor
+    build.build()
+    flat = torch.zeros(13 * 4, dtype=torch.float32, device="cuda")
+    hyp = torch.zeros((2, 12), dtype=torch.float32, device="cuda")
+    L = torch.zeros(2, dtype=torch.float64, device="cuda")
+    st = voldor.lib().voldor_score_records_noalloc(ctypes.c_void_p(flat.data_ptr() + 4), 4,
+                                                  ctypes.c_void_p(hyp.data_ptr()), 2, ctypes.c_double(1e-12),
+                                                  ctypes.c_double(1.0), ctypes.c_void_p(L.data_ptr()),
+                                                  ctypes.c_void_p(0))
+    assert st == voldor.ERR_INVALID_ARG
+    rec = torch.zeros((4, 12), dtype=torch.float32, device="cuda")
+    for bad in (dict(records=rec.double()), dict(records=rec[:, :9].contiguous()), dict(L=L[:1])):
+        args = dict(records=rec, hyps=hyp, L=L)
+        args.update(bad)
+        with pytest.raises(ValueError):
+            voldor.score_records_noalloc(args["records"], args["hyps"], args["L"], 1e-12, 1.0)
+    torch.cuda.synchronize()
