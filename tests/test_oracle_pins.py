@@ -486,3 +486,118 @@ def test_full_loop_noiseless_fixed_point(oracle_lib):
     assert st == 0
     assert np.abs(ow.poses - poses).max() < 1e-9
     assert np.max(np.abs(ow.theta - depth)) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# MIE sweep: neighbour propagation (Fig. 5, Sec. 5.1)
+# ---------------------------------------------------------------------------
+def _chain_starts(W, H, k):
+    """Pixel indices of the first position of every chain of direction k mod 4
+    ([left to right, top to bottom, right to left, bottom to top])."""
+    d = k % 4
+    if d == 0:
+        return [r * W for r in range(H)]
+    if d == 1:
+        return list(range(W))
+    if d == 2:
+        return [r * W + W - 1 for r in range(H)]
+    return [(H - 1) * W + c for c in range(W)]
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
+def test_mie_sweep_propagates_the_chain_winner(oracle_lib, k):
+    """Only each chain's first pixel starts at the true depth; every other
+    pixel starts wrong, and the depth samples cannot reach the truth (inverse
+    depth range [0.3, 1] excludes 1/5). One sweep must carry the truth down
+    every chain through the neighbour candidate: each later pixel is labelled
+    nbr and holds the true depth exactly, the chain starts keep theirs (prev).
+    Taking the neighbour from the pre-sweep depth, running a chain backwards
+    or dropping the candidate all leave wrong depths behind."""
+    flows, K, poses, depth = fronto_parallel_window(W=24, H=18, T=3)
+    H, W = depth.shape
+    ow = oracle_lib.OracleWindow(flows, K, S=8, inv_depth_min=0.3, inv_depth_max=1.0)
+    ow.poses[:] = poses
+    ow.theta[:] = 2.0
+    starts = _chain_starts(W, H, k)
+    ow.theta.flat[starts] = 5.0
+    q = np.ones((3, H, W))
+    labels = ow.mie_sweep(k, q)
+    expect = np.ones(H * W, dtype=np.uint8)
+    expect[starts] = 0
+    assert np.array_equal(labels.ravel(), expect)
+    assert np.all(ow.theta == 5.0)
+
+
+# ---------------------------------------------------------------------------
+# Pose hypotheses: weights (Eq. 19) and the meanshift seed
+# ---------------------------------------------------------------------------
+def test_hypothesis_weight_is_the_product_of_the_groups_rigidness(oracle_lib):
+    """Each hypothesis carries prod_i W_t(j_i) over the three pixels of its
+    group, with the unsmoothed W of its own frame t (Eq. 19): W is set by hand
+    to distinct values per (t, j), the group's pixels are re-drawn from the
+    frame's valid list, and the product is compared exactly."""
+    flows, K, poses, depth = fronto_parallel_window(W=24, H=18, T=3)
+    ow = oracle_lib.OracleWindow(flows, K, S=96, inv_depth_min=0.05, inv_depth_max=1.0)
+    ow.theta[:] = depth
+    ow.poses[:] = poses
+    rng = np.random.default_rng(19)
+    ow.wmap[:] = rng.uniform(0.05, 1.0, size=ow.wmap.shape)
+    for t in (1, 2, 3):
+        valid = ow.valid_pixels(t)
+        R, tv, wts, grp, slot = ow.collect_hypotheses(1, t)
+        assert len(grp) == 96
+        for h in range(len(grp)):
+            ok, j = ow.draw_group(1, t, int(grp[h]), valid)
+            Wt = ow.wmap[t - 1].ravel()
+            assert ok and wts[h] == Wt[j[0]] * Wt[j[1]] * Wt[j[2]]
+        assert len(np.unique(wts)) > 10
+
+
+def _two_motion_window(W=40, H=30, f=30.0, depth=5.0, split=0.7, tA=(0.05, -0.03), tB=(-1.0, 0.8)):
+    """A fronto-parallel plane whose left `split` of the columns moves with
+    the camera translation tA and whose other columns move as if the camera
+    had translated by tB (a second rigid motion): noiseless P3P groups inside
+    either region return that region's pose exactly."""
+    K = (f, f, (W - 1) / 2.0, (H - 1) / 2.0)
+    flows = np.zeros((1, H, W, 2))
+    cols = int(round(split * W))
+    flows[0, :, :cols] = [f * tA[0] / depth, f * tA[1] / depth]
+    flows[0, :, cols:] = [f * tB[0] / depth, f * tB[1] / depth]
+    TA, TB = np.eye(4), np.eye(4)
+    TA[:2, 3] = tA
+    TB[:2, 3] = tB
+    return flows, K, TA, TB, np.full((H, W), depth), cols
+
+
+def test_meanshift_is_seeded_at_the_best_dense_score(oracle_lib):
+    """Two rigid motions: region A (70 % of the pixels, W = 0.6) moves with the
+    camera pose TA, region B (30 %, W = 1) with TB, their flows 7.7 px apart.
+    By hand: under TA the residual is zero on A and 7.7 px on B; under TB the
+    same residual falls on A. The weighted pixel count puts 0.3 N under the
+    penalty for TA against 0.42 N for TB, and A's small observed flow
+    (0.35 px: a small Fisk scale alpha, Eq. 5) makes each of TB's penalties
+    the larger one, so the dense score's argmax lies in A's cluster. The
+    heaviest hypotheses (Eq. 19: 1 in B, 0.216 in A) lie in B, and a meanshift
+    with a narrow kernel started in B stays in B. So the update must return
+    TA, and only a seed at the argmax of L_h does."""
+    flows, K, TA, TB, depth, cols = _two_motion_window()
+    ow = oracle_lib.OracleWindow(flows, K, S=256, inv_depth_min=0.05, inv_depth_max=1.0,
+                                 sigma_t=1e-8, sigma_r=1e-10)
+    ow.theta[:] = depth
+    ow.poses[0] = TA
+    ow.wmap[0][:, :cols] = 0.6
+    ow.wmap[0][:, cols:] = 1.0
+    R, tv, wts, grp, slot = ow.collect_hypotheses(0, 1)
+    L = ow.score(1, R, tv)
+    near = lambda i, T: np.abs(R[i] - T[:3, :3]).max() < 1e-9 and np.abs(tv[i] - T[:3, 3]).max() < 1e-9
+    best = int(np.argmax(L))
+    heavy = next(i for i in range(len(R)) if near(i, TB))       # B's cluster carries the largest weight
+    assert near(best, TA) and wts[heavy] == wts.max() == 1.0 and wts[best] < wts.max()
+    p6 = np.array([oracle_lib.se3_log(Ri, ti) for Ri, ti in zip(R, tv)])
+    _, x_heavy = oracle_lib.meanshift(p6, wts, heavy, 1e-8, 1e-10, 100, 1e-10)
+    Rh, th = oracle_lib.se3_exp(x_heavy)
+    assert np.abs(th - TB[:3, 3]).max() < 1e-9                  # a wrong seed ends in B
+    st, n, L_o, seed, its = ow.pose_update(0, 1)
+    assert st == 0 and n == 256 and seed == best
+    assert np.abs(L_o - L).max() == 0.0
+    assert np.abs(ow.poses[0] - TA).max() < 1e-9
