@@ -304,7 +304,8 @@ voldor_status voldor_probe_bounded_wait(long long polls, long long* cycles);
  * ------------------------------------------------------------------------- */
 
 /* Autotunes the dense-scoring tile shape of one window: hypotheses per thread
- * (4 or 8, i.e. 1024 or 2048 hypotheses per block) and pixel chunks (1, 2, 4
+ * (2, 4 or 8, i.e. 512, 1024 or 2048 hypotheses per block, 3, 2 or 1 blocks
+ * per SM) and pixel chunks (1, 2, 4
  * or 8 waves of resident blocks), timing each candidate with CUDA events on
  * the window's own frame-1 hypotheses and records. Keeps the fastest;
  * discards captured graphs that used another shape. Overwrites the stage
@@ -312,7 +313,7 @@ voldor_status voldor_probe_bounded_wait(long long polls, long long* cycles);
  * Synchronises. Outputs may be NULL. */
 voldor_status voldor_autotune(voldor_ctx* ctx, int* hyps_per_thread, int* chunks, float* best_ms);
 
-/* Sets the dense-scoring tile shape directly (hyps_per_thread 4 or 8). */
+/* Sets the dense-scoring tile shape directly (hyps_per_thread 2, 4 or 8). */
 voldor_status voldor_set_score_shape(voldor_ctx* ctx, int hyps_per_thread, int chunks);
 
 /* A batch of windows run as one CUDA graph: every window's n_iters

@@ -19,8 +19,9 @@
 // 64-bit register pair and one .f32x2 instruction does both lanes, which
 // halves the issue slots of the FMA-pipe work (the pipe still does 128 lane
 // operations per SM clock: after the SFU it is this kernel's second limit).
-// Each thread carries 2 pairs (4 hypotheses, two 256-thread blocks per SM:
-// the default shape) or 4 pairs (8 hypotheses, one block per SM); the pixel
+// Each thread carries 1 pair (2 hypotheses, three 256-thread blocks per SM:
+// the default shape), 2 pairs (4 hypotheses, two blocks per SM) or 4 pairs
+// (8 hypotheses, one block per SM); the pixel
 // loop is software-pipelined over two consecutive pixels; pixel records are
 // bulk-copied into shared memory tile by tile and expanded there into both
 // lanes; sums are FP32 per 256-pixel tile, then FP64.
@@ -552,7 +553,7 @@ static int num_sms()
 // of the resident blocks of a tile shape.
 int score_chunks_for(int S, int N, int hpt, int waves)
 {
-    const int minb = hpt == 8 ? 1 : 2;
+    const int minb = hpt == 8 ? 1 : (hpt == 4 ? 2 : 3);
     const int tiles = (S + kScoreThreads * hpt - 1) / (kScoreThreads * hpt);
     int chunks = (num_sms() * minb * waves + tiles - 1) / tiles;
     if (chunks > N) chunks = N;
@@ -564,7 +565,8 @@ int score_chunks(int S, int N) { return score_chunks_for(S, N, kScoreDefaultHpt,
 int score_chunks_max(int S, int N)
 {
     const int a = score_chunks_for(S, N, 8, kTuneMaxWaves), b = score_chunks_for(S, N, 4, kTuneMaxWaves);
-    return a > b ? a : b;
+    const int c = score_chunks_for(S, N, 2, kTuneMaxWaves);
+    return std::max(a, std::max(b, c));
 }
 
 template <int SLOTS, int MINB>
@@ -585,6 +587,7 @@ void launch_score(const DevParams& p, const DevState& s, int log_idx, cudaStream
 {
     const int li = log_idx < kScoreLogMax ? log_idx : -1;
     if (s.score_hpt == 4) launch_score_shape<2, 2>(p, s, li, st);
+    else if (s.score_hpt == 2) launch_score_shape<1, 3>(p, s, li, st);
     else launch_score_shape<4, 1>(p, s, li, st);
 }
 

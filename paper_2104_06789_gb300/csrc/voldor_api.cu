@@ -805,9 +805,9 @@ voldor_status voldor_autotune(voldor_ctx* c, int* hpt_out, int* chunks_out, floa
     int best_hpt = saved_hpt, best_chunks = saved_chunks;
     float best = 1e30f;
     bool ok = true;
-    const int hpts[2] = {8, 4};
+    const int hpts[3] = {8, 4, 2};
     const int waves[4] = {1, 2, 4, kTuneMaxWaves};
-    for (int hi = 0; hi < 2 && ok; ++hi) {
+    for (int hi = 0; hi < 3 && ok; ++hi) {
         for (int wi = 0; wi < 4 && ok; ++wi) {
             c->ds.score_hpt = hpts[hi];
             c->ds.n_chunks = score_chunks_for(c->params.hyps_per_frame, c->N, hpts[hi], waves[wi]);
@@ -840,7 +840,7 @@ voldor_status voldor_autotune(voldor_ctx* c, int* hpt_out, int* chunks_out, floa
 
 voldor_status voldor_set_score_shape(voldor_ctx* c, int hpt, int chunks)
 {
-    if (!c || (hpt != 4 && hpt != 8) || chunks < 1) return VOLDOR_ERR_INVALID_ARG;
+    if (!c || (hpt != 2 && hpt != 4 && hpt != 8) || chunks < 1) return VOLDOR_ERR_INVALID_ARG;
     if (chunks > score_chunks_max(c->params.hyps_per_frame, c->N)) return VOLDOR_ERR_INVALID_ARG;
     if (c->poisoned) return kCuda;
     if (hpt != c->ds.score_hpt || chunks != c->ds.n_chunks) {

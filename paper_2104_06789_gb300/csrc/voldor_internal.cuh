@@ -16,8 +16,8 @@ constexpr int kMaxT = 16;
 constexpr int kMaxSols = 4;            // P3P has at most four solutions
 constexpr int kScoreThreads = 256;     // dense scoring block
 constexpr int kScoreHypsPerThread = 8;   // hypotheses per thread of the allocation-free scoring (ILP)
-constexpr int kScoreDefaultHpt = 4;      // a window's dense-scoring shape until autotuned: 4 hypotheses
-constexpr int kScoreDefaultWaves = 8;    // per thread, two blocks per SM, pixel chunks for 8 waves
+constexpr int kScoreDefaultHpt = 2;      // a window's dense-scoring shape until autotuned: 2 hypotheses
+constexpr int kScoreDefaultWaves = 8;    // per thread, three blocks per SM, pixel chunks for 8 waves
 constexpr int kScoreBlocksPerSM = 1;
 constexpr int kScoreHypsPerBlock = kScoreThreads * kScoreHypsPerThread;
 constexpr int kMeanshiftCtas = 8;      // thread-block cluster of the meanshift
@@ -103,7 +103,7 @@ struct DevState {
     float* fb_fwd;            // [T][H][W] forward messages
     long long* score_log;     // [kScoreLogMax][2] (n_hyp, n_pix) of timed scoring launches
     int n_chunks;             // dense scoring pixel chunks
-    int score_hpt;            // dense scoring hypotheses per thread (4 or 8)
+    int score_hpt;            // dense scoring hypotheses per thread (2, 4 or 8)
 };
 
 // ---------------------------------------------------------------------------

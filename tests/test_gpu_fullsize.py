@@ -1,13 +1,14 @@
 """Parity at the benchmark's full size and launch configuration: the
 1242x375, T = 8 driving window with FP16 flows, S = 8192 hypotheses per frame
-(the dense scoring's default shape -- 4 hypotheses per thread, two blocks per
+(the dense scoring's default shape -- 2 hypotheses per thread, three blocks per
 SM -- and pixel-chunk count, as bench.py times it), teacher-forced as the small-window tests are.
 
 - dense scores: sampled hypotheses recomputed by the oracle over all 465,750
   pixels, 1e-5 relative; one launch with a full last tile (8192 hypotheses:
-  eight 1024-hypothesis tiles) and two whose last tile is partial (6844: 700
-  hypotheses on six of the block's eight warps; 6400: 256 hypotheses scored by
-  four teams of two warps, each on a quarter of every pixel tile);
+  sixteen 512-hypothesis tiles) and two whose last tile is partial (6844: 188
+  hypotheses, three groups of 64 scored by two teams of three warps; 6400: 256
+  hypotheses scored by two teams of four warps, each team on half of every
+  pixel tile);
 - per-pixel log-likelihoods (unsmoothed rigidness) at every (t, j): 1e-5
   relative;
 - smoothed rigidness (forward-backward) at every (t, j): 2e-5 absolute;

@@ -67,6 +67,27 @@ def test_dense_scores(vd, oracle_lib, scene, t, n):
     assert rel.max() < 1e-5, rel.max()
 
 
+# every dense-scoring shape the autotuner can pick (2, 4 or 8 hypotheses per
+# thread: 3, 2 or 1 blocks per SM), with ragged pixel-chunk counts and a
+# partial last hypothesis tile
+@pytest.mark.parametrize("hpt,chunks,n", [(2, 7, 700), (2, 13, 1100), (4, 7, 1100), (8, 5, 2100)])
+def test_dense_scores_every_shape(vd, oracle_lib, scene, hpt, chunks, n):
+    w = scene
+    t = 2
+    rng = np.random.default_rng(60 + hpt + n)
+    depth, rig = f32_state(rng, w)
+    g = _gpu_window(vd, w, S=max(256, n))
+    g.set_score_shape(hpt, chunks)
+    g.set_state(poses=w.poses, depth=depth, rigidness=rig, iteration=0)
+    ow = oracle_window(oracle_lib, w, w.flows.astype(np.float32).astype(np.float64), 256, depth, rig, w.poses)
+    R, tv = f32_hypotheses(rng, w.poses[t - 1][:3, :3], w.poses[t - 1][:3, 3], n)
+    L_gpu = g.score_hypotheses(t, R, tv)
+    L_ref = ow.score(t, R, tv)
+    rel = np.abs(L_gpu - L_ref) / np.abs(L_ref)
+    assert rel.max() < 1e-5, rel.max()
+    g.destroy()
+
+
 # tiny images (108 and 231 pixels): the pixel chunks hold one or a few
 # records, so pixel tiles of a single pixel (the pipelined pixel loop's first
 # and last stage only) and warp teams with an empty share of a tile occur
