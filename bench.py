@@ -65,6 +65,8 @@ def parse_args():
                     help="flow residual model (Gaussian: the ablation variant)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched (config 4) and learned-vs-plain (config 5) measurements of the default line")
     ap.add_argument("--batch", type=int, default=0,
                     help="run the batched workload instead: this many windows of mixed size and T in one graph")
     ap.add_argument("--learned", type=int, default=0,
@@ -562,6 +564,10 @@ def run_ours(args):
     err = None
     if world == 1 and not args.no_cpu:
         err = error_vs_oracle(win, w, flows16, params, variant_overrides(args))
+    batch = learned_cmp = None
+    if world == 1 and not args.no_extra and (args.criterion, args.residual) == ("mie", "fisk"):
+        batch = batch_summary(args.iters)
+        learned_cmp = learned_summary(args.iters)
 
     cfg = config_dict(w, args, world)
     if hyps_scored is not None:
@@ -570,7 +576,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": cfg, "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_parallel": cpu_par,
-            "e2e": e2e, "error_vs_oracle": err, "gpu_launches": int(launches), "clocks": clocks}
+            "e2e": e2e, "error_vs_oracle": err, "gpu_launches": int(launches), "clocks": clocks,
+            "batch": batch, "learned_vs_plain": learned_cmp}
     print(json.dumps(line), flush=True)
     win.destroy()
     if dist is not None:
@@ -700,6 +707,97 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
     for g, _, _ in wins:
         g.destroy()
+
+
+def batch_summary(iters, warmup=2, steps=3, n=64, S=4096):
+    """Config 4 inside the default run: n windows of the mixed workload
+    (batch_workload) at a fixed S per frame, each window's dense-scoring tile
+    shape autotuned, in one CUDA graph; windows/s from the median batch wall
+    time, per-window latency p50/p99 from the graph's own events, and the
+    same windows one after another (em_step each) beside it."""
+    import torch
+
+    from paper_2104_06789_gb300 import voldor
+    wl = batch_workload(n)
+    stream = torch.cuda.Stream()
+    wins, shapes = [], {}
+    for i, (b, T) in enumerate(wl):
+        flows = np.ascontiguousarray(b.flows[:T].astype(np.float16))
+        p = voldor.default_params(hyps_per_frame=S, inv_depth_min=b.inv_depth_range[0],
+                                  inv_depth_max=b.inv_depth_range[1], window_id=i)
+        g = voldor.Window(flows, b.K, p)
+        g.bootstrap(b.poses[0])
+        hpt, ch, _ = g.autotune()
+        shapes[f"{hpt}x{ch}"] = shapes.get(f"{hpt}x{ch}", 0) + 1
+        wins.append((g, b, T))
+    batch = voldor.Batch([g for g, _, _ in wins], iters)
+    lat, walls = [], []
+    for rep in range(warmup + steps):
+        for g, b, _ in wins:
+            g.bootstrap(b.poses[0])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        l = batch.run(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rep >= warmup:
+            lat.extend(l.tolist())
+            walls.append(e0.elapsed_time(e1))
+    batch.destroy()
+    seq = []
+    for _ in range(2):
+        for g, b, _ in wins:
+            g.bootstrap(b.poses[0])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for g, _, _ in wins:
+            g.em_step(iters)
+        torch.cuda.synchronize()
+        seq.append((time.perf_counter() - t0) * 1e3)
+    errs = []
+    for g, b, T in wins:
+        P, _, _ = g.get_pose_depth_rigidness(depth=False, rigidness=False)
+        errs.append(float(np.mean(np.linalg.norm(P[:, :3, 3] - b.poses[:T, :3, 3], axis=1))))
+        g.destroy()
+    wall = float(np.median(walls))
+    units = sum(b.W * b.H * T * iters for _, b, T in wins)
+    return {"workload": f"{n} windows, resolutions uniform over 320x240 / 640x480 / 1242x375, T uniform in [3, 8]",
+            "hyps_per_frame": S, "tile_shape": "autotuned per window", "shapes": shapes, "em_iters": iters,
+            "windows_per_s": n / (wall / 1e3), "ms_per_batch": wall,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "mpixel_frame_per_s": units / (wall / 1e3) / 1e6,
+            "sequential_ms": float(np.median(seq)), "speedup_vs_sequential": float(np.median(seq)) / wall,
+            "median_translation_error_m": float(np.median(errs))}
+
+
+WEIGHTS = os.path.join(ROOT, "paper_2104_06789_gb300", "weights", "proposal_handheld_1242x375_T8.npy")
+
+
+def learned_summary(iters, heldout=16, S=4096):
+    """The metric's second half inside the default run: the proposal network
+    (weights trained on 2000 handheld windows at 1242x375, T = 8 by
+    `bench.py --learned 2000`), evaluated on held-out windows: iterations and
+    wall time (bootstrap + EM iterations, CUDA events) until the median pose
+    error reaches the plain EM's after `iters` iterations (within 1 %)."""
+    from paper_2104_06789_gb300 import learned, voldor
+    if not os.path.exists(WEIGHTS):
+        return {"unavailable": "trained weights not found"}
+    net = voldor.Net(learned.SCENE["T"], np.load(WEIGHTS))
+    held = learned.build_dataset([learned.HELDOUT_SEED0 + i for i in range(heldout)], S=S, label_iters=0,
+                                 workers=max(1, min(heldout, (os.cpu_count() or 2) - 1)))
+    res = learned.compare(net, held, S=S, max_iters=iters + 1, plain_iters=iters)
+    net.destroy()
+    out = {"workload": f"{heldout} held-out handheld windows at 1242x375 f=718 T=8 (scene seeds "
+                       f"{learned.HELDOUT_SEED0}..{learned.HELDOUT_SEED0 + heldout - 1})",
+           "hyps_per_frame": S, "target_median_err_m": res["median_target_err_m"],
+           "plain": {"iters": iters, "ms": res["plain_ms"]}, "iteration_ms": res["iteration_ms"]}
+    for m, name in (("learned_w", "learned_rigidness_prior"), ("learned", "learned_depth_and_rigidness")):
+        k, ms = res[f"{m}_median_iters_to_target"], res[f"{m}_median_ms"]
+        out[name] = {"iters": k, "ms": ms, "speedup": (res["plain_ms"] / ms) if ms else None,
+                     "median_err_m": res[f"{m}_median_err_m"]}
+    out["plain"]["median_err_m"] = res["plain_median_err_m"]
+    return out
 
 
 def measured_peaks():

@@ -8,54 +8,71 @@
 // with another kernel's, and fused FP64 multiply-adds cut the FP64
 // instructions of the geometry (this GPU's FP64 rate is a small fraction of
 // its FP32 rate).
+#include "df32.cuh"
 #include "voldor_internal.cuh"
 
 namespace vd {
 
 // ---------------------------------------------------------------------------
 // Pose preparation of frame t: one record per pixel whose pi_{t-1} is valid,
-// compacted in pixel order. The count pass computes each pixel's point in
-// camera t-1, P = C_{t-1} theta K^-1 [x y 1] (FP64), its reciprocal depth and
-// pi_{t-1}, stores them (SoA, pix_geo[6][N]) and counts the valid pixels per
-// block, and its last block to finish scans the counts into block offsets;
-// the write pass reads them back (valid iff P_z > 0 and pi_{t-1} inside the
-// image, the same test on the same values), samples the flow at pi_{t-1}
-// bilinearly (FP64) and writes the records at its block's offset.
+// compacted in pixel order. Both passes compute each pixel's point in camera
+// t-1, P = C_{t-1} theta K^-1 [x y 1], and pi_{t-1} in df32 (float-float on
+// the FP32 pipe, ~44 bits: the validity test 0 <= pi_{t-1} <= size - 1 and
+// the bilinear sample position are those of an FP64 computation but within
+// ~1e-11 px). The count pass counts the valid pixels per block and stores
+// per-warp ballots of them, and its last block to finish scans the counts
+// into block offsets; the write pass recomputes the same values, samples the
+// flow at pi_{t-1} bilinearly (df32) and writes the records at its block's
+// offset.
 // ---------------------------------------------------------------------------
-__global__ void k_prep_count(DevParams p, DevState s, int t)
+struct PrepGeo {
+    DF Px, Py, Pz, u, v;
+    bool valid;
+};
+
+__device__ __forceinline__ void load_cum_df(const DevState& s, int t, DF* C)
 {
-    __shared__ double C[12];
-    if (threadIdx.x < 12) C[threadIdx.x] = s.cum[12 * (t - 1) + threadIdx.x];
+    if (threadIdx.x < 12) C[threadIdx.x] = df_of(s.cum[12 * (t - 1) + threadIdx.x]);
     __syncthreads();
+}
+
+__device__ __forceinline__ PrepGeo prep_geometry(const DevParams& p, const DF* C, int t, int j, float th)
+{
+    const int x = j % p.W, y = j / p.W;
+    const DF fx{p.kdf[0], p.kdf[1]}, fy{p.kdf[2], p.kdf[3]}, cx{p.kdf[4], p.kdf[5]}, cy{p.kdf[6], p.kdf[7]};
+    const DF ifx{p.kdf[8], p.kdf[9]}, ify{p.kdf[10], p.kdf[11]};
+    PrepGeo g;
+    const float xf = small_int_to_float(x), yf = small_int_to_float(y);
+    const DF X = df_mul(df_mul(df_add(df_neg(cx), xf), ifx), th);
+    const DF Y = df_mul(df_mul(df_add(df_neg(cy), yf), ify), th);
+    const DF Z = df_of(th);
+    g.u = df_of(xf);
+    g.v = df_of(yf);
+    if (t == 1) {
+        g.Px = X; g.Py = Y; g.Pz = Z;
+    } else {
+        g.Px = df_add(df_add(df_mul(C[0], X), df_mul(C[1], Y)), df_add(df_mul(C[2], Z), C[3]));
+        g.Py = df_add(df_add(df_mul(C[4], X), df_mul(C[5], Y)), df_add(df_mul(C[6], Z), C[7]));
+        g.Pz = df_add(df_add(df_mul(C[8], X), df_mul(C[9], Y)), df_add(df_mul(C[10], Z), C[11]));
+    }
+    g.valid = df_gt0(g.Pz);
+    if (g.valid && t > 1) {
+        const DF iz = df_div(df_of(1.f), g.Pz);
+        g.u = df_add(df_mul(df_mul(fx, g.Px), iz), cx);
+        g.v = df_add(df_mul(df_mul(fy, g.Py), iz), cy);
+    }
+    g.valid = g.valid && df_ge(g.u, 0.f) && df_le(g.u, small_int_to_float(p.W - 1)) && df_ge(g.v, 0.f) &&
+              df_le(g.v, small_int_to_float(p.H - 1));
+    return g;
+}
+
+__global__ void __launch_bounds__(kPixThreads) k_prep_count(DevParams p, DevState s, int t)
+{
+    __shared__ DF C[12];
+    load_cum_df(s, t, C);
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     bool valid = false;
-    if (j < p.N) {
-        const int x = j % p.W, y = j / p.W;
-        const double th = (double)s.theta[j];
-        const double dx = ((double)x - p.cxd) * p.inv_fxd, dy = ((double)y - p.cyd) * p.inv_fyd;
-        double Px = th * dx, Py = th * dy, Pz = th, u = (double)x, v = (double)y, iz = 0.0;
-        if (t > 1) {
-            const double X = Px, Y = Py, Z = Pz;
-            Px = C[0] * X + C[1] * Y + C[2] * Z + C[3];
-            Py = C[4] * X + C[5] * Y + C[6] * Z + C[7];
-            Pz = C[8] * X + C[9] * Y + C[10] * Z + C[11];
-        }
-        if (Pz > 0.0) {
-            iz = rcp64(Pz);
-            if (t > 1) {
-                u = p.fxd * Px * iz + p.cxd;
-                v = p.fyd * Py * iz + p.cyd;
-            }
-        }
-        valid = Pz > 0.0 && u >= 0.0 && u <= (double)(p.W - 1) && v >= 0.0 && v <= (double)(p.H - 1);
-        const size_t N = (size_t)p.N;
-        s.pix_geo[j] = Px;
-        s.pix_geo[N + j] = Py;
-        s.pix_geo[2 * N + j] = Pz;
-        s.pix_geo[3 * N + j] = u;
-        s.pix_geo[4 * N + j] = v;
-        s.pix_geo[5 * N + j] = iz;
-    }
+    if (j < p.N) valid = prep_geometry(p, C, t, j, s.theta[j]).valid;
     // per-warp ballots of the valid pixels: with the block offsets they map
     // the i-th valid pixel (pixel order) to its index for the minimal groups
     const unsigned bal = __ballot_sync(0xffffffffu, valid);
@@ -103,51 +120,51 @@ __global__ void k_prep_count(DevParams p, DevState s, int t)
     }
 }
 
-__global__ void k_prep_write(DevParams p, DevState s, int t)
+__global__ void __launch_bounds__(kPixThreads) k_prep_write(DevParams p, DevState s, int t)
 {
+    __shared__ DF C[12];
     __shared__ int warp_sum[kPixThreads / 32];
+    load_cum_df(s, t, C);
     const int base = s.pix_block_count[blockIdx.x];      // this block's offset (set by the count pass)
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const size_t N = (size_t)p.N;
-    bool valid = false;
-    double Px = 0.0, Py = 0.0, iz = 0.0, u = 0.0, v = 0.0;
-    if (j < p.N) {
-        Px = s.pix_geo[j];
-        Py = s.pix_geo[N + j];
-        const double Pz = s.pix_geo[2 * N + j];
-        u = s.pix_geo[3 * N + j];
-        v = s.pix_geo[4 * N + j];
-        iz = s.pix_geo[5 * N + j];
-        valid = Pz > 0.0 && u >= 0.0 && u <= (double)(p.W - 1) && v >= 0.0 && v <= (double)(p.H - 1);
-    }
-    const unsigned bal = __ballot_sync(0xffffffffu, valid);
+    PrepGeo g;
+    g.valid = false;
+    if (j < p.N) g = prep_geometry(p, C, t, j, s.theta[j]);
+    const unsigned bal = __ballot_sync(0xffffffffu, g.valid);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
     if (lane == 0) warp_sum[warp] = __popc(bal);
     __syncthreads();
     int rank = __popc(bal & ((1u << lane) - 1u));
     for (int w = 0; w < warp; ++w) rank += warp_sum[w];
-    if (valid) {
-        const int x0 = min((int)floor(u), p.W - 2), y0 = min((int)floor(v), p.H - 2);
-        const double ax = u - x0, ay = v - y0;
+    if (g.valid) {
+        const int x0 = min(df_floor(g.u), p.W - 2), y0 = min(df_floor(g.v), p.H - 2);
+        const DF ax = df_add(g.u, -small_int_to_float(x0)), ay = df_add(g.v, -small_int_to_float(y0));
         const size_t fb = (size_t)(t - 1) * N + (size_t)y0 * p.W + x0;
         const float2 f00 = load_flow(s.flows, p.flow_f16, fb), f10 = load_flow(s.flows, p.flow_f16, fb + 1);
         const float2 f01 = load_flow(s.flows, p.flow_f16, fb + p.W);
         const float2 f11 = load_flow(s.flows, p.flow_f16, fb + p.W + 1);
-        const double w00 = (1.0 - ax) * (1.0 - ay), w10 = ax * (1.0 - ay), w01 = (1.0 - ax) * ay, w11 = ax * ay;
-        const double fu = w00 * f00.x + w10 * f10.x + w01 * f01.x + w11 * f11.x;
-        const double fv = w00 * f00.y + w10 * f10.y + w01 * f01.y + w11 * f11.y;
-        const float n = sqrtf((float)(fu * fu + fv * fv));
+        const DF gu0 = df_add(df_mul(df_two_sum(f10.x, -f00.x), ax), f00.x);
+        const DF gu1 = df_add(df_mul(df_two_sum(f11.x, -f01.x), ax), f01.x);
+        const DF gv0 = df_add(df_mul(df_two_sum(f10.y, -f00.y), ax), f00.y);
+        const DF gv1 = df_add(df_mul(df_two_sum(f11.y, -f01.y), ax), f01.y);
+        const DF fud = df_add(gu0, df_mul(df_sub(gu1, gu0), ay));
+        const DF fvd = df_add(gv0, df_mul(df_sub(gv1, gv0), ay));
+        const DF ifx{p.kdf[8], p.kdf[9]};
+        const float fu = df_to_float(fud), fv = df_to_float(fvd);
+        const float ut = df_to_float(df_mul(fud, ifx)), vt = df_to_float(df_mul(fvd, ifx));
+        const DF iz = df_div(df_of(1.f), g.Pz);
+        const float n = sqrtf(fmaf(fu, fu, fv * fv));
+        const float fx2 = df_to_float(df_mul(DF{p.kdf[0], p.kdf[1]}, DF{p.kdf[0], p.kdf[1]}));
         PixRec r;
-        r.a = make_float4((float)(Px * iz), (float)(p.fy_over_fx_d * Py * iz), (float)iz, (float)(fu * p.inv_fxd));
+        r.a = make_float4(df_to_float(df_mul(g.Px, iz)), df_to_float(df_mul(df_mul(g.Py, iz), p.fy_over_fx)),
+                          df_to_float(iz), ut);
         if (p.residual == VOLDOR_RESIDUAL_GAUSSIAN) {
             const GaussConst gc = gauss_const(p, n);
-            r.b = make_float4((float)(fv * p.inv_fxd), (float)(p.fxd * p.fxd) * gc.inv_alpha, -gc.x_mu * gc.inv_alpha,
-                              0.f);
+            r.b = make_float4(vt, fx2 * gc.inv_alpha, -gc.x_mu * gc.inv_alpha, 0.f);
         } else {
             const FiskConst fc = fisk_const(p, n);
-            r.b = make_float4((float)(fv * p.inv_fxd), fc.beta, fc.beta * (p.log2_fx2 - fc.log2_alpha),
-                              (float)(p.fxd * p.fxd) * fc.mu_over_beta);
+            r.b = make_float4(vt, fc.beta, fc.beta * (p.log2_fx2 - fc.log2_alpha), fx2 * fc.mu_over_beta);
         }
         r.c = make_float4(s.wmap[(size_t)(t - 1) * N + j], 0.f, 0.f, 0.f);
         s.pix[base + rank] = r;
@@ -174,55 +191,71 @@ void launch_pose_prep(const DevParams& p, const DevState& s, int t, cudaStream_t
 
 // Emissions rho/(rho+mu) of every (t, j) at the current depth (E-step input)
 // or, written into W, the unsmoothed rigidness update: per (t, j) the rigid
-// flow and residual in FP64 and the likelihood in FP32 (neg_ell); log(1/2)
-// where the model takes rho := mu (pi_{t-1} invalid or the point behind camera
-// t). The point is carried from frame to frame: the point in camera
-// t (T_t applied to the point in camera t-1) and its projection pi_t are the
-// next frame's point in camera (t+1)-1 and pi_{(t+1)-1}, since C_t X =
-// T_t (C_{t-1} X), so each frame transforms and projects once (FP64).
-__global__ void k_emissions(DevParams p, DevState s, float* out)
+// flow and residual in df32 (float-float, on the FP32 pipe) and the
+// likelihood in FP32 (neg_ell); log(1/2) where the model takes rho := mu
+// (pi_{t-1} invalid or the point behind camera t). The point is carried from
+// frame to frame: the point in camera t (T_t applied to the point in camera
+// t-1) and its projection pi_t are the next frame's point in camera (t+1)-1
+// and pi_{(t+1)-1}, since C_t X = T_t (C_{t-1} X), so each frame transforms
+// and projects once. The residual xi - v_ob (tenths of a pixel) is the
+// difference of quantities of up to hundreds of pixels: the sample position,
+// the bilinear flow (in lerp form, with df32 fractions) and the rigid flow
+// are all kept in df32 and only the residual is rounded to FP32.
+__global__ void __launch_bounds__(kPixThreads) k_emissions(DevParams p, DevState s, float* out)
 {
-    __shared__ FramesD f;
-    load_frames(p, s, f);
+    __shared__ DF Tdf[kMaxT][12];
+    for (int i = threadIdx.x; i < p.T * 12; i += blockDim.x) Tdf[i / 12][i % 12] = df_of(s.poses[i]);
+    __syncthreads();
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= p.N) return;
     const int x = j % p.W, y = j / p.W;
-    const double th = (double)s.theta[j];
-    const double dx = ((double)x - p.cxd) * p.inv_fxd, dy = ((double)y - p.cyd) * p.inv_fyd;
-    double Px = th * dx, Py = th * dy, Pz = th;     // the point in camera t-1 (camera 0 for t = 1)
-    double u = (double)x, v = (double)y;            // pi_{t-1}
-    bool front = th > 0.0;                          // P_z > 0 and (u, v) defined
+    const DF fx{p.kdf[0], p.kdf[1]}, fy{p.kdf[2], p.kdf[3]}, cx{p.kdf[4], p.kdf[5]}, cy{p.kdf[6], p.kdf[7]};
+    const DF ifx{p.kdf[8], p.kdf[9]}, ify{p.kdf[10], p.kdf[11]};
+    const float th = s.theta[j];
+    // the point in camera t-1 (camera 0 for t = 1) and pi_{t-1}
+    const float xf = small_int_to_float(x), yf = small_int_to_float(y);
+    DF Px = df_mul(df_mul(df_add(df_neg(cx), xf), ifx), th);
+    DF Py = df_mul(df_mul(df_add(df_neg(cy), yf), ify), th);
+    DF Pz = df_of(th);
+    DF u = df_of(xf), v = df_of(yf);
+    bool front = th > 0.f;                          // P_z > 0 and (u, v) defined
+    const float Wm1 = small_int_to_float(p.W - 1), Hm1 = small_int_to_float(p.H - 1);
     for (int t = 1; t <= p.T; ++t) {
         float ell = -0.69314718055994531f;          // rho := mu
-        double fu = 0.0, fv = 0.0;
-        const bool valid_prev =
-            front && u >= 0.0 && u <= (double)(p.W - 1) && v >= 0.0 && v <= (double)(p.H - 1);
+        DF fu = df_of(0.f), fv = df_of(0.f);
+        const bool valid_prev = front && df_ge(u, 0.f) && df_le(u, Wm1) && df_ge(v, 0.f) && df_le(v, Hm1);
         if (valid_prev) {
-            const int x0 = min((int)floor(u), p.W - 2), y0 = min((int)floor(v), p.H - 2);
-            const double ax = u - x0, ay = v - y0;
+            const int x0 = min(df_floor(u), p.W - 2), y0 = min(df_floor(v), p.H - 2);
+            const DF ax = df_add(u, -small_int_to_float(x0)), ay = df_add(v, -small_int_to_float(y0));
             const size_t base = (size_t)(t - 1) * p.N + (size_t)y0 * p.W + x0;
             const float2 f00 = load_flow(s.flows, p.flow_f16, base), f10 = load_flow(s.flows, p.flow_f16, base + 1);
             const float2 f01 = load_flow(s.flows, p.flow_f16, base + p.W);
             const float2 f11 = load_flow(s.flows, p.flow_f16, base + p.W + 1);
-            const double w00 = (1.0 - ax) * (1.0 - ay), w10 = ax * (1.0 - ay), w01 = (1.0 - ax) * ay, w11 = ax * ay;
-            fu = w00 * f00.x + w10 * f10.x + w01 * f01.x + w11 * f11.x;
-            fv = w00 * f00.y + w10 * f10.y + w01 * f01.y + w11 * f11.y;
+            // f00 + ax (f10 - f00), f01 + ax (f11 - f01), then the same in y
+            const DF gu0 = df_add(df_mul(df_two_sum(f10.x, -f00.x), ax), f00.x);
+            const DF gu1 = df_add(df_mul(df_two_sum(f11.x, -f01.x), ax), f01.x);
+            const DF gv0 = df_add(df_mul(df_two_sum(f10.y, -f00.y), ax), f00.y);
+            const DF gv1 = df_add(df_mul(df_two_sum(f11.y, -f01.y), ax), f01.y);
+            fu = df_add(gu0, df_mul(df_sub(gu1, gu0), ay));
+            fv = df_add(gv0, df_mul(df_sub(gv1, gv0), ay));
         }
-        const double* Tt = f.Tt[t - 1];
-        const double Qx = Tt[0] * Px + Tt[1] * Py + Tt[2] * Pz + Tt[3];
-        const double Qy = Tt[4] * Px + Tt[5] * Py + Tt[6] * Pz + Tt[7];
-        const double Qz = Tt[8] * Px + Tt[9] * Py + Tt[10] * Pz + Tt[11];
-        const bool front_t = Qz > 0.0;
-        double uq = 0.0, vq = 0.0;
+        const DF* Tt = Tdf[t - 1];
+        const DF Qx = df_add(df_add(df_mul(Tt[0], Px), df_mul(Tt[1], Py)), df_add(df_mul(Tt[2], Pz), Tt[3]));
+        const DF Qy = df_add(df_add(df_mul(Tt[4], Px), df_mul(Tt[5], Py)), df_add(df_mul(Tt[6], Pz), Tt[7]));
+        const DF Qz = df_add(df_add(df_mul(Tt[8], Px), df_mul(Tt[9], Py)), df_add(df_mul(Tt[10], Pz), Tt[11]));
+        const bool front_t = df_gt0(Qz);
+        DF uq = df_of(0.f), vq = df_of(0.f);
         if (front_t) {
-            const double iq = rcp64(Qz);
-            uq = p.fxd * Qx * iq + p.cxd;
-            vq = p.fyd * Qy * iq + p.cyd;
+            const DF iq = df_div(df_of(1.f), Qz);
+            uq = df_add(df_mul(df_mul(fx, Qx), iq), cx);
+            vq = df_add(df_mul(df_mul(fy, Qy), iq), cy);
         }
         if (valid_prev && front_t) {
-            const double ru = (uq - u) - fu, rv = (vq - v) - fv;
-            const float xs = (float)fmin(fmax(ru * ru + rv * rv, (double)p.x_min), (double)p.x_max);
-            ell = -neg_ell(p, xs, sqrtf((float)(fu * fu + fv * fv)), false);
+            const float ru = df_to_float(df_sub(df_sub(uq, u), fu));
+            const float rv = df_to_float(df_sub(df_sub(vq, v), fv));
+            const float xs = fminf(fmaxf(fmaf(ru, ru, rv * rv), p.x_min), p.x_max);
+            const float fuf = df_to_float(fu), fvf = df_to_float(fv);
+            ell = -neg_ell(p, xs, sqrtf(fmaf(fuf, fuf, fvf * fvf)), false);
         }
         out[(size_t)(t - 1) * p.N + j] = expf(ell);
         Px = Qx; Py = Qy; Pz = Qz;

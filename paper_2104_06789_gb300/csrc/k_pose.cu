@@ -282,19 +282,34 @@ __device__ int valid_pixel_at(const DevState& s, int nb, int i)
     return -1;
 }
 
-// Point in camera t-1 and bearing of the flow target of valid pixel j, from
-// the FP64 geometry the count pass stored (pix_geo) and an FP64 bilinear
-// sample of X_t at pi_{t-1}.
-__device__ bool group_point(const DevParams& p, const DevState& s, int t, int j, double* P, double* bear)
+// Point in camera t-1 and bearing of the flow target of valid pixel j, in
+// FP64 (P3P's inputs): P = C_{t-1} theta K^-1 [x y 1], pi_{t-1} its
+// projection (the pixel itself for t = 1), the flow X_t sampled bilinearly at
+// pi_{t-1}. False if the pixel has no correspondence after all (the pose
+// preparation lists it by the same test in float-float; the two can differ
+// only within ~1e-11 px of the image border).
+__device__ bool group_point(const DevParams& p, const DevState& s, const double* C, int t, int j, double* P,
+                            double* bear)
 {
-    const size_t N = (size_t)p.N;
-    P[0] = s.pix_geo[j];
-    P[1] = s.pix_geo[N + j];
-    P[2] = s.pix_geo[2 * N + j];
-    const double u = s.pix_geo[3 * N + j], v = s.pix_geo[4 * N + j];
+    const int x = j % p.W, y = j / p.W;
+    const double th = (double)s.theta[j];
+    const double d[3] = {((double)x - p.cxd) / p.fxd, ((double)y - p.cyd) / p.fyd, 1.0};
+    double u, v;
+    if (t == 1) {
+        P[0] = th * d[0]; P[1] = th * d[1]; P[2] = th;
+        u = x; v = y;
+        if (!(P[2] > 0.0)) return false;
+    } else {
+        const double X = th * d[0], Y = th * d[1], Z = th;
+        for (int r = 0; r < 3; ++r) P[r] = C[r * 4 + 0] * X + C[r * 4 + 1] * Y + C[r * 4 + 2] * Z + C[r * 4 + 3];
+        if (!(P[2] > 0.0)) return false;
+        u = p.fxd * P[0] / P[2] + p.cxd;
+        v = p.fyd * P[1] / P[2] + p.cyd;
+    }
+    if (!(u >= 0.0 && u <= (double)(p.W - 1) && v >= 0.0 && v <= (double)(p.H - 1))) return false;
     const int x0 = min((int)floor(u), p.W - 2), y0 = min((int)floor(v), p.H - 2);
     const double ax = u - x0, ay = v - y0;
-    const size_t base = (size_t)(t - 1) * N + (size_t)y0 * p.W + x0;
+    const size_t base = (size_t)(t - 1) * p.N + (size_t)y0 * p.W + x0;
     const float2 f00 = load_flow(s.flows, p.flow_f16, base), f10 = load_flow(s.flows, p.flow_f16, base + 1);
     const float2 f01 = load_flow(s.flows, p.flow_f16, base + p.W), f11 = load_flow(s.flows, p.flow_f16, base + p.W + 1);
     const double w00 = (1 - ax) * (1 - ay), w10 = ax * (1 - ay), w01 = (1 - ax) * ay, w11 = ax * ay;
@@ -317,9 +332,10 @@ __device__ int solve_group(const DevParams& p, const DevState& s, int t, int k, 
     if (idx[0] == idx[1] || idx[0] == idx[2] || idx[1] == idx[2]) return 0;
     double P[3][3], b[3][3];
     double weight = 1.0;
+    const double* C = s.cum + 12 * (t - 1);
     for (int i = 0; i < 3; ++i) {
         const int j = valid_pixel_at(s, nb, idx[i]);
-        if (j < 0 || !group_point(p, s, t, j, P[i], b[i])) return 0;
+        if (j < 0 || !group_point(p, s, C, t, j, P[i], b[i])) return 0;
         weight *= (double)s.wmap[(size_t)(t - 1) * p.N + j];
     }
     *weight_out = weight;

@@ -106,6 +106,12 @@ DevParams make_dev_params(const voldor_ctx& c)
     d.inv_fxd = 1.0 / c.K.fx; d.inv_fyd = 1.0 / c.K.fy; d.fy_over_fx_d = c.K.fy / c.K.fx;
     d.sigma_t = p.sigma_t; d.sigma_r = p.sigma_r; d.ms_tol = p.ms_tol;
     d.seed = p.seed; d.window_id = p.window_id;
+    const double kv[6] = {c.K.fx, c.K.fy, c.K.cx, c.K.cy, 1.0 / c.K.fx, 1.0 / c.K.fy};
+    for (int i = 0; i < 6; ++i) {
+        const float h = (float)kv[i];
+        d.kdf[2 * i] = h;
+        d.kdf[2 * i + 1] = (float)(kv[i] - (double)h);
+    }
     return d;
 }
 
@@ -137,7 +143,6 @@ size_t layout(voldor_ctx& c, char* base)
     c.flag_dev = (int*)take(4);
     s.pix = (PixRec*)take(N * sizeof(PixRec));
     s.pix_block_count = (int*)take(((N + kPixThreads - 1) / kPixThreads) * 4);
-    s.pix_geo = (double*)take(6 * N * sizeof(double));
     s.prep_done = (unsigned*)take(4);
     s.pix_count = (int*)take(4);
     s.pix_vmask = (unsigned*)take(((N + kPixThreads - 1) / kPixThreads) * (kPixThreads / 32) * 4);

@@ -47,6 +47,9 @@ struct DevParams {
     double inv_fxd, inv_fyd, fy_over_fx_d;
     double sigma_t, sigma_r, ms_tol;
     uint64_t seed, window_id;
+    // fx, fy, cx, cy, 1/fx, 1/fy as float-float pairs (hi, lo) for the df32
+    // geometry passes
+    float kdf[12];
 };
 
 // Per-pixel record of a frame for dense scoring (three float4 = 48 B).
@@ -75,7 +78,6 @@ struct DevState {
     PixRec* pix;              // [N] compacted valid pixels of the current frame
     int* pix_block_count;     // [ceil(N / kPixThreads)] valid pixels per block, then the blocks' record offsets
     unsigned* prep_done;      // [1] blocks of the count pass finished (0 between launches)
-    double* pix_geo;          // [6][N] P_x, P_y, P_z in camera t-1, pi_{t-1} (u, v), 1 / P_z of the frame being prepared
     int* pix_count;           // [1]
     unsigned* pix_vmask;      // [ceil(N / kPixThreads) * kPixThreads / 32] per-warp ballots of the valid pixels
     // P3P
