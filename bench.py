@@ -43,12 +43,14 @@ ALGO_MUFU_MIX = {("mie", "fisk"): (1, 2, 1), ("mle", "fisk"): (1, 2, 1),
                  ("mie", "gaussian"): (1, 1, 1), ("mle", "gaussian"): (1, 0, 0)}
 NOMINAL_SMS, NOMINAL_MAX_MHZ = 152, 2070.0
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per k_score launch,
-# mean over the 40 launches of one driving-window step (S = 8192, 5 iterations),
-# from one ncu capture of the current default MIE / Fisk kernel (cold L2 at each
-# launch: 13.59 MB read, < 1 KB written; the first frame's launch reads 22.82 MB
-# against 22.75 MB of records and hypotheses). The other variants and hypothesis
-# counts were not captured: their traffic is reported as null.
-SCORE_TRAFFIC_BYTES = {("mie", "fisk", 8192): 13.59e6}
+# mean over the 40 launches of one driving-window step (S = 8192 on every frame,
+# 5 iterations), from one ncu capture of the current default MIE / Fisk kernel
+# (2 hypotheses per thread, three blocks per SM), over two complete iterations:
+# 14.19 MB read, < 1 KB written, against 48 B per valid record + 48 B per
+# hypothesis of algorithmic bytes (13.8 MB at the mean of ~280k valid pixels
+# per frame; frame 1: 23.32 MB read for 22.75 MB). The other
+# variants and hypothesis counts were not captured: their traffic is null.
+SCORE_TRAFFIC_BYTES = {("mie", "fisk", 8192): 14.19e6}
 
 
 def parse_args():
@@ -566,7 +568,7 @@ def run_ours(args):
         err = error_vs_oracle(win, w, flows16, params, variant_overrides(args))
     batch = learned_cmp = None
     if world == 1 and not args.no_extra and (args.criterion, args.residual) == ("mie", "fisk"):
-        batch = batch_summary(args.iters)
+        batch = batch_summary(args.iters, pair_rate)
         learned_cmp = learned_summary(args.iters)
 
     cfg = config_dict(w, args, world)
@@ -709,12 +711,16 @@ def run_batch(args):
         g.destroy()
 
 
-def batch_summary(iters, warmup=2, steps=3, n=64, S=4096):
+def batch_summary(iters, pair_rate, warmup=2, steps=3, n=64, S=4096):
     """Config 4 inside the default run: n windows of the mixed workload
     (batch_workload) at a fixed S per frame, each window's dense-scoring tile
     shape autotuned, in one CUDA graph; windows/s from the median batch wall
     time, per-window latency p50/p99 from the graph's own events, and the
-    same windows one after another (em_step each) beside it."""
+    same windows one after another (em_step each) beside it. The batch's
+    dense-scoring pairs (hypotheses x valid pixels, read from every window's
+    scoring log) over `pair_rate` (the driving window's measured pairs/s)
+    give the time the scoring alone needs at full-GPU occupancy: a lower
+    bound for any batching of these windows with this scoring kernel."""
     import torch
 
     from paper_2104_06789_gb300 import voldor
@@ -755,6 +761,13 @@ def batch_summary(iters, warmup=2, steps=3, n=64, S=4096):
             g.em_step(iters)
         torch.cuda.synchronize()
         seq.append((time.perf_counter() - t0) * 1e3)
+    pairs = 0.0
+    for g, b, _ in wins:
+        g.enable_timing(True)
+        g.bootstrap(b.poses[0])
+        g.em_step(iters)
+        pairs += float(g.get_score_times()[1].sum())
+        g.enable_timing(False)
     errs = []
     for g, b, T in wins:
         P, _, _ = g.get_pose_depth_rigidness(depth=False, rigidness=False)
@@ -768,6 +781,8 @@ def batch_summary(iters, warmup=2, steps=3, n=64, S=4096):
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "mpixel_frame_per_s": units / (wall / 1e3) / 1e6,
             "sequential_ms": float(np.median(seq)), "speedup_vs_sequential": float(np.median(seq)) / wall,
+            "scoring_pairs": pairs, "scoring_bound_ms": pairs / pair_rate * 1e3 if pair_rate else None,
+            "scoring_bound_frac": (pairs / pair_rate * 1e3) / wall if pair_rate else None,
             "median_translation_error_m": float(np.median(errs))}
 
 
