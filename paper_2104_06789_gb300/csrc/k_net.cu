@@ -4,8 +4,8 @@
 // rigidness logit used in place of the triangulation bootstrap. BF16
 // activations and weights, FP32 accumulation: the convolutions of the forward
 // pass and of the input gradient on tcgen05 (TMEM accumulators, TMA row
-// loads), the weight gradient on mma.sync m16n8k16 with ldmatrix operand
-// loads; FP32 Adam on master weights.
+// loads), the weight gradient on tcgen05 too (operands transposed into
+// shared memory with ldmatrix / stmatrix); FP32 Adam on master weights.
 //
 // Input: the flows of each frame divided by that frame's mean flow magnitude
 // (the network sees the shape of the flow field, not its overall size).
@@ -38,8 +38,6 @@ typedef __nv_bfloat16 bf16;
 
 constexpr int kNetLayers = 6;
 constexpr int kNetWidth = 32;
-constexpr int kTileW = 32, kTileH = 4;          // block tile: 4 rows of 32 pixels, one row per warp
-constexpr int kHaloW = kTileW + 2, kHaloH = kTileH + 2;
 constexpr int kAlignBins = 2048;                // histogram bins per level of the median search
 constexpr float kAlignRange = 16.f;             // first level covers log-ratios in [-16, 16)
 
@@ -48,51 +46,10 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p)
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
-}
-
 __device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3)
 {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
                  : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
-}
-
-__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t& r0, uint32_t& r1)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(addr));
-}
-
-__device__ __forceinline__ void ldsm_x2_t(uint32_t addr, uint32_t& r0, uint32_t& r1)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(addr));
-}
-
-__device__ __forceinline__ void mma_bf16(float* c, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
-                                         uint32_t b1)
-{
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                 "{%0,%1,%2,%3};"
-                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// Loads the (kTileH + 2) x (kTileW + 2) input halo of a tile, CIN channels per
-// pixel (global channel stride cin_g), zero outside the image.
-template <int CIN, int CS>
-__device__ __forceinline__ void load_halo(bf16* s, const bf16* in, int cin_g, int H, int W, int b, int x0, int y0)
-{
-    constexpr int VEC = CIN / 8;   // 16-byte vectors per pixel
-    for (int i = threadIdx.x; i < kHaloH * kHaloW * VEC; i += blockDim.x) {
-        const int q = i / VEC, v = i % VEC;
-        const int gy = y0 + q / kHaloW - 1, gx = x0 + q % kHaloW - 1;
-        uint4 val = make_uint4(0, 0, 0, 0);
-        if (gy >= 0 && gy < H && gx >= 0 && gx < W)
-            val = *reinterpret_cast<const uint4*>(in + (((size_t)b * H + gy) * W + gx) * cin_g + v * 8);
-        *reinterpret_cast<uint4*>(s + q * CS + v * 8) = val;
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -514,13 +471,7 @@ static bool launch_conv_tc(const ConvArgs& a, cudaStream_t st)
     return true;
 }
 
-// ---------------------------------------------------------------------------
-// Weight gradient: dw[co][tap][ci] += sum_p dout[p][co] in[p + off(tap)][ci],
-// db[co] += sum_p dout[p][co]. GEMM with M = output channels (MT m16 tiles),
-// N = CIN, K = pixels of `tiles` consecutive spatial tiles per block; warp w
-// owns taps w, w+4, w+8. Operands come from shared memory with transposing
-// ldmatrix (both are stored pixel-major). FP32 atomics into dw at the end.
-// ---------------------------------------------------------------------------
+// Arguments of the weight-gradient kernel below.
 struct WgradArgs {
     const bf16* in;
     int cin_g;
@@ -530,96 +481,234 @@ struct WgradArgs {
     float* db;              // [n_out]
     int n_out, cin_real;
     int H, W, B;
-    int tiles_x, tiles_y;
-    int tiles_per_block;
+    int* err;               // set to 1 if a bounded wait expired
 };
 
-template <int CIN, int MT>
-__global__ void __launch_bounds__(128) k_conv_wgrad(WgradArgs a)
+// ---------------------------------------------------------------------------
+// Weight gradient on the fifth-generation tensor cores:
+// dw[co][tap][ci] += sum_p dout[p][co] in[p + off(tap)][ci] and
+// db[co] += sum_p dout[p][co], as one GEMM per layer: D[m][n] =
+// sum_k A[m][k] B[n][k] with
+// m = tap * CIN + ci (the 9 CIN rows of the layer's input, shifted by the
+// tap), n = output channel, k = pixel; one extra row of ones (m = 9 CIN)
+// gives the bias gradient sum_p dout[p][n]. Rows are cut into 128-row M tiles
+// (tcgen05.mma M = 128, N = NCO, K = 16, BF16 in, FP32 accumulators in TMEM
+// that persist over all of a CTA's work items).
+//
+// A work item is KP = 64 consecutive output pixels of one image row. Its
+// three input rows (66 pixels each, zero outside the image) and its output
+// gradients are staged pixel-major in shared memory, then transposed 8 x 8 at
+// a time (ldmatrix .trans, then stmatrix) into the K-major, unswizzled
+// core-matrix layout of the two operands: element (m, k) of an M tile at
+// (k / 8) * 2048 + (m / 8) * 128 + (m % 8) * 16 + (k % 8) * 2 bytes, and
+// (n, k) of B at (k / 8) * (NCO / 8) * 128 + (n / 8) * 128 + (n % 8) * 16 +
+// (k % 8) * 2. One thread issues the item's MMAs and commits them to an
+// mbarrier; the next item's pixel-major staging overlaps them, and every
+// thread waits on the commit (bounded) before overwriting the operands. At
+// the end each thread reads its TMEM row (tcgen05.ld) and adds it to the
+// FP32 gradients with atomics.
+// ---------------------------------------------------------------------------
+constexpr int kWgKP = 64;                                 // pixels per work item (K)
+constexpr int kWgThreads = 128;
+
+template <int CIN, int NCO>
+struct WgShape {
+    static constexpr int kRows = 9 * CIN + 1;                           // + the ones row
+    static constexpr int kMT = (kRows + 127) / 128;
+    static constexpr int kInRowBytes = (kWgKP + 2) * CIN * 2;
+    static constexpr int kInBytes = 3 * kInRowBytes;
+    static constexpr int kDoBytes = kWgKP * NCO * 2;
+    static constexpr int kATileBytes = (kWgKP / 8) * 2048;
+    static constexpr int kBLbo = (NCO / 8) * 128;
+    static constexpr int kBBytes = (kWgKP / 8) * kBLbo;
+    static constexpr int kInOff = 0;
+    static constexpr int kDoOff = kInOff + kInBytes;
+    static constexpr int kAOff = (kDoOff + kDoBytes + 1023) / 1024 * 1024;
+    static constexpr int kBOff = kAOff + kMT * kATileBytes;
+    static constexpr int kBarOff = kBOff + kBBytes;
+    static constexpr int kSmemBytes = kBarOff + 32;
+    static constexpr int kTmemCols = kMT * NCO <= 32 ? 32 : (kMT * NCO <= 64 ? 64 : 128);
+    static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NCO >> 3) << 17) |
+                                       ((uint32_t)(128 >> 4) << 24);
+};
+
+__device__ __forceinline__ void stsm_x4(uint32_t addr, uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3)
 {
-    constexpr int CS = CIN + 8;
-    constexpr int OS = MT * 16 + 8;             // dout pixel stride in shared memory
-    constexpr int NT = CIN / 8;
-    __shared__ __align__(16) bf16 in_s[kHaloH * kHaloW * CS];
-    __shared__ __align__(16) bf16 do_s[kTileH * kTileW * OS];
-    __shared__ float db_s[MT * 16];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gid = lane >> 2, tig = lane & 3;
-    float acc[3][MT][NT][4];
+    asm volatile("stmatrix.sync.aligned.m8n8.x4.shared.b16 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(r0), "r"(r1),
+                 "r"(r2), "r"(r3) : "memory");
+}
+
+template <int CIN, int NCO>
+__global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(WgradArgs a)
+{
+    using S = WgShape<CIN, NCO>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const uint32_t sbase = smem_addr(smem);
+    const uint32_t in_s = sbase + S::kInOff, do_s = sbase + S::kDoOff, A_s = sbase + S::kAOff, B_s = sbase + S::kBOff;
+    const uint32_t bar = sbase + S::kBarOff, done = bar + 8;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + S::kBarOff + 16);
+    volatile int& bad = *reinterpret_cast<volatile int*>(smem + S::kBarOff + 20);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int segs = (a.W + kWgKP - 1) / kWgKP;
+    const int n_items = a.B * a.H * segs;
+
+    // constant rows of A in every M tile: the ones row (bias gradient) and zero padding
+    for (int i = tid; i < S::kMT * 128 * kWgKP; i += blockDim.x) {
+        const int m = i / kWgKP, k = i % kWgKP;
+        if (m < 9 * CIN) continue;
+        const int mt = m / 128, mm = m % 128;
+        const uint32_t off = S::kAOff + mt * S::kATileBytes + (k / 8) * 2048 + (mm / 8) * 128 + (mm % 8) * 16 + (k % 8) * 2;
+        *reinterpret_cast<bf16*>(smem + off) = __float2bfloat16_rn(m == 9 * CIN ? 1.f : 0.f);
+    }
+    if (tid == 0) {
+        tc_mbar_init(bar, 1);
+        tc_mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        bad = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                     "r"((uint32_t)S::kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    // an item's input rows and output gradients, loaded into registers one
+    // item ahead (the loads of item i + 1 are in flight while item i is
+    // transposed and multiplied) and stored pixel-major at the top of the loop
+    constexpr int kInVec = 3 * (kWgKP + 2) * (CIN / 8), kDoVec = kWgKP * (NCO / 8);
+    constexpr int kInPer = (kInVec + kWgThreads - 1) / kWgThreads, kDoPer = (kDoVec + kWgThreads - 1) / kWgThreads;
+    uint4 pin[kInPer], pdo[kDoPer];
+    auto fetch = [&](int it) {
+        const int b = it / (a.H * segs), rem = it % (a.H * segs);
+        const int y = rem / segs, x0 = (rem % segs) * kWgKP;
 #pragma unroll
-    for (int ti = 0; ti < 3; ++ti)
-#pragma unroll
-        for (int m = 0; m < MT; ++m)
-#pragma unroll
-            for (int n = 0; n < NT; ++n) acc[ti][m][n][0] = acc[ti][m][n][1] = acc[ti][m][n][2] = acc[ti][m][n][3] = 0.f;
-    if (threadIdx.x < MT * 16) db_s[threadIdx.x] = 0.f;
-    const int total_tiles = a.tiles_x * a.tiles_y * a.B;
-    for (int tt = 0; tt < a.tiles_per_block; ++tt) {
-        const int tile = blockIdx.x * a.tiles_per_block + tt;
-        if (tile >= total_tiles) break;
-        const int b = tile / (a.tiles_x * a.tiles_y);
-        const int rem = tile % (a.tiles_x * a.tiles_y);
-        const int x0 = (rem % a.tiles_x) * kTileW, y0 = (rem / a.tiles_x) * kTileH;
-        __syncthreads();
-        load_halo<CIN, CS>(in_s, a.in, a.cin_g, a.H, a.W, b, x0, y0);
-        for (int i = threadIdx.x; i < kTileH * kTileW * (MT * 2); i += blockDim.x) {
-            const int q = i / (MT * 2), v = i % (MT * 2);
-            const int gy = y0 + q / kTileW, gx = x0 + q % kTileW;
-            uint4 val = make_uint4(0, 0, 0, 0);
-            if (gy < a.H && gx < a.W)
-                val = *reinterpret_cast<const uint4*>(a.dout + (((size_t)b * a.H + gy) * a.W + gx) * a.cout_g + v * 8);
-            *reinterpret_cast<uint4*>(do_s + q * OS + v * 8) = val;
-        }
-        __syncthreads();
-        if (threadIdx.x < a.n_out) {
-            float sdb = 0.f;
-            for (int q = 0; q < kTileH * kTileW; ++q) sdb += __bfloat162float(do_s[q * OS + threadIdx.x]);
-            db_s[threadIdx.x] += sdb;
-        }
-        // K steps: 16 consecutive pixels of one tile row
-        for (int ks = 0; ks < kTileH * kTileW / 16; ++ks) {
-            const int r = ks >> 1, h = ks & 1;
-            uint32_t af[MT][4];
-#pragma unroll
-            for (int m = 0; m < MT; ++m) {
-                const int k = (lane & 7) + ((lane >> 4) << 3);
-                const int moff = ((lane >> 3) & 1) << 3;
-                ldsm_x4_t(smem_addr(do_s + (r * kTileW + h * 16 + k) * OS + m * 16 + moff), af[m][0], af[m][1], af[m][2],
-                          af[m][3]);
+        for (int j = 0; j < kInPer; ++j) {
+            const int i = tid + j * kWgThreads;
+            pin[j] = make_uint4(0, 0, 0, 0);
+            if (i < kInVec) {
+                const int v = i % (CIN / 8), q = i / (CIN / 8);
+                const int ky = q / (kWgKP + 2), xx = q % (kWgKP + 2);
+                const int gy = y + ky - 1, gx = x0 + xx - 1;
+                if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W)
+                    pin[j] = *reinterpret_cast<const uint4*>(a.in + (((size_t)b * a.H + gy) * a.W + gx) * a.cin_g + v * 8);
             }
+        }
 #pragma unroll
-            for (int ti = 0; ti < 3; ++ti) {
-                const int tap = warp + 4 * ti;
-                if (tap >= 9) break;
-                const int ky = tap / 3, kx = tap % 3;
-#pragma unroll
-                for (int n = 0; n < NT; ++n) {
-                    uint32_t b0, b1;
-                    const int k = lane & 15;
-                    ldsm_x2_t(smem_addr(in_s + ((r + ky) * kHaloW + h * 16 + k + kx) * CS + n * 8), b0, b1);
-#pragma unroll
-                    for (int m = 0; m < MT; ++m) mma_bf16(acc[ti][m][n], af[m][0], af[m][1], af[m][2], af[m][3], b0, b1);
+        for (int j = 0; j < kDoPer; ++j) {
+            const int i = tid + j * kWgThreads;
+            pdo[j] = make_uint4(0, 0, 0, 0);
+            if (i < kDoVec) {
+                const int v = i % (NCO / 8), px = i / (NCO / 8), gx = x0 + px;
+                if (gx < a.W && v * 8 < a.n_out) {
+                    pdo[j] = *reinterpret_cast<const uint4*>(a.dout + (((size_t)b * a.H + y) * a.W + gx) * a.cout_g + v * 8);
+                    if (v * 8 + 8 > a.n_out) {                // channels past n_out are zero
+                        bf16* e = reinterpret_cast<bf16*>(&pdo[j]);
+                        for (int c = a.n_out - v * 8; c < 8; ++c) e[c] = __float2bfloat16_rn(0.f);
+                    }
                 }
             }
+        }
+    };
+    if (blockIdx.x < n_items) fetch(blockIdx.x);
+    int local = 0;                                            // items of this CTA so far
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++local) {
+        // pixel-major staging of this item (the operands of the previous item
+        // may still be read by its MMAs; these buffers are not)
+#pragma unroll
+        for (int j = 0; j < kInPer; ++j) {
+            const int i = tid + j * kWgThreads;
+            if (i < kInVec) {
+                const int v = i % (CIN / 8), q = i / (CIN / 8);
+                const int ky = q / (kWgKP + 2), xx = q % (kWgKP + 2);
+                *reinterpret_cast<uint4*>(smem + S::kInOff + ky * S::kInRowBytes + xx * CIN * 2 + v * 16) = pin[j];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kDoPer; ++j) {
+            const int i = tid + j * kWgThreads;
+            if (i < kDoVec) {
+                const int v = i % (NCO / 8), px = i / (NCO / 8);
+                *reinterpret_cast<uint4*>(smem + S::kDoOff + px * NCO * 2 + v * 16) = pdo[j];
+            }
+        }
+        if (it + (int)gridDim.x < n_items) fetch(it + gridDim.x);
+        // the previous item's MMAs have read A and B; a wait that expires sets
+        // `bad`, which every thread reads after the same barrier
+        if (local > 0) tc_wait(bar, (uint32_t)((local - 1) & 1), &bad);
+        __syncthreads();
+        if (bad) break;
+        // 8 x 8 transposes into the K-major operands: A blocks (tap, ci group, k group), then B blocks
+        constexpr int kABlocks = 9 * (CIN / 8) * (kWgKP / 8), kBBlocks = (NCO / 8) * (kWgKP / 8);
+        static_assert((kABlocks + kBBlocks) % 16 == 0, "four x4 transposes per round, one per warp");
+        for (int q0 = warp * 4; q0 < kABlocks + kBBlocks; q0 += 16) {
+            const int blk = q0 + (lane >> 3), r = lane & 7;
+            uint32_t src, dst;
+            if (blk < kABlocks) {
+                const int kg = blk % (kWgKP / 8), g = (blk / (kWgKP / 8)) % (CIN / 8), tap = blk / ((kWgKP / 8) * (CIN / 8));
+                const int ky = tap / 3, kx = tap % 3;
+                const int m = tap * CIN + g * 8 + r, mt = m / 128, mm = m % 128;
+                src = in_s + ky * S::kInRowBytes + (8 * kg + r + kx) * CIN * 2 + g * 16;
+                dst = A_s + mt * S::kATileBytes + kg * 2048 + (mm / 8) * 128 + r * 16;
+            } else {
+                const int bb = blk - kABlocks, kg = bb % (kWgKP / 8), g = bb / (kWgKP / 8);
+                src = do_s + (8 * kg + r) * NCO * 2 + g * 16;
+                dst = B_s + kg * S::kBLbo + g * 128 + r * 16;
+            }
+            // lane l gives row l % 8 of block l / 8: the transposing load, then the
+            // plain store, writes each block's transpose to the destination rows
+            uint32_t r0, r1, r2, r3;
+            ldsm_x4_t(src, r0, r1, r2, r3);
+            stsm_x4(dst, r0, r1, r2, r3);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int mt = 0; mt < S::kMT; ++mt)
+#pragma unroll
+                for (int s16 = 0; s16 < kWgKP / 16; ++s16) {
+                    const uint64_t ad = tc_desc(A_s + mt * S::kATileBytes + s16 * 2 * 2048, 2048, 128);
+                    const uint64_t bd = tc_desc(B_s + s16 * 2 * S::kBLbo, S::kBLbo, 128);
+                    tc_mma(tmem + mt * NCO, ad, bd, S::kIdesc, (local > 0 || s16 > 0) ? 1u : 0u);
+                }
+            tc_commit(bar);
         }
     }
-#pragma unroll
-    for (int ti = 0; ti < 3; ++ti) {
-        const int tap = warp + 4 * ti;
-        if (tap >= 9) break;
-#pragma unroll
-        for (int m = 0; m < MT; ++m)
-#pragma unroll
-            for (int n = 0; n < NT; ++n)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int co = m * 16 + gid + ((e >> 1) << 3);
-                    const int ci = n * 8 + 2 * tig + (e & 1);
-                    if (co < a.n_out && ci < a.cin_real) atomicAdd(a.dw + ((size_t)co * 9 + tap) * a.cin_real + ci, acc[ti][m][n][e]);
-                }
+    if (tid == 0) {
+        tc_commit(done);                                      // arrives once every MMA issued has completed
+        bool drained = false;
+        for (long long i = 0; i < kTcWaitLimit && !drained; ++i) drained = tc_try_wait(done, 0);
+        if (!drained) bad = 1;
     }
     __syncthreads();
-    if (threadIdx.x < a.n_out) atomicAdd(a.db + threadIdx.x, db_s[threadIdx.x]);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!bad && local > 0) {
+#pragma unroll
+        for (int mt = 0; mt < S::kMT; ++mt) {
+            float v[NCO];
+            tc_ld<NCO>(tmem + ((uint32_t)(warp * 32) << 16) + mt * NCO, v);
+            const int m = mt * 128 + warp * 32 + lane;
+            if (m < 9 * CIN) {
+                const int tap = m / CIN, ci = m % CIN;
+                if (ci < a.cin_real)
+                    for (int co = 0; co < a.n_out; ++co) atomicAdd(a.dw + ((size_t)co * 9 + tap) * a.cin_real + ci, v[co]);
+            } else if (m == 9 * CIN) {
+                for (int co = 0; co < a.n_out; ++co) atomicAdd(a.db + co, v[co]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)S::kTmemCols));
+    }
+    if (tid == 0 && bad) atomicExch(a.err, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -975,6 +1064,34 @@ bool forward(voldor_net* n, const void* flows, int f16, int B, int H, int W, cud
     return true;
 }
 
+template <int CIN, int NCO>
+static bool launch_wgrad_tc(const WgradArgs& a, cudaStream_t st)
+{
+    using S = WgShape<CIN, NCO>;
+    static bool attr[kTcMaxDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kTcMaxDevices) return false;
+    int sms = 0;
+    {
+        std::lock_guard<std::mutex> lock(g_tc_mutex);
+        if (!attr[dev]) {
+            if (cudaFuncSetAttribute(k_wgrad_tc<CIN, NCO>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmemBytes) !=
+                cudaSuccess)
+                return false;
+            attr[dev] = true;
+        }
+        if (g_tc_sms[dev] <= 0 &&
+            (cudaDeviceGetAttribute(&g_tc_sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+             g_tc_sms[dev] <= 0))
+            g_tc_sms[dev] = 152;
+        sms = g_tc_sms[dev];
+    }
+    const int items = a.B * a.H * ((a.W + kWgKP - 1) / kWgKP);
+    const int grid = std::min(items, 3 * sms);
+    k_wgrad_tc<CIN, NCO><<<grid, kWgThreads, S::kSmemBytes, st>>>(a);
+    return true;
+}
+
 void wgrad(voldor_net* n, int l, const bf16* in, int cin_g, const bf16* dout, int cout_g, int B, int H, int W, cudaStream_t st)
 {
     WgradArgs a{};
@@ -982,15 +1099,12 @@ void wgrad(voldor_net* n, int l, const bf16* in, int cin_g, const bf16* dout, in
     a.dw = n->grad + n->L.w_off[l]; a.db = n->grad + n->L.b_off[l];
     a.n_out = n->L.cout[l]; a.cin_real = n->L.cin[l];
     a.H = H; a.W = W; a.B = B;
-    a.tiles_x = (W + kTileW - 1) / kTileW; a.tiles_y = (H + kTileH - 1) / kTileH;
-    const int total = a.tiles_x * a.tiles_y * B;
-    a.tiles_per_block = total > 1216 ? (total + 1215) / 1216 : 1;
-    const int blocks = (total + a.tiles_per_block - 1) / a.tiles_per_block;
+    a.err = n->tc_err;
     const int cinp = n->L.cin_pad[l];
-    const int mt = n->L.cout[l] > 16 ? 2 : 1;
-    if (cinp == 16 && mt == 2) k_conv_wgrad<16, 2><<<blocks, 128, 0, st>>>(a);
-    else if (cinp == 32 && mt == 2) k_conv_wgrad<32, 2><<<blocks, 128, 0, st>>>(a);
-    else if (cinp == 32 && mt == 1) k_conv_wgrad<32, 1><<<blocks, 128, 0, st>>>(a);
+    const bool wide = n->L.cout[l] > 16;
+    if (cinp == 16 && wide) launch_wgrad_tc<16, 32>(a, st);
+    else if (cinp == 32 && wide) launch_wgrad_tc<32, 32>(a, st);
+    else if (cinp == 32 && !wide) launch_wgrad_tc<32, 16>(a, st);
 }
 
 // Backward pass after forward(); target [pix][2] (log-depth, rigidness).
