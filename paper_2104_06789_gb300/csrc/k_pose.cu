@@ -90,9 +90,9 @@ __device__ double cubic_max_root(double A, double B, double C)
     return m;
 }
 
-// Real roots of a quartic (ascending coefficients) by Ferrari's method, each
-// polished by Newton steps on the quartic. Returns the count (<= 4).
-__device__ int quartic_real_roots(const double* a, double* roots)
+// Real root candidates of a quartic (ascending coefficients) by Ferrari's
+// method, before polishing, shifted back by -b/4. Returns the count (<= 4).
+__device__ int quartic_candidates(const double* a, double* roots)
 {
     double amax = 0.0;
     for (int i = 0; i < 4; ++i) amax = fmax(amax, fabs(a[i]));
@@ -122,19 +122,22 @@ __device__ int quartic_real_roots(const double* a, double* roots)
             if (z2 >= 0.0) { y[n++] = sqrt(z2); y[n++] = -sqrt(z2); }
         }
     }
-    for (int i = 0; i < n; ++i) {
-        double x = y[i] - 0.25 * b;
-        for (int it = 0; it < 3; ++it) {
-            const double f = horner4(a, x);
-            const double df = ((4.0 * a[4] * x + 3.0 * a[3]) * x + 2.0 * a[2]) * x + a[1];
-            if (!(fabs(df) > 0.0)) break;
-            const double xn = x - f / df;
-            if (!(fabs(horner4(a, xn)) < fabs(f))) break;
-            x = xn;
-        }
-        roots[i] = x;
-    }
+    for (int i = 0; i < n; ++i) roots[i] = y[i] - 0.25 * b;
     return n;
+}
+
+// One candidate root polished by Newton steps on the quartic.
+__device__ double polish_quartic_root(const double* a, double x)
+{
+    for (int it = 0; it < 3; ++it) {
+        const double f = horner4(a, x);
+        const double df = ((4.0 * a[4] * x + 3.0 * a[3]) * x + 2.0 * a[2]) * x + a[1];
+        if (!(fabs(df) > 0.0)) break;
+        const double xn = x - f / df;
+        if (!(fabs(horner4(a, xn)) < fabs(f))) break;
+        x = xn;
+    }
+    return x;
 }
 
 // Frame spanned by a triangle: f1 along q3 - q1, f3 normal, f2 = f3 x f1
@@ -169,83 +172,94 @@ struct P3PSol {
     double Rt[12];
 };
 
-__device__ int p3p_solve(const double P[3][3], const double b[3][3], P3PSol* out)
+// The quartic of a P3P instance and the quantities its roots are mapped back
+// with. False for a degenerate triangle.
+struct P3PSetup {
+    double d12, d13, d23, c12, c13, c23;
+    double N[3], D[2], Q[5];
+};
+
+__device__ bool p3p_setup(const double P[3][3], const double b[3][3], P3PSetup& q)
 {
     double e12[3], e13[3], e23[3];
     for (int i = 0; i < 3; ++i) { e12[i] = P[0][i] - P[1][i]; e13[i] = P[0][i] - P[2][i]; e23[i] = P[1][i] - P[2][i]; }
     const double d12 = d3dot(e12, e12), d13 = d3dot(e13, e13), d23 = d3dot(e23, e23);
-    if (!(d12 > 0.0 && d13 > 0.0 && d23 > 0.0)) return 0;
+    if (!(d12 > 0.0 && d13 > 0.0 && d23 > 0.0)) return false;
     const double c12 = d3dot(b[0], b[1]), c13 = d3dot(b[0], b[2]), c23 = d3dot(b[1], b[2]);
     const double K2 = d13 / d12;
     const double g[3] = {K2 - 1.0, -2.0 * K2 * c12, K2};
-    const double N[3] = {(d23 - d13) * g[0] + d23, (d23 - d13) * g[1], (d23 - d13) * g[2] - d13};
-    const double D[2] = {2.0 * d13 * c13, -2.0 * d13 * c23};
-    double Q[5] = {0, 0, 0, 0, 0};
+    q.d12 = d12; q.d13 = d13; q.d23 = d23; q.c12 = c12; q.c13 = c13; q.c23 = c23;
+    q.N[0] = (d23 - d13) * g[0] + d23; q.N[1] = (d23 - d13) * g[1]; q.N[2] = (d23 - d13) * g[2] - d13;
+    q.D[0] = 2.0 * d13 * c13; q.D[1] = -2.0 * d13 * c23;
+    const double* N = q.N;
+    const double* D = q.D;
+    for (int i = 0; i < 5; ++i) q.Q[i] = 0.0;
     for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) Q[i + j] += N[i] * N[j];
+        for (int j = 0; j < 3; ++j) q.Q[i + j] += N[i] * N[j];
     for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 2; ++j) Q[i + j] -= 2.0 * c13 * N[i] * D[j];
+        for (int j = 0; j < 2; ++j) q.Q[i + j] -= 2.0 * c13 * N[i] * D[j];
     const double DD[3] = {D[0] * D[0], 2.0 * D[0] * D[1], D[1] * D[1]};
     for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) Q[i + j] -= g[i] * DD[j];
-    double us[4];
-    const int nr = quartic_real_roots(Q, us);
-    int n = 0;
-    for (int r = 0; r < nr; ++r) {
-        const double u = us[r];
-        if (!(u > 0.0)) continue;
-        const double Du = D[0] + D[1] * u;
-        if (Du == 0.0) continue;
-        const double v = (N[0] + (N[1] + N[2] * u) * u) / Du;
-        const double q1 = 1.0 + u * u - 2.0 * c12 * u;
-        if (!(q1 > 0.0)) continue;
-        double s[3];
-        s[0] = sqrt(d12 / q1);
-        s[1] = u * s[0];
-        s[2] = v * s[0];
-        if (!(s[0] > 0.0 && s[1] > 0.0 && s[2] > 0.0) || !isfinite(s[2])) continue;
-        for (int it = 0; it < 5; ++it) {
-            const double F[3] = {s[0] * s[0] + s[1] * s[1] - 2.0 * c12 * s[0] * s[1] - d12,
-                                 s[0] * s[0] + s[2] * s[2] - 2.0 * c13 * s[0] * s[2] - d13,
-                                 s[1] * s[1] + s[2] * s[2] - 2.0 * c23 * s[1] * s[2] - d23};
-            const double J[9] = {2.0 * (s[0] - c12 * s[1]), 2.0 * (s[1] - c12 * s[0]), 0.0,
-                                 2.0 * (s[0] - c13 * s[2]), 0.0, 2.0 * (s[2] - c13 * s[0]),
-                                 0.0, 2.0 * (s[1] - c23 * s[2]), 2.0 * (s[2] - c23 * s[1])};
-            double ds[3];
-            if (!solve3x3(J, F, ds)) break;
-            const double nsv[3] = {s[0] - ds[0], s[1] - ds[1], s[2] - ds[2]};
-            const double G0 = nsv[0] * nsv[0] + nsv[1] * nsv[1] - 2.0 * c12 * nsv[0] * nsv[1] - d12;
-            const double G1 = nsv[0] * nsv[0] + nsv[2] * nsv[2] - 2.0 * c13 * nsv[0] * nsv[2] - d13;
-            const double G2 = nsv[1] * nsv[1] + nsv[2] * nsv[2] - 2.0 * c23 * nsv[1] * nsv[2] - d23;
-            if (!(fabs(G0) + fabs(G1) + fabs(G2) < fabs(F[0]) + fabs(F[1]) + fabs(F[2]))) break;
-            s[0] = nsv[0]; s[1] = nsv[1]; s[2] = nsv[2];
-        }
-        if (!(s[0] > 0.0 && s[1] > 0.0 && s[2] > 0.0)) continue;
-        double Qc[3][3];
-        for (int i = 0; i < 3; ++i)
-            for (int c = 0; c < 3; ++c) Qc[i][c] = s[i] * b[i][c];
-        double Fw[9], Fc[9];
-        if (!tri_frame(P[0], P[1], P[2], Fw) || !tri_frame(Qc[0], Qc[1], Qc[2], Fc)) continue;
-        P3PSol sol;
-        sol.s1 = s[0];
-        double cw[3], cc[3];
-        for (int c = 0; c < 3; ++c) {
-            cw[c] = (P[0][c] + P[1][c] + P[2][c]) / 3.0;
-            cc[c] = (Qc[0][c] + Qc[1][c] + Qc[2][c]) / 3.0;
-        }
-        for (int r0 = 0; r0 < 3; ++r0) {
-            for (int c = 0; c < 3; ++c)
-                sol.Rt[r0 * 4 + c] = Fc[r0 * 3 + 0] * Fw[c * 3 + 0] + Fc[r0 * 3 + 1] * Fw[c * 3 + 1] + Fc[r0 * 3 + 2] * Fw[c * 3 + 2];
-        }
-        for (int r0 = 0; r0 < 3; ++r0)
-            sol.Rt[r0 * 4 + 3] = cc[r0] - (sol.Rt[r0 * 4 + 0] * cw[0] + sol.Rt[r0 * 4 + 1] * cw[1] + sol.Rt[r0 * 4 + 2] * cw[2]);
-        // insertion by s1
-        int pos = n;
-        while (pos > 0 && out[pos - 1].s1 > sol.s1) { out[pos] = out[pos - 1]; --pos; }
-        out[pos] = sol;
-        ++n;
+        for (int j = 0; j < 3; ++j) q.Q[i + j] -= g[i] * DD[j];
+    return true;
+}
+
+// The pose of one polished root u of the quartic: v, the distances s_i
+// (polished by Newton steps on the three distance equations), then the
+// rotation and translation that map the world triangle onto the camera
+// triangle. False if the root gives no solution with all s_i > 0.
+__device__ bool p3p_from_root(const double P[3][3], const double b[3][3], const P3PSetup& q, const double u,
+                              P3PSol& sol)
+{
+    const double d12 = q.d12, d13 = q.d13, d23 = q.d23, c12 = q.c12, c13 = q.c13, c23 = q.c23;
+    const double* N = q.N;
+    const double* D = q.D;
+    if (!(u > 0.0)) return false;
+    const double Du = D[0] + D[1] * u;
+    if (Du == 0.0) return false;
+    const double v = (N[0] + (N[1] + N[2] * u) * u) / Du;
+    const double q1 = 1.0 + u * u - 2.0 * c12 * u;
+    if (!(q1 > 0.0)) return false;
+    double s[3];
+    s[0] = sqrt(d12 / q1);
+    s[1] = u * s[0];
+    s[2] = v * s[0];
+    if (!(s[0] > 0.0 && s[1] > 0.0 && s[2] > 0.0) || !isfinite(s[2])) return false;
+    for (int it = 0; it < 5; ++it) {
+        const double F[3] = {s[0] * s[0] + s[1] * s[1] - 2.0 * c12 * s[0] * s[1] - d12,
+                             s[0] * s[0] + s[2] * s[2] - 2.0 * c13 * s[0] * s[2] - d13,
+                             s[1] * s[1] + s[2] * s[2] - 2.0 * c23 * s[1] * s[2] - d23};
+        const double J[9] = {2.0 * (s[0] - c12 * s[1]), 2.0 * (s[1] - c12 * s[0]), 0.0,
+                             2.0 * (s[0] - c13 * s[2]), 0.0, 2.0 * (s[2] - c13 * s[0]),
+                             0.0, 2.0 * (s[1] - c23 * s[2]), 2.0 * (s[2] - c23 * s[1])};
+        double ds[3];
+        if (!solve3x3(J, F, ds)) break;
+        const double nsv[3] = {s[0] - ds[0], s[1] - ds[1], s[2] - ds[2]};
+        const double G0 = nsv[0] * nsv[0] + nsv[1] * nsv[1] - 2.0 * c12 * nsv[0] * nsv[1] - d12;
+        const double G1 = nsv[0] * nsv[0] + nsv[2] * nsv[2] - 2.0 * c13 * nsv[0] * nsv[2] - d13;
+        const double G2 = nsv[1] * nsv[1] + nsv[2] * nsv[2] - 2.0 * c23 * nsv[1] * nsv[2] - d23;
+        if (!(fabs(G0) + fabs(G1) + fabs(G2) < fabs(F[0]) + fabs(F[1]) + fabs(F[2]))) break;
+        s[0] = nsv[0]; s[1] = nsv[1]; s[2] = nsv[2];
     }
-    return n;
+    if (!(s[0] > 0.0 && s[1] > 0.0 && s[2] > 0.0)) return false;
+    double Qc[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int c = 0; c < 3; ++c) Qc[i][c] = s[i] * b[i][c];
+    double Fw[9], Fc[9];
+    if (!tri_frame(P[0], P[1], P[2], Fw) || !tri_frame(Qc[0], Qc[1], Qc[2], Fc)) return false;
+    sol.s1 = s[0];
+    double cw[3], cc[3];
+    for (int c = 0; c < 3; ++c) {
+        cw[c] = (P[0][c] + P[1][c] + P[2][c]) / 3.0;
+        cc[c] = (Qc[0][c] + Qc[1][c] + Qc[2][c]) / 3.0;
+    }
+    for (int r0 = 0; r0 < 3; ++r0) {
+        for (int c = 0; c < 3; ++c)
+            sol.Rt[r0 * 4 + c] = Fc[r0 * 3 + 0] * Fw[c * 3 + 0] + Fc[r0 * 3 + 1] * Fw[c * 3 + 1] + Fc[r0 * 3 + 2] * Fw[c * 3 + 2];
+    }
+    for (int r0 = 0; r0 < 3; ++r0)
+        sol.Rt[r0 * 4 + 3] = cc[r0] - (sol.Rt[r0 * 4 + 0] * cw[0] + sol.Rt[r0 * 4 + 1] * cw[1] + sol.Rt[r0 * 4 + 2] * cw[2]);
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -321,45 +335,37 @@ __device__ bool group_point(const DevParams& p, const DevState& s, const double*
     return d3unit(bear);
 }
 
-// Solves group g; returns its solution count and weight.
-__device__ int solve_group(const DevParams& p, const DevState& s, int t, int k, int g, int n_valid, int nb,
-                           P3PSol* sols, double* weight_out)
-{
-    *weight_out = 0.0;
-    const U64x4 r = philox4x64_10((uint64_t)g, (uint64_t)t, (uint64_t)k, (uint64_t)kStreamPose, p.seed, p.window_id);
-    int idx[3];
-    for (int i = 0; i < 3; ++i) idx[i] = (int)__umul64hi(r.v[i], (uint64_t)n_valid);
-    if (idx[0] == idx[1] || idx[0] == idx[2] || idx[1] == idx[2]) return 0;
-    double P[3][3], b[3][3];
-    double weight = 1.0;
-    const double* C = s.cum + 12 * (t - 1);
-    for (int i = 0; i < 3; ++i) {
-        const int j = valid_pixel_at(s, nb, idx[i]);
-        if (j < 0 || !group_point(p, s, C, t, j, P[i], b[i])) return 0;
-        weight *= (double)s.wmap[(size_t)(t - 1) * p.N + j];
-    }
-    *weight_out = weight;
-    return p3p_solve(P, b, sols);
-}
+// Groups are solved in order in chunks of kP3PChunk (one warp each: four
+// lanes per group, one per root of its quartic) until the frame has S
+// solutions or the budget of G groups is spent. A warp claims chunks with an
+// atomic counter, so the claimed chunks are always 0, 1, ..., c - 1, and every
+// claimed chunk is solved: the solved groups form a prefix of the group order.
+// After its first chunk a warp claims another only while the solutions found
+// so far plus the chunks still in flight, at the yield observed so far, fall
+// short of S; the warp that completes the last chunk in flight sees exact
+// counts, so the run ends with at least S solutions in the prefix (or the
+// whole budget solved), and the first S solutions in group order are the same
+// whatever the timing.
+//
+// Within a quad, lanes 0-2 compute the FP64 point and bearing of the group's
+// pixels 0-2 and share them by shuffles; every lane forms the quartic and its
+// Ferrari candidates, lane r polishes candidate r and turns it into a pose,
+// and each solution's slot is its rank by s1 among the quad's solutions
+// (ties by root order): the group's solutions sorted by s1. A warp's
+// FP64 dependency chain is then the common part and one root, not up to four
+// roots in turn.
+constexpr int kP3PChunk = 8;
 
-// Groups are solved in order in chunks of 32 (one warp each) until the frame
-// has S solutions or the budget of G groups is spent. A warp claims chunks
-// with an atomic counter, so the claimed chunks are always 0, 1, ..., c - 1,
-// and every claimed chunk is solved: the solved groups form a prefix of the
-// group order. After its first chunk a warp claims another only while the
-// solutions found so far plus the chunks still in flight, at the yield
-// observed so far, fall short of S; the warp that completes the last chunk
-// in flight sees exact counts, so the run ends with at least S solutions in
-// the prefix (or the whole budget solved), and the first S solutions in
-// group order are the same whatever the timing.
 __global__ void __launch_bounds__(32) k_p3p_groups(DevParams p, DevState s, int t)
 {
-    const int lane = threadIdx.x;
+    const int lane = threadIdx.x, quad = lane >> 2, r = lane & 3, base = lane & ~3;
+    const unsigned FULL = 0xffffffffu;
     const int n_valid = *s.pix_count;
     if (n_valid < 3) return;                              // every group repeats a pixel
     const int k = *s.iter;
     const int nb = (p.N + kPixThreads - 1) / kPixThreads;
-    const int n_chunks = (p.G + 31) / 32;
+    const int n_chunks = (p.G + kP3PChunk - 1) / kP3PChunk;
+    const double* C = s.cum + 12 * (t - 1);
     bool first = true;
     for (;;) {
         int c = -1;
@@ -374,22 +380,77 @@ __global__ void __launch_bounds__(32) k_p3p_groups(DevParams p, DevState s, int 
             if (claim) c = atomicAdd(s.p3p_claims, 1);
         }
         first = false;
-        c = __shfl_sync(0xffffffffu, c, 0);
+        c = __shfl_sync(FULL, c, 0);
         if (c < 0 || c >= n_chunks) break;
-        const int g = c * 32 + lane;
-        int n = 0;
-        if (g < p.G) {
-            P3PSol sols[kMaxSols];
-            double weight;
-            n = solve_group(p, s, t, k, g, n_valid, nb, sols, &weight);
-            s.grp_count[g] = n;
-            s.grp_weight[g] = weight;
-            double* o = s.grp_sols + (size_t)g * kMaxSols * 12;
-            for (int i = 0; i < n; ++i)
-                for (int q = 0; q < 12; ++q) o[i * 12 + q] = sols[i].Rt[q];
+        const int g = c * kP3PChunk + quad;
+        const bool active = g < p.G;
+        // the group's pixels: j_i = V_t[hi64(r_i n)] (all lanes of the quad draw the same)
+        int idx[3] = {0, 0, 0};
+        bool distinct = false;
+        if (active) {
+            const U64x4 rr = philox4x64_10((uint64_t)g, (uint64_t)t, (uint64_t)k, (uint64_t)kStreamPose, p.seed,
+                                           p.window_id);
+            for (int i = 0; i < 3; ++i) idx[i] = (int)__umul64hi(rr.v[i], (uint64_t)n_valid);
+            distinct = idx[0] != idx[1] && idx[0] != idx[2] && idx[1] != idx[2];
         }
-        int tot = n;
-        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        // lane r < 3: pixel r's point in camera t-1 and bearing (FP64)
+        double Pm[3] = {0.0, 0.0, 0.0}, bm[3] = {0.0, 0.0, 1.0};
+        double wv = 0.0;
+        int ok = 1;
+        if (active && distinct && r < 3) {
+            const int ri = r == 0 ? idx[0] : (r == 1 ? idx[1] : idx[2]);
+            const int j = valid_pixel_at(s, nb, ri);
+            ok = (j >= 0 && group_point(p, s, C, t, j, Pm, bm)) ? 1 : 0;
+            if (ok) wv = (double)s.wmap[(size_t)(t - 1) * p.N + j];
+        }
+        double P[3][3], b[3][3];
+        double weight = 1.0;
+        int okall = 1;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                P[i][q] = __shfl_sync(FULL, Pm[q], base + i);
+                b[i][q] = __shfl_sync(FULL, bm[q], base + i);
+            }
+            weight *= __shfl_sync(FULL, wv, base + i);
+            okall &= __shfl_sync(FULL, ok, base + i);
+        }
+        const bool valid_group = active && distinct && okall;
+        if (!valid_group) weight = 0.0;
+        // the quartic (every lane), then lane r's root
+        P3PSetup qs;
+        int nr = 0;
+        double cand[4] = {0.0, 0.0, 0.0, 0.0};
+        if (valid_group && p3p_setup(P, b, qs)) nr = quartic_candidates(qs.Q, cand);
+        P3PSol sol;
+        sol.s1 = 0.0;
+        bool has = false;
+        if (r < nr) {
+            const double u0 = r == 0 ? cand[0] : (r == 1 ? cand[1] : (r == 2 ? cand[2] : cand[3]));
+            has = p3p_from_root(P, b, qs, polish_quartic_root(qs.Q, u0), sol);
+        }
+        // slot = rank by s1 among the quad's solutions, ties by root order
+        int rank = 0, cnt = 0;
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            const double so = __shfl_sync(FULL, sol.s1, base + o);
+            const int ho = __shfl_sync(FULL, has ? 1 : 0, base + o);
+            cnt += ho;
+            if (has && ho && (so < sol.s1 || (so == sol.s1 && o < r))) ++rank;
+        }
+        if (active) {
+            if (r == 0) {
+                s.grp_count[g] = cnt;
+                s.grp_weight[g] = weight;
+            }
+            if (has) {
+                double* o = s.grp_sols + ((size_t)g * kMaxSols + rank) * 12;
+                for (int q = 0; q < 12; ++q) o[q] = sol.Rt[q];
+            }
+        }
+        int tot = (r == 0) ? cnt : 0;
+        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(FULL, tot, o);
         __threadfence();
         if (lane == 0) atomicAdd(s.p3p_done, (1ull << 32) | (unsigned long long)tot);
     }
@@ -398,8 +459,8 @@ __global__ void __launch_bounds__(32) k_p3p_groups(DevParams p, DevState s, int 
 // Groups solved for the current frame (a prefix of the group order).
 __device__ __forceinline__ int groups_solved(const DevParams& p, const DevState& s)
 {
-    const int n_chunks = (p.G + 31) / 32;
-    return min(min(*s.p3p_claims, n_chunks) * 32, p.G);
+    const int n_chunks = (p.G + kP3PChunk - 1) / kP3PChunk;
+    return min(min(*s.p3p_claims, n_chunks) * kP3PChunk, p.G);
 }
 
 // One warp per block spreads the FP64 solves over the SMs. The first wave
@@ -407,8 +468,8 @@ __device__ __forceinline__ int groups_solved(const DevParams& p, const DevState&
 // (1.4-1.5 solutions per group); further chunks are claimed as needed.
 void launch_p3p_groups(const DevParams& p, const DevState& s, int t, cudaStream_t st)
 {
-    const int n_chunks = (p.G + 31) / 32;
-    const int wave = std::max(1, std::min(n_chunks, (3 * p.S + 127) / 128));
+    const int n_chunks = (p.G + kP3PChunk - 1) / kP3PChunk;
+    const int wave = std::max(1, std::min(n_chunks, (3 * p.S + 4 * kP3PChunk - 1) / (4 * kP3PChunk)));
     k_p3p_groups<<<wave, 32, 0, st>>>(p, s, t);
 }
 
