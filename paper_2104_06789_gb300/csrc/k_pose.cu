@@ -690,6 +690,8 @@ k_meanshift(DevParams p, DevState s, int t)
     __shared__ double part[2][8];
     __shared__ double gath[kMeanshiftCtas * 7];
     __shared__ double xs[8];
+    __shared__ double tot_s[8];
+    __shared__ double dsq[8];
     __shared__ double seedp[6];
     __shared__ double bval[32];
     __shared__ int bidx[32];
@@ -795,20 +797,30 @@ k_meanshift(DevParams p, DevState s, int t)
         if (tid < kMeanshiftCtas * 7)
             gath[tid] = *cluster.map_shared_rank(&part[buf][tid % 7], (unsigned)(tid / 7));
         __syncthreads();
+        // component c of the cluster's sums, added in rank order by thread c
+        // (each FP64 instruction is a long issue on this GPU's FP64 pipe, so
+        // the 7 x 8 additions and the 6 coordinate updates run in parallel,
+        // not in one thread)
+        if (tid < 7) {
+            double v = 0.0;
+            for (unsigned r = 0; r < kMeanshiftCtas; ++r) v += gath[r * 7 + tid];
+            tot_s[tid] = v;
+        }
+        __syncthreads();
+        const bool mass = tot_s[0] > 0.0;
+        if (mass && tid < 6) {
+            const double xn = seedp[tid] + tot_s[1 + tid] * (1.0 / tot_s[0]);
+            const double d = xn - xs[tid];
+            dsq[tid] = d * d;
+            xs[tid] = xn;
+        }
+        __syncthreads();
         if (tid == 0) {
-            double tot[7] = {0, 0, 0, 0, 0, 0, 0};
-            for (unsigned r = 0; r < kMeanshiftCtas; ++r)
-                for (int c = 0; c < 7; ++c) tot[c] += gath[r * 7 + c];
-            if (!(tot[0] > 0.0)) {
+            if (!mass) {
                 flag = (it == 0) ? 2 : 1;
             } else {
                 double step = 0.0;
-                const double inv = 1.0 / tot[0];
-                for (int c = 0; c < 6; ++c) {
-                    const double xn = seedp[c] + tot[1 + c] * inv;
-                    step += (xn - xs[c]) * (xn - xs[c]);
-                    xs[c] = xn;
-                }
+                for (int c = 0; c < 6; ++c) step += dsq[c];
                 step = sqrt(step);
                 flag = (step < p.ms_tol || (step >= prev_step && step < 1e-7)) ? 1 : 0;
                 prev_step = step;

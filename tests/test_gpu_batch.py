@@ -62,7 +62,7 @@ def test_batch_rejects_bad_input(vd):
     g = _make(vd, w, 0)
     with pytest.raises(vd.VoldorError):
         vd.Batch([g, g], 1)
-    p = vd.default_params(hyps_per_frame=64, )
+    p = vd.default_params(hyps_per_frame=64)
     raw = vd.Window(w.flows.astype(np.float32), w.K, p)           # not bootstrapped
     with pytest.raises(vd.VoldorError) as e:
         vd.Batch([g, raw], 1)

@@ -134,7 +134,7 @@ def test_bootstrap_mode_epipolar_equals_the_epipolar_call(vd):
     bootstrap with 512 samples and |t_1| = 1: same poses, depth and state."""
     w = synthetic.driving(seed=3001, W=414, H=125, f=239.3, T=3)
     p = vd.default_params(inv_depth_min=w.inv_depth_range[0], inv_depth_max=w.inv_depth_range[1],
-                          hyps_per_frame=64, )
+                          hyps_per_frame=64)
     a = vd.Window(w.flows.astype(np.float32), w.K, p)
     b = vd.Window(w.flows.astype(np.float32), w.K, p)
     T1 = a.bootstrap_epipolar(512, 1.0)

@@ -31,7 +31,7 @@ def test_scale_matches_the_oracle(vd, seed, s):
     w = synthetic.driving(seed=seed, W=414, H=125, f=239.3, T=2)
     depth, rig = _state(w, s)
     p = vd.default_params(inv_depth_min=w.inv_depth_range[0], inv_depth_max=w.inv_depth_range[1],
-                          hyps_per_frame=64, )
+                          hyps_per_frame=64)
     g = vd.Window(w.flows.astype(np.float32), w.K, p)
     g.bootstrap(w.poses[0])
     g.set_state(poses=w.poses, depth=depth, rigidness=rig)
@@ -57,7 +57,7 @@ def test_scale_matches_the_oracle(vd, seed, s):
 def test_no_ground_is_degenerate(vd):
     w = synthetic.small_planes(seed=1000)
     p = vd.default_params(inv_depth_min=w.inv_depth_range[0], inv_depth_max=w.inv_depth_range[1],
-                          hyps_per_frame=64, )
+                          hyps_per_frame=64)
     g = vd.Window(w.flows.astype(np.float32), w.K, p)
     assert vd.lib().voldor_ground_scale(g._h, 1.65, 0.17, 0, None) == vd.ERR_NOT_BOOTSTRAPPED
     g.bootstrap(w.poses[0])

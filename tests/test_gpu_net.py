@@ -151,7 +151,7 @@ def test_learned_bootstrap_scale_alignment(vd):
     from paper_2104_06789_gb300 import synthetic
     w = synthetic.small_planes(seed=1000)
     p = vd.default_params(inv_depth_min=w.inv_depth_range[0], inv_depth_max=w.inv_depth_range[1],
-                          hyps_per_frame=64, )
+                          hyps_per_frame=64)
     win = vd.Window(w.flows.astype(np.float32), w.K, p)
     win.bootstrap(w.poses[0])
     _, D_tri, _ = win.get_pose_depth_rigidness(poses=False, rigidness=False)
