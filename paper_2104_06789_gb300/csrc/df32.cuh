@@ -52,15 +52,6 @@ __device__ __forceinline__ float small_int_to_float(int i)
     return __fsub_rn(__int_as_float(0x4B000000 | i), 8388608.f);
 }
 
-// From FP64 (set-up only: two FP64 operations).
-__device__ __forceinline__ DF df_of(double d)
-{
-    const float h = __double2float_rn(d);
-    return DF{h, __double2float_rn(d - (double)h)};
-}
-
-__device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
-
 __device__ __forceinline__ float df_to_float(DF a) { return __fadd_rn(a.hi, a.lo); }
 
 __device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }

@@ -30,15 +30,20 @@ struct PrepGeo {
     bool valid;
 };
 
+// C_{t-1} as float-float pairs, written by the frame set-up
 __device__ __forceinline__ void load_cum_df(const DevState& s, int t, DF* C)
 {
-    if (threadIdx.x < 12) C[threadIdx.x] = df_of(s.cum[12 * (t - 1) + threadIdx.x]);
+    if (threadIdx.x < 12) {
+        const float* c = s.cum_df + 24 * (t - 1) + 2 * threadIdx.x;
+        C[threadIdx.x] = DF{c[0], c[1]};
+    }
     __syncthreads();
 }
 
 __device__ __forceinline__ PrepGeo prep_geometry(const DevParams& p, const DF* C, int t, int j, float th)
 {
-    const int x = j % p.W, y = j / p.W;
+    int x, y;
+    pixel_xy(p, j, x, y);
     const DF fx{p.kdf[0], p.kdf[1]}, fy{p.kdf[2], p.kdf[3]}, cx{p.kdf[4], p.kdf[5]}, cy{p.kdf[6], p.kdf[7]};
     const DF ifx{p.kdf[8], p.kdf[9]}, ify{p.kdf[10], p.kdf[11]};
     PrepGeo g;
@@ -197,18 +202,20 @@ void launch_pose_prep(const DevParams& p, const DevState& s, int t, cudaStream_t
 // frame to frame: the point in camera t (T_t applied to the point in camera
 // t-1) and its projection pi_t are the next frame's point in camera (t+1)-1
 // and pi_{(t+1)-1}, since C_t X = T_t (C_{t-1} X), so each frame transforms
-// and projects once. The residual xi - v_ob (tenths of a pixel) is the
+// and projects once (the frame set-up's float-float copy of T_t). The residual xi - v_ob (tenths of a pixel) is the
 // difference of quantities of up to hundreds of pixels: the sample position,
 // the bilinear flow (in lerp form, with df32 fractions) and the rigid flow
 // are all kept in df32 and only the residual is rounded to FP32.
 __global__ void __launch_bounds__(kPixThreads) k_emissions(DevParams p, DevState s, float* out)
 {
     __shared__ DF Tdf[kMaxT][12];
-    for (int i = threadIdx.x; i < p.T * 12; i += blockDim.x) Tdf[i / 12][i % 12] = df_of(s.poses[i]);
+    for (int i = threadIdx.x; i < p.T * 12; i += blockDim.x)
+        Tdf[i / 12][i % 12] = DF{s.poses_df[2 * i], s.poses_df[2 * i + 1]};
     __syncthreads();
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= p.N) return;
-    const int x = j % p.W, y = j / p.W;
+    int x, y;
+    pixel_xy(p, j, x, y);
     const DF fx{p.kdf[0], p.kdf[1]}, fy{p.kdf[2], p.kdf[3]}, cx{p.kdf[4], p.kdf[5]}, cy{p.kdf[6], p.kdf[7]};
     const DF ifx{p.kdf[8], p.kdf[9]}, ify{p.kdf[10], p.kdf[11]};
     const float th = s.theta[j];

@@ -25,12 +25,26 @@ __global__ void k_frame_setup(DevParams p, DevState s)
     const int c = threadIdx.x;
     if (c >= 4) return;
     double C0 = c == 0 ? 1.0 : 0.0, C1 = c == 1 ? 1.0 : 0.0, C2 = c == 2 ? 1.0 : 0.0;
+    // a value as a float-float pair (hi, lo): hi = fl32(v), lo = fl32(v - hi)
+    auto split = [](double v, float* o) {
+        const float h = (float)v;
+        o[0] = h;
+        o[1] = (float)(v - (double)h);
+    };
     for (int t = 1; t <= p.T; ++t) {
         double* cum = s.cum + 12 * (t - 1);
         cum[c] = C0;
         cum[4 + c] = C1;
         cum[8 + c] = C2;
         const double* At = A + 12 * (t - 1);
+        float* cd = s.cum_df + 24 * (t - 1);
+        float* pd = s.poses_df + 24 * (t - 1);
+        split(C0, cd + 2 * c);
+        split(C1, cd + 2 * (4 + c));
+        split(C2, cd + 2 * (8 + c));
+        split(At[c], pd + 2 * c);
+        split(At[4 + c], pd + 2 * (4 + c));
+        split(At[8 + c], pd + 2 * (8 + c));
         float* f = s.frames32 + 24 * (t - 1);     // E_c = R_c - I, t_c, E_t = R_t - I, t_t
         if (c < 3) {
             f[c] = (float)(C0 - (c == 0 ? 1.0 : 0.0));

@@ -106,6 +106,7 @@ DevParams make_dev_params(const voldor_ctx& c)
     d.inv_fxd = 1.0 / c.K.fx; d.inv_fyd = 1.0 / c.K.fy; d.fy_over_fx_d = c.K.fy / c.K.fx;
     d.sigma_t = p.sigma_t; d.sigma_r = p.sigma_r; d.ms_tol = p.ms_tol;
     d.seed = p.seed; d.window_id = p.window_id;
+    d.w_magic = (unsigned)((1ull << 32) / (unsigned long long)c.W);
     const double kv[6] = {c.K.fx, c.K.fy, c.K.cx, c.K.cy, 1.0 / c.K.fx, 1.0 / c.K.fy};
     for (int i = 0; i < 6; ++i) {
         const float h = (float)kv[i];
@@ -138,6 +139,8 @@ size_t layout(voldor_ctx& c, char* base)
     s.poses = (double*)take(T * 12 * 8);
     s.cum = (double*)take(T * 12 * 8);
     s.frames32 = (float*)take(T * 24 * 4);
+    s.cum_df = (float*)take(T * 24 * 4);
+    s.poses_df = (float*)take(T * 24 * 4);
     s.iter = (int*)take(4);
     s.status = (int*)take(16);
     c.flag_dev = (int*)take(4);

@@ -50,7 +50,19 @@ struct DevParams {
     // fx, fy, cx, cy, 1/fx, 1/fy as float-float pairs (hi, lo) for the df32
     // geometry passes
     float kdf[12];
+    unsigned w_magic;                   // floor(2^32 / W): pixel index -> row without a division
 };
+
+// (x, y) of pixel j: q = hi32(j floor(2^32 / W)) is floor(j / W) or one less,
+// and one comparison corrects it (exact for 0 <= j < 2^31).
+__device__ __forceinline__ void pixel_xy(const DevParams& p, int j, int& x, int& y)
+{
+    unsigned q = __umulhi((unsigned)j, p.w_magic);
+    unsigned r = (unsigned)j - q * (unsigned)p.W;
+    if (r >= (unsigned)p.W) { ++q; r -= (unsigned)p.W; }
+    x = (int)r;
+    y = (int)q;
+}
 
 // Per-pixel record of a frame for dense scoring (three float4 = 48 B).
 //  a = {xb, yb2, w, ut}: normalised coords x/z, (fy/fx) y/z, inverse depth 1/z
@@ -72,6 +84,8 @@ struct DevState {
     double* poses;            // [T][12] row-major [R | t]
     double* cum;              // [T][12] C_{t-1} = T_{t-1} ... T_1 (FP64)
     float* frames32;          // [T][24] FP32 E_c = R_c - I, t_c, E_t = R_t - I, t_t
+    float* cum_df;            // [T][12][2] C_{t-1} as float-float pairs (hi, lo)
+    float* poses_df;          // [T][12][2] T_t as float-float pairs
     int* iter;                // [1] iteration counter k
     int* status;              // [4] n_hyp, seed, meanshift steps, status bits
     // dense scoring scratch
