@@ -589,28 +589,42 @@ def run_ours(args):
 # ---------------------------------------------------------------------------
 # batched workload: many windows of mixed resolution and T in one CUDA graph
 # ---------------------------------------------------------------------------
-def batch_workload(n, seed=4000):
-    """n windows, resolutions uniform over {320x240, 640x480, 1242x375} and T
-    uniform in [3, 8]; two rendered scenes per resolution (planar-patch scenes
-    at 320x240, handheld scenes otherwise, focal scaled with the width), each
-    window taking the first T flows of one of them and its own Philox key."""
+def _render_window(job):
+    """One window of the mixed batch (module level: runs in spawned workers)."""
     from paper_2104_06789_gb300 import synthetic
+    W, H, T, sd = job
+    if W == 320:
+        return synthetic.small_planes(seed=sd, W=W, H=H, f=0.75 * W, T=T)
+    return synthetic.handheld(seed=sd, W=W, H=H, f=0.82 * W, T=T)
+
+
+def batch_workload(n, seed=4000):
+    """n independently rendered windows: resolution uniform over {320x240,
+    640x480, 1242x375}, T uniform in [3, 8] and a scene seed of its own each
+    (planar-patch scenes at 320x240, handheld scenes otherwise, focal scaled
+    with the width). Rendered on spawned processes, one thread each.
+    Returns [(window, T)]."""
+    import multiprocessing as mp
     rng = np.random.default_rng(seed)
-    bases = {}
-    for r, (W, H) in enumerate([(320, 240), (640, 480), (1242, 375)]):
-        for v in range(2):
-            sd = seed + 10 * r + v
-            if W == 320:
-                bases[(r, v)] = synthetic.small_planes(seed=sd, W=W, H=H, f=0.75 * W, T=8)
-            else:
-                bases[(r, v)] = synthetic.handheld(seed=sd, W=W, H=H, f=0.82 * W, T=8)
-    out = []
+    sizes = [(320, 240), (640, 480), (1242, 375)]
+    jobs = []
     for i in range(n):
-        r = int(rng.integers(0, 3))
-        T = int(rng.integers(3, 9))
-        b = bases[(r, int(rng.integers(0, 2)))]
-        out.append((b, T))
-    return out
+        W, H = sizes[int(rng.integers(0, 3))]
+        jobs.append((W, H, int(rng.integers(3, 9)), seed + 1 + i))
+    workers = max(1, min(len(jobs), (os.cpu_count() or 2) - 1))
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    os.environ.update({k: "1" for k in keys})
+    try:
+        with mp.get_context("spawn").Pool(workers) as pool:
+            wins = pool.map(_render_window, jobs, chunksize=1)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return [(b, job[2]) for b, job in zip(wins, jobs)]
 
 
 def run_batch(args):

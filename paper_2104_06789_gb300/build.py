@@ -39,8 +39,8 @@ def _nvcc():
 
 
 def _sources():
-    return [os.path.join(CSRC, u) for u in UNITS] + [os.path.join(CSRC, "voldor_internal.cuh"),
-                                                      os.path.join(INCLUDE, "voldor.h")]
+    headers = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith(".cuh")]
+    return [os.path.join(CSRC, u) for u in UNITS] + headers + [os.path.join(INCLUDE, "voldor.h")]
 
 
 def up_to_date() -> bool:

@@ -539,7 +539,7 @@ __device__ __forceinline__ void stsm_x4(uint32_t addr, uint32_t r0, uint32_t r1,
 }
 
 template <int CIN, int NCO>
-__global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(WgradArgs a)
+__global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const __grid_constant__ WgradArgs a)
 {
     using S = WgShape<CIN, NCO>;
     extern __shared__ __align__(1024) unsigned char smem[];
