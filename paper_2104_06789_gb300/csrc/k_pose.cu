@@ -6,6 +6,7 @@
 
 #include <cooperative_groups.h>
 
+#include "df32.cuh"
 #include "voldor_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -626,8 +627,21 @@ __global__ void k_hyp_write(DevParams p, DevState s)
         for (int c = 0; c < 3; ++c) f[r * 3 + c] = (float)(sc[r] * (Rt[r * 4 + c] - (r == c ? 1.0 : 0.0)) / sc[c]);
         f[9 + r] = (float)(sc[r] * Rt[r * 4 + 3]);
     }
-    se3_log_quat(Rt, s.hyp_p + (size_t)h * 6);
+    // the se(3) logarithm and the weight in the meanshift's FP32 form: each
+    // coordinate as a float-float pair (hi = v rounded, lo = v - hi rounded)
+    double pv[6];
+    se3_log_quat(Rt, pv);
+    float4* pw = reinterpret_cast<float4*>(s.hyp_pw + (size_t)h * 16);
+    float hi[6], lo[6];
+    for (int c = 0; c < 6; ++c) {
+        hi[c] = (float)pv[c];
+        lo[c] = (float)(pv[c] - (double)hi[c]);
+    }
     s.hyp_w[h] = s.grp_weight[g];
+    pw[0] = make_float4(hi[0], hi[1], hi[2], hi[3]);
+    pw[1] = make_float4(hi[4], hi[5], lo[0], lo[1]);
+    pw[2] = make_float4(lo[2], lo[3], lo[4], lo[5]);
+    pw[3] = make_float4((float)s.grp_weight[g], 0.f, 0.f, 0.f);
     s.hyp_info[(size_t)h * 2 + 0] = g;
     s.hyp_info[(size_t)h * 2 + 1] = i;
 }
@@ -663,12 +677,18 @@ void score_hyps_from_host(const DevParams& p, const DevState& s, int n, cudaStre
 // ---------------------------------------------------------------------------
 // Meanshift (Eqs. 18-19): x <- sum_h w_h K(x - p_h) p_h / sum_h w_h K(x - p_h),
 // K(d) = exp(-d^T Sigma^-1 d / 2), seeded at argmax_h L_h (lowest index on
-// ties), on a cluster of kMeanshiftCtas CTAs. The state x and all sums across
-// threads are FP64; each hypothesis is held as its FP32 offset from the seed,
-// so the Gaussian and the per-thread partial sums are FP32 on small numbers.
-// Every CTA reduces the cluster's partial sums in the same order, so all take
-// the same steps; partial buffers alternate by iteration parity so one
-// cluster barrier per step suffices. The iteration stops when the step is
+// ties), on a cluster of kMeanshiftCtas CTAs. Everything runs on the FP32
+// pipe (an FP64 instruction is a long issue on this GPU's FP64 pipe, and this
+// kernel is a chain of small dependent steps): the argmax compares the FP64
+// scores as order-preserving integer keys; each hypothesis is held as its
+// FP32 offset from the seed, taken from float-float copies of the se(3)
+// logarithms, so the Gaussian and the per-thread partial sums are FP32 on
+// small numbers; sums across warps and CTAs and the state (the offset of x
+// from the seed) are float-float, about 44 significant bits. Every CTA
+// reduces the cluster's partial sums in the same order, so all take the same
+// steps; partial buffers alternate by iteration parity so one cluster barrier
+// per step suffices, and one warp finishes the step (sums across CTAs, new
+// state, convergence) with shuffles. The iteration stops when the step is
 // below ms_tol, when a step below 1e-7 no longer contracts (the FP32 noise
 // floor of the kernel weights), or after ms_max_iter steps.
 // ---------------------------------------------------------------------------
@@ -680,20 +700,31 @@ __device__ __forceinline__ float warp_sum_f(float v)
     return v;
 }
 
+// Order-preserving integer key of a double: a < b iff key(a) < key(b) for
+// non-NaN values, -0 and +0 equal.
+__device__ __forceinline__ long long score_key(double v)
+{
+    long long b = __double_as_longlong(v);
+    if (b == (long long)0x8000000000000000ull) b = 0;
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffll);
+}
+
+__device__ __forceinline__ DF shfl_df(DF v, int src)
+{
+    return DF{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+}
+
 __global__ void __cluster_dims__(kMeanshiftCtas, 1, 1) __launch_bounds__(kMeanshiftThreads, 1)
 k_meanshift(DevParams p, DevState s, int t)
 {
     cg::cluster_group cluster = cg::this_cluster();
     const unsigned rank = cluster.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-    __shared__ double wred[32][8];
-    __shared__ double part[2][8];
-    __shared__ double gath[kMeanshiftCtas * 7];
-    __shared__ double xs[8];
-    __shared__ double tot_s[8];
-    __shared__ double dsq[8];
-    __shared__ double seedp[6];
-    __shared__ double bval[32];
+    __shared__ float wred[32][8];
+    __shared__ float2 part[2][8];
+    __shared__ float xo_hi[6], xo_lo[6];      // x - p_seed, float-float
+    __shared__ float seed_hi[6], seed_lo[6];
+    __shared__ long long bkey[32];
     __shared__ int bidx[32];
     __shared__ int flag;
     const int n = *s.n_hyp;
@@ -704,26 +735,38 @@ k_meanshift(DevParams p, DevState s, int t)
         return;   // uniform over the cluster: every CTA reads the same n
     }
     // argmax of L (lowest index on ties; NaN never wins)
-    double bv = -INFINITY;
+    long long bk = 0;
     int bi = 0x7fffffff;
     for (int h = tid; h < n; h += blockDim.x) {
         const double v = s.scores[h];
-        if (v > bv || (v == bv && h < bi)) { bv = v; bi = h; }
+        const long long raw = __double_as_longlong(v) & 0x7fffffffffffffffll;
+        if (raw > 0x7ff0000000000000ll) continue;                 // NaN
+        const long long k = score_key(v);
+        if (bi == 0x7fffffff || k > bk || (k == bk && h < bi)) { bk = k; bi = h; }
     }
     for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+        if (oi != 0x7fffffff && (bi == 0x7fffffff || ok > bk || (ok == bk && oi < bi))) { bk = ok; bi = oi; }
     }
-    if (lane == 0) { bval[warp] = bv; bidx[warp] = bi; }
+    if (lane == 0) { bkey[warp] = bk; bidx[warp] = bi; }
     __syncthreads();
     if (tid == 0) {
-        double v = bval[0];
+        long long k = bkey[0];
         int i = bidx[0];
         for (int w = 1; w < nwarp; ++w)
-            if (bval[w] > v || (bval[w] == v && bidx[w] < i)) { v = bval[w]; i = bidx[w]; }
+            if (bidx[w] != 0x7fffffff && (i == 0x7fffffff || bkey[w] > k || (bkey[w] == k && bidx[w] < i))) {
+                k = bkey[w];
+                i = bidx[w];
+            }
         if (i == 0x7fffffff) i = 0;
-        for (int c = 0; c < 6; ++c) { seedp[c] = s.hyp_p[(size_t)i * 6 + c]; xs[c] = seedp[c]; }
+        const float* ps = s.hyp_pw + (size_t)i * 16;
+        for (int c = 0; c < 6; ++c) {
+            seed_hi[c] = ps[c];
+            seed_lo[c] = ps[6 + c];
+            xo_hi[c] = 0.f;
+            xo_lo[c] = 0.f;
+        }
         bidx[0] = i;
         flag = 0;
     }
@@ -733,32 +776,45 @@ k_meanshift(DevParams p, DevState s, int t)
     // kMsCached stay in registers, the rest (S above kMsCached x the cluster's
     // threads) go to global memory
     const int stride = kMeanshiftCtas * blockDim.x, h0 = rank * blockDim.x + tid;
+    DF sd[6];
+    for (int c = 0; c < 6; ++c) sd[c] = DF{seed_hi[c], seed_lo[c]};
     float4 r0[kMsCached], r1[kMsCached];
 #pragma unroll
     for (int k = 0; k < kMsCached; ++k) { r0[k] = make_float4(0.f, 0.f, 0.f, 0.f); r1[k] = r0[k]; }
     for (int h = h0, k = 0; h < n; h += stride, ++k) {
-        const double* ph = s.hyp_p + (size_t)h * 6;
-        const float4 o0 = make_float4((float)(ph[0] - seedp[0]), (float)(ph[1] - seedp[1]),
-                                      (float)(ph[2] - seedp[2]), (float)(ph[3] - seedp[3]));
-        const float4 o1 = make_float4((float)(ph[4] - seedp[4]), (float)(ph[5] - seedp[5]), (float)s.hyp_w[h], 0.f);
+        const float4* pw = reinterpret_cast<const float4*>(s.hyp_pw + (size_t)h * 16);
+        const float4 a = pw[0], b = pw[1], c2 = pw[2], d = pw[3];
+        const float ph[6] = {a.x, a.y, a.z, a.w, b.x, b.y}, pl[6] = {b.z, b.w, c2.x, c2.y, c2.z, c2.w};
+        float o[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) o[c] = df_to_float(df_sub(DF{ph[c], pl[c]}, sd[c]));
+        const float4 o0 = make_float4(o[0], o[1], o[2], o[3]);
+        const float4 o1 = make_float4(o[4], o[5], d.x, 0.f);
         if (k < kMsCached) {
 #pragma unroll
             for (int i = 0; i < kMsCached; ++i)
                 if (i == k) { r0[i] = o0; r1[i] = o1; }
         } else {
-            float4* o = reinterpret_cast<float4*>(s.hyp_dp + (size_t)h * 8);
-            o[0] = o0;
-            o[1] = o1;
+            float4* od = reinterpret_cast<float4*>(s.hyp_dp + (size_t)h * 8);
+            od[0] = o0;
+            od[1] = o1;
         }
     }
-    const float ivt = (float)(1.0 / p.sigma_t), ivr = (float)(1.0 / p.sigma_r);
+    __shared__ float consts[3];
+    if (tid == 0) {
+        consts[0] = (float)(1.0 / p.sigma_t);
+        consts[1] = (float)(1.0 / p.sigma_r);
+        consts[2] = (float)p.ms_tol;
+    }
+    __syncthreads();
+    const float ivt = consts[0], ivr = consts[1], tol = consts[2];
     const float mlog2e = -0.5f * 1.4426950408889634f;
     int it = 0;
     bool degenerate = false;
-    double prev_step = INFINITY;
+    float prev_step = INFINITY;
     for (; it < p.ms_max_iter; ++it) {
         float dx[6];
-        for (int c = 0; c < 6; ++c) dx[c] = (float)(xs[c] - seedp[c]);
+        for (int c = 0; c < 6; ++c) dx[c] = xo_hi[c] + xo_lo[c];
         float acc[7] = {0, 0, 0, 0, 0, 0, 0};
         // hypotheses in increasing h (the registers' first, then global memory)
         auto add = [&](const float4 q0, const float4 q1) {
@@ -778,57 +834,65 @@ k_meanshift(DevParams p, DevState s, int t)
             const float4* o = reinterpret_cast<const float4*>(s.hyp_dp + (size_t)h * 8);
             add(o[0], o[1]);
         }
-        // warp sums in FP32 (each lane holds at most 4 terms; a warp-wide FP64 add
-        // costs this GPU's FP64 pipe ~16 cycles), the rest of the reduction in FP64
+        // warp sums in FP32 (each lane holds at most 4 terms), then the CTA's
+        // warps in order as float-float
         float accw[7];
         for (int c = 0; c < 7; ++c) accw[c] = warp_sum_f(acc[c]);
         if (lane == 0)
-            for (int c = 0; c < 7; ++c) wred[warp][c] = (double)accw[c];
+            for (int c = 0; c < 7; ++c) wred[warp][c] = accw[c];
         __syncthreads();
         const int buf = it & 1;
         if (tid < 7) {
-            double v = 0.0;
-            for (int w = 0; w < nwarp; ++w) v += wred[w][tid];
-            part[buf][tid] = v;
+            DF v{0.f, 0.f};
+            for (int w = 0; w < nwarp; ++w) v = df_add(v, wred[w][tid]);
+            part[buf][tid] = make_float2(v.hi, v.lo);
         }
         cluster.sync();
-        // the CTAs' partial sums, fetched in parallel from distributed shared
-        // memory, then added in rank order by one thread
-        if (tid < kMeanshiftCtas * 7)
-            gath[tid] = *cluster.map_shared_rank(&part[buf][tid % 7], (unsigned)(tid / 7));
-        __syncthreads();
-        // component c of the cluster's sums, added in rank order by thread c
-        // (each FP64 instruction is a long issue on this GPU's FP64 pipe, so
-        // the 7 x 8 additions and the 6 coordinate updates run in parallel,
-        // not in one thread)
-        if (tid < 7) {
-            double v = 0.0;
-            for (unsigned r = 0; r < kMeanshiftCtas; ++r) v += gath[r * 7 + tid];
-            tot_s[tid] = v;
-        }
-        __syncthreads();
-        const bool mass = tot_s[0] > 0.0;
-        if (mass && tid < 6) {
-            const double xn = seedp[tid] + tot_s[1 + tid] * (1.0 / tot_s[0]);
-            const double d = xn - xs[tid];
-            dsq[tid] = d * d;
-            xs[tid] = xn;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            if (!mass) {
-                flag = (it == 0) ? 2 : 1;
-            } else {
-                double step = 0.0;
-                for (int c = 0; c < 6; ++c) step += dsq[c];
-                step = sqrt(step);
-                flag = (step < p.ms_tol || (step >= prev_step && step < 1e-7)) ? 1 : 0;
-                prev_step = step;
+        if (warp == 0) {
+            // entry e = r * 7 + c (component c of rank r's sums, from distributed
+            // shared memory) is fetched by lane e % 32 into slot e / 32; lane
+            // c < 7 adds the entries of its component in rank order
+            static_assert(kMeanshiftCtas * 7 <= 64, "two entries per lane");
+            DF g[2] = {DF{0.f, 0.f}, DF{0.f, 0.f}};
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int e = lane + 32 * q;
+                if (e < kMeanshiftCtas * 7) {
+                    const float2 v = *cluster.map_shared_rank(&part[buf][e % 7], (unsigned)(e / 7));
+                    g[q] = DF{v.x, v.y};
+                }
+            }
+            DF tot{0.f, 0.f};
+            for (int r = 0; r < kMeanshiftCtas; ++r) {
+                const int e = r * 7 + (lane < 7 ? lane : 0);
+                const DF v0 = shfl_df(g[0], e & 31), v1 = shfl_df(g[1], e & 31);
+                tot = df_add(tot, e < 32 ? v0 : v1);
+            }
+            const DF t0 = shfl_df(tot, 0);
+            const bool mass = t0.hi > 0.f;
+            float dd = 0.f;
+            if (mass && lane >= 1 && lane < 7) {
+                const DF xn = df_div(tot, t0);                    // mean offset of component lane - 1
+                const DF xo{xo_hi[lane - 1], xo_lo[lane - 1]};
+                dd = df_to_float(df_sub(xn, xo));
+                dd *= dd;
+                xo_hi[lane - 1] = xn.hi;
+                xo_lo[lane - 1] = xn.lo;
+            }
+            float s2 = 0.f;
+            for (int c = 1; c < 7; ++c) s2 += __shfl_sync(0xffffffffu, dd, c);
+            if (lane == 0) {
+                if (!mass) {
+                    flag = (it == 0) ? 2 : 1;
+                } else {
+                    const float step = sqrtf(s2);
+                    flag = (step < tol || (step >= prev_step && step < 1e-7f)) ? 1 : 0;
+                    prev_step = step;
+                }
             }
         }
         __syncthreads();
         const int f = flag;
-        __syncthreads();
         if (f == 2) { degenerate = true; break; }
         if (f == 1) { ++it; break; }
     }
@@ -841,7 +905,8 @@ k_meanshift(DevParams p, DevState s, int t)
             s.status[3] += 1;
         } else {
             double x[6];
-            for (int c = 0; c < 6; ++c) x[c] = xs[c];
+            for (int c = 0; c < 6; ++c)
+                x[c] = ((double)seed_hi[c] + (double)seed_lo[c]) + ((double)xo_hi[c] + (double)xo_lo[c]);
             se3_exp_vec(x, s.poses + 12 * (t - 1));
         }
     }

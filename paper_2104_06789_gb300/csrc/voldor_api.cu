@@ -158,7 +158,7 @@ size_t layout(voldor_ctx& c, char* base)
     s.n_hyp = (int*)take(4);
     s.hyp_Rt = (double*)take(S * 12 * 8);
     s.hyp_f32 = (float*)take(S * 12 * 4);
-    s.hyp_p = (double*)take(S * 6 * 8);
+    s.hyp_pw = (float*)take(S * 16 * 4);
     s.hyp_w = (double*)take(S * 8);
     s.hyp_dp = (float*)take(S * 8 * 4);
     s.hyp_info = (long long*)take(S * 2 * 8);

@@ -104,7 +104,7 @@ struct DevState {
     int* n_hyp;               // [1]
     double* hyp_Rt;           // [S][12]
     float* hyp_f32;           // [S][12] scoring form
-    double* hyp_p;            // [S][6] se(3) log
+    float* hyp_pw;            // [S][16] se(3) log as float-float (hi of the 6 coordinates, then lo), group weight, 0 0 0
     double* hyp_w;            // [S]
     float* hyp_dp;            // [S][8] meanshift scratch: p_h - p_seed (6), w_h, 0
     long long* hyp_info;      // [S][2]
