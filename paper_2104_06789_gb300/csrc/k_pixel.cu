@@ -20,64 +20,59 @@ namespace vd {
 __global__ void k_frame_setup(DevParams p, DevState s)
 {
     __shared__ double A[kMaxT * 12];
+    __shared__ double Cs[kMaxT * 12];          // C_{t-1}, [t - 1][3][4]
     for (int i = threadIdx.x; i < p.T * 12; i += blockDim.x) A[i] = s.poses[i];
     __syncthreads();
+    // the product chain C_t = T_t C_{t-1}: thread c < 4 carries column c
     const int c = threadIdx.x;
-    if (c >= 4) return;
-    double C0 = c == 0 ? 1.0 : 0.0, C1 = c == 1 ? 1.0 : 0.0, C2 = c == 2 ? 1.0 : 0.0;
-    // a value as a float-float pair (hi, lo): hi = fl32(v), lo = fl32(v - hi)
-    auto split = [](double v, float* o) {
-        const float h = (float)v;
-        o[0] = h;
-        o[1] = (float)(v - (double)h);
-    };
-    for (int t = 1; t <= p.T; ++t) {
-        double* cum = s.cum + 12 * (t - 1);
-        cum[c] = C0;
-        cum[4 + c] = C1;
-        cum[8 + c] = C2;
-        const double* At = A + 12 * (t - 1);
-        float* cd = s.cum_df + 24 * (t - 1);
-        float* pd = s.poses_df + 24 * (t - 1);
-        split(C0, cd + 2 * c);
-        split(C1, cd + 2 * (4 + c));
-        split(C2, cd + 2 * (8 + c));
-        split(At[c], pd + 2 * c);
-        split(At[4 + c], pd + 2 * (4 + c));
-        split(At[8 + c], pd + 2 * (8 + c));
-        float* f = s.frames32 + 24 * (t - 1);     // E_c = R_c - I, t_c, E_t = R_t - I, t_t
-        if (c < 3) {
-            f[c] = (float)(C0 - (c == 0 ? 1.0 : 0.0));
-            f[3 + c] = (float)(C1 - (c == 1 ? 1.0 : 0.0));
-            f[6 + c] = (float)(C2 - (c == 2 ? 1.0 : 0.0));
-            f[12 + c] = (float)(At[c] - (c == 0 ? 1.0 : 0.0));
-            f[15 + c] = (float)(At[4 + c] - (c == 1 ? 1.0 : 0.0));
-            f[18 + c] = (float)(At[8 + c] - (c == 2 ? 1.0 : 0.0));
+    if (c < 4) {
+        double C0 = c == 0 ? 1.0 : 0.0, C1 = c == 1 ? 1.0 : 0.0, C2 = c == 2 ? 1.0 : 0.0;
+        for (int t = 1; t <= p.T; ++t) {
+            double* Ct = Cs + 12 * (t - 1);
+            Ct[c] = C0;
+            Ct[4 + c] = C1;
+            Ct[8 + c] = C2;
+            const double* At = A + 12 * (t - 1);
+            double n0 = At[0] * C0 + At[1] * C1 + At[2] * C2;
+            double n1 = At[4] * C0 + At[5] * C1 + At[6] * C2;
+            double n2 = At[8] * C0 + At[9] * C1 + At[10] * C2;
+            if (c == 3) {
+                n0 = n0 + At[3];
+                n1 = n1 + At[7];
+                n2 = n2 + At[11];
+            }
+            C0 = n0;
+            C1 = n1;
+            C2 = n2;
+        }
+    }
+    __syncthreads();
+    // every stage's outputs, one element (t, r, col) per thread: C_{t-1} in FP64
+    // and as float-float pairs (hi = fl32(v), lo = fl32(v - hi)), T_t as
+    // float-float pairs, and both as E = R - I, t in FP32
+    for (int i = threadIdx.x; i < p.T * 12; i += blockDim.x) {
+        const int t1 = i / 12, e = i % 12, r = e / 4, col = e % 4;
+        const double cv = Cs[i], av = A[i];
+        s.cum[i] = cv;
+        const float ch = (float)cv, ah = (float)av;
+        s.cum_df[2 * i] = ch;
+        s.cum_df[2 * i + 1] = (float)(cv - (double)ch);
+        s.poses_df[2 * i] = ah;
+        s.poses_df[2 * i + 1] = (float)(av - (double)ah);
+        float* f = s.frames32 + 24 * t1;        // E_c = R_c - I, t_c, E_t = R_t - I, t_t
+        if (col < 3) {
+            f[3 * r + col] = (float)(cv - (r == col ? 1.0 : 0.0));
+            f[12 + 3 * r + col] = (float)(av - (r == col ? 1.0 : 0.0));
         } else {
-            f[9] = (float)C0;
-            f[10] = (float)C1;
-            f[11] = (float)C2;
-            f[21] = (float)At[3];
-            f[22] = (float)At[7];
-            f[23] = (float)At[11];
+            f[9 + r] = (float)cv;
+            f[21 + r] = (float)av;
         }
-        double n0 = At[0] * C0 + At[1] * C1 + At[2] * C2;
-        double n1 = At[4] * C0 + At[5] * C1 + At[6] * C2;
-        double n2 = At[8] * C0 + At[9] * C1 + At[10] * C2;
-        if (c == 3) {
-            n0 = n0 + At[3];
-            n1 = n1 + At[7];
-            n2 = n2 + At[11];
-        }
-        C0 = n0;
-        C1 = n1;
-        C2 = n2;
     }
 }
 
 void launch_frame_setup(const DevParams& p, const DevState& s, cudaStream_t st)
 {
-    k_frame_setup<<<1, 32, 0, st>>>(p, s);
+    k_frame_setup<<<1, kMaxT * 12, 0, st>>>(p, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -627,23 +627,37 @@ __global__ void k_hyp_write(DevParams p, DevState s)
         for (int c = 0; c < 3; ++c) f[r * 3 + c] = (float)(sc[r] * (Rt[r * 4 + c] - (r == c ? 1.0 : 0.0)) / sc[c]);
         f[9 + r] = (float)(sc[r] * Rt[r * 4 + 3]);
     }
-    // the se(3) logarithm and the weight in the meanshift's FP32 form: each
-    // coordinate as a float-float pair (hi = v rounded, lo = v - hi rounded)
+    s.hyp_w[h] = s.grp_weight[g];
+    s.hyp_info[(size_t)h * 2 + 0] = g;
+    s.hyp_info[(size_t)h * 2 + 1] = i;
+}
+
+// The meanshift's form of hypothesis h (after k_hyp_write): its se(3)
+// logarithm, each coordinate as a float-float pair (hi = v rounded, lo =
+// v - hi rounded), and its weight in FP32. A long FP64 chain per hypothesis,
+// needed only by the meanshift: it runs on a side branch beside the scoring.
+__global__ void k_hyp_log(DevParams p, DevState s)
+{
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= *s.n_hyp) return;
+    const long long g = s.hyp_info[(size_t)h * 2 + 0], i = s.hyp_info[(size_t)h * 2 + 1];
     double pv[6];
-    se3_log_quat(Rt, pv);
-    float4* pw = reinterpret_cast<float4*>(s.hyp_pw + (size_t)h * 16);
+    se3_log_quat(s.grp_sols + ((size_t)g * kMaxSols + i) * 12, pv);
     float hi[6], lo[6];
     for (int c = 0; c < 6; ++c) {
         hi[c] = (float)pv[c];
         lo[c] = (float)(pv[c] - (double)hi[c]);
     }
-    s.hyp_w[h] = s.grp_weight[g];
+    float4* pw = reinterpret_cast<float4*>(s.hyp_pw + (size_t)h * 16);
     pw[0] = make_float4(hi[0], hi[1], hi[2], hi[3]);
     pw[1] = make_float4(hi[4], hi[5], lo[0], lo[1]);
     pw[2] = make_float4(lo[2], lo[3], lo[4], lo[5]);
-    pw[3] = make_float4((float)s.grp_weight[g], 0.f, 0.f, 0.f);
-    s.hyp_info[(size_t)h * 2 + 0] = g;
-    s.hyp_info[(size_t)h * 2 + 1] = i;
+    pw[3] = make_float4((float)s.hyp_w[h], 0.f, 0.f, 0.f);
+}
+
+void launch_hyp_log(const DevParams& p, const DevState& s, cudaStream_t st)
+{
+    k_hyp_log<<<(p.S + 127) / 128, 128, 0, st>>>(p, s);
 }
 
 void launch_hyp_collect(const DevParams& p, const DevState& s, cudaStream_t st)

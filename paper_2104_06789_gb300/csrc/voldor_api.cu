@@ -37,6 +37,7 @@ struct voldor_ctx {
     cudaError_t first_error = cudaSuccess;           // the error that poisoned the context
     cudaStream_t aux = nullptr;                      // second stream: P3P beside the pose preparation
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;   // hypothesis logarithms beside the scoring
     void* epi_base = nullptr;                        // epipolar bootstrap scratch
     int epi_cap = 0;                                 // samples it holds
     int epi_M = 0;                                   // samples of the last epipolar bootstrap
@@ -221,11 +222,18 @@ bool enqueue_pose_update(voldor_ctx* c, int t, cudaEvent_t ev0, cudaEvent_t ev1,
     launch_prep_write(p, s, t, st);
     if (!cuda_ok(c, cudaStreamWaitEvent(st, c->ev_join, 0))) return false;
     launch_hyp_collect(p, s, st);
+    // the meanshift's form of the hypotheses (FP64 se(3) logarithms) is
+    // computed beside the dense scoring
+    if (!cuda_ok(c, cudaEventRecord(c->ev_fork2, st))) return false;
+    if (!cuda_ok(c, cudaStreamWaitEvent(c->aux, c->ev_fork2, 0))) return false;
+    launch_hyp_log(p, s, c->aux);
+    if (!cuda_ok(c, cudaEventRecord(c->ev_join2, c->aux))) return false;
     // External records become event-record nodes when the stream is captured
     if (ev0 && !cuda_ok(c, cudaEventRecordWithFlags(ev0, st, cudaEventRecordExternal))) return false;
     launch_score(p, s, log_idx, st);
     if (ev1 && !cuda_ok(c, cudaEventRecordWithFlags(ev1, st, cudaEventRecordExternal))) return false;
     launch_score_reduce(p, s, st);
+    if (!cuda_ok(c, cudaStreamWaitEvent(st, c->ev_join2, 0))) return false;
     launch_meanshift(p, s, t, st);
     return launched(c);
 }
@@ -420,7 +428,9 @@ voldor_status voldor_init_window(voldor_ctx** out, int width, int height, int T,
     layout(*c, (char*)c->arena);
     if (!cuda_ok(c, cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking)) ||
         !cuda_ok(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) ||
-        !cuda_ok(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming))) {
+        !cuda_ok(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming)) ||
+        !cuda_ok(c, cudaEventCreateWithFlags(&c->ev_fork2, cudaEventDisableTiming)) ||
+        !cuda_ok(c, cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming))) {
         voldor_destroy(c);
         return kCuda;
     }
@@ -596,6 +606,8 @@ void voldor_destroy(voldor_ctx* c)
     if (c->aux) { cudaStreamSynchronize(c->aux); cudaStreamDestroy(c->aux); }
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_fork2) cudaEventDestroy(c->ev_fork2);
+    if (c->ev_join2) cudaEventDestroy(c->ev_join2);
     if (c->arena) cudaFree(c->arena);
     if (c->epi_base) cudaFree(c->epi_base);
     if (c->ground_base) cudaFree(c->ground_base);

@@ -279,6 +279,7 @@ void launch_prep_count(const DevParams& p, const DevState& s, int t, cudaStream_
 void launch_prep_write(const DevParams& p, const DevState& s, int t, cudaStream_t st);
 void launch_p3p_groups(const DevParams& p, const DevState& s, int t, cudaStream_t st);
 void launch_hyp_collect(const DevParams& p, const DevState& s, cudaStream_t st);
+void launch_hyp_log(const DevParams& p, const DevState& s, cudaStream_t st);
 void launch_score(const DevParams& p, const DevState& s, int log_idx, cudaStream_t st);
 void launch_score_reduce(const DevParams& p, const DevState& s, cudaStream_t st);
 void launch_meanshift(const DevParams& p, const DevState& s, int t, cudaStream_t st);
