@@ -96,7 +96,7 @@ constexpr int kTcM = 128;                        // output pixels per row strip 
 constexpr int kTcCols = kTcM + 2;                // input columns per row slot
 constexpr int kTcRowBytes = 2176;                // one channel block of a slot: 130 x 16 B, padded to 128 B
 constexpr int kTcSlots = 6;                      // input-row ring slots
-constexpr int kTcAcc = 4;                        // TMEM accumulators (output rows in flight)
+constexpr int kTcAcc = 8;                        // TMEM accumulator slots (output rows in flight)
 constexpr int kTcCtasPerSm = 2;
 constexpr int kTcRows = 16;                      // output rows per work item
 constexpr int kTcThreads = 192;
@@ -107,8 +107,8 @@ struct TcShape {
     static constexpr int kCB = CIN / 8;                          // channel blocks
     static constexpr int kSlotBytes = kCB * kTcRowBytes;
     static constexpr int kSlotTxBytes = kCB * kTcCols * 16;         // bytes the row's TMA boxes deliver
-    static constexpr int kKSteps = 9 * CIN / 16;                 // MMAs per output row
-    static constexpr int kWStepBytes = N * 16 * 2;               // one K step of B
+    static constexpr int kKSteps = 3 * CIN / 16;                 // K steps per input row (kx, channel pairs)
+    static constexpr int kWStepBytes = 3 * N * 16 * 2;           // one K step of B: the three ky blocks
     static constexpr int kRingBytes = kTcSlots * kSlotBytes;
     static constexpr int kWBytes = kKSteps * kWStepBytes;
     // ring | weights | barriers: full[slots] empty[slots] acc_full[acc] acc_empty[acc] done |
@@ -117,9 +117,13 @@ struct TcShape {
     static constexpr int kBarBytes = ((2 * kTcSlots + 2 * kTcAcc + 1) * 8 + 15) / 16 * 16;
     static constexpr int kSmemBytes = kBarOff + kBarBytes + 16;
     static constexpr int kTmemCols = kTcAcc * N <= 32 ? 32 : (kTcAcc * N <= 64 ? 64 : (kTcAcc * N <= 128 ? 128 : 256));
-    static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-                                       ((uint32_t)(kTcM >> 4) << 24);
 };
+
+// Instruction descriptor of an M = 128, N = n, BF16 x BF16 -> FP32 MMA, both operands K-major.
+__host__ __device__ constexpr uint32_t tc_idesc(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+}
 
 __device__ __forceinline__ void tc_mbar_init(uint32_t bar, uint32_t count)
 {
@@ -230,6 +234,17 @@ __device__ __forceinline__ TcItem tc_item(int i, int H, int W)
     return t;
 }
 
+// Zero 8 * X consecutive TMEM columns of the warp's 32 lanes.
+template <int X>
+__device__ __forceinline__ void tc_zero(uint32_t taddr)
+{
+    const uint32_t z = 0u;
+#pragma unroll
+    for (int i = 0; i < X; ++i)
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr + 8 * i), "r"(z)
+                     : "memory");
+}
+
 template <int CIN, int N>
 __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_conv_tc(const __grid_constant__ CUtensorMap tin, ConvArgs a)
 {
@@ -244,15 +259,16 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_conv_tc(const __gr
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_items = a.B * ((a.H + kTcRows - 1) / kTcRows) * ((a.W + kTcM - 1) / kTcM);
 
-    // weights -> B operand layout: [K step][n group][k half][8 rows][8 channels]
-    for (int i = threadIdx.x; i < N * 9 * (CIN / 8); i += blockDim.x) {
-        const int n = i / (9 * (CIN / 8)), rem = i % (9 * (CIN / 8));
-        const int tap = rem / (CIN / 8), cb = rem % (CIN / 8);
+    // weights -> B operand layout: [K step][n group][k half][8 rows][8 channels] with
+    // K step s = kx * (CIN / 16) + cp and n = blk * N + co, blk = 2 - ky
+    for (int i = threadIdx.x; i < S::kKSteps * 3 * N * 2; i += blockDim.x) {
+        const int st = i / (3 * N * 2), rem = i % (3 * N * 2);
+        const int n = rem >> 1, kh = rem & 1;
+        const int kx = st / (CIN / 16), cp = st % (CIN / 16);
+        const int co = n % N, ky = 2 - n / N;
         uint4 v = make_uint4(0, 0, 0, 0);
-        if (n < a.w_rows) v = *reinterpret_cast<const uint4*>(a.w + ((size_t)n * 9 + tap) * CIN + cb * 8);
-        const int step = tap * (CIN / 16) + cb / 2;
-        const uint32_t off = step * S::kWStepBytes + (n >> 3) * 256 + (cb & 1) * 128 + (n & 7) * 16;
-        *reinterpret_cast<uint4*>(smem + S::kRingBytes + off) = v;
+        if (co < a.w_rows) v = *reinterpret_cast<const uint4*>(a.w + ((size_t)co * 9 + ky * 3 + kx) * CIN + cp * 16 + kh * 8);
+        *reinterpret_cast<uint4*>(smem + S::kRingBytes + st * S::kWStepBytes + (n >> 3) * 256 + kh * 128 + (n & 7) * 16) = v;
     }
     if (threadIdx.x == 0) {
         for (int i = 0; i < kTcSlots; ++i) {
@@ -277,6 +293,13 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_conv_tc(const __gr
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
+    if (warp < 4) {                                   // every accumulator slot starts at zero
+        tc_zero<kTcAcc * N / 8>(tmem + ((uint32_t)(warp * 32) << 16));
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
     if (warp == 4) {
         if (lane == 0) {
@@ -301,43 +324,42 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_conv_tc(const __gr
         }
     } else if (warp == 5) {
         if (lane == 0) {
-            // MMA issuer
-            uint32_t ld = 0, orow = 0;
+            // MMA issuer: tick k of an item consumes input row y0 - 1 + k (all three
+            // kx shifts, N = 3 N columns: ky = 2, 1, 0 for output rows k - 2, k - 1,
+            // k of the item), so output row j accumulates ky = 0, 1, 2 over ticks
+            // j, j + 1, j + 2; output row g of the CTA's work sits in TMEM slot
+            // g % kTcAcc, zeroed by the epilogue after it reads it out
+            uint32_t ld = 0, G = 0;
             for (int it = blockIdx.x; it < n_items && !bad; it += gridDim.x) {
                 const TcItem t = tc_item(it, a.H, a.W);
-                const uint32_t L0 = ld;
-                if (!tc_wait(full + 8 * (L0 % kTcSlots), (L0 / kTcSlots) & 1, &bad)) break;
-                if (!tc_wait(full + 8 * ((L0 + 1) % kTcSlots), ((L0 + 1) / kTcSlots) & 1, &bad)) break;
-                for (int k = 0; k < t.rows; ++k, ++orow) {
-                    const uint32_t li = L0 + k + 2;
-                    if (!tc_wait(full + 8 * (li % kTcSlots), (li / kTcSlots) & 1, &bad)) break;
-                    const uint32_t buf = orow % kTcAcc;
-                    if (orow >= kTcAcc && !tc_wait(acc_empty + 8 * buf, ((orow / kTcAcc) - 1) & 1, &bad)) break;
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t d = tmem + buf * N;
-                    uint32_t acc = 0;
-#pragma unroll
-                    for (int ky = 0; ky < 3; ++ky) {
-                        const uint32_t row = ring + ((L0 + k + ky) % kTcSlots) * S::kSlotBytes;
-#pragma unroll
-                        for (int kx = 0; kx < 3; ++kx)
-#pragma unroll
-                            for (int cp = 0; cp < CIN / 16; ++cp) {
-                                const int step = (ky * 3 + kx) * (CIN / 16) + cp;
-                                const uint64_t ad = tc_desc(row + cp * 2 * kTcRowBytes + kx * 16, kTcRowBytes, 128);
-                                const uint64_t bd = tc_desc(wsm + step * S::kWStepBytes, 128, 256);
-                                tc_mma(d, ad, bd, S::kIdesc, acc);
-                                acc = 1;
-                            }
+                for (int k = 0; k < t.rows + 2; ++k, ++ld) {
+                    const uint32_t slot = ld % kTcSlots;
+                    if (!tc_wait(full + 8 * slot, (ld / kTcSlots) & 1, &bad)) break;
+                    const int b0 = max(0, 2 - k), b1 = min(3, t.rows - k + 2);
+                    if (b1 == 3) {                               // first contribution to row k
+                        const uint32_t gn = G + k;
+                        if (gn >= kTcAcc && !tc_wait(acc_empty + 8 * (gn % kTcAcc), ((gn / kTcAcc) - 1) & 1, &bad)) break;
                     }
-                    tc_commit(acc_full + 8 * buf);
-                    tc_commit(empty + 8 * ((L0 + k) % kTcSlots));           // input row y - 1 is done
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t g0 = G + k - 2 + b0;
+                    const int s0 = g0 % kTcAcc, nb = b1 - b0, nb1 = min(nb, kTcAcc - s0);
+                    const uint32_t d1 = tmem + s0 * N, i1 = tc_idesc(nb1 * N), i2 = tc_idesc((nb - nb1) * N);
+                    const uint32_t row = ring + slot * S::kSlotBytes;
+#pragma unroll
+                    for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+                        for (int cp = 0; cp < CIN / 16; ++cp) {
+                            const int st = kx * (CIN / 16) + cp;
+                            const uint64_t ad = tc_desc(row + cp * 2 * kTcRowBytes + kx * 16, kTcRowBytes, 128);
+                            const uint32_t bb = wsm + st * S::kWStepBytes + b0 * N * 32;
+                            tc_mma(d1, ad, tc_desc(bb, 128, 256), i1, 1u);
+                            if (nb1 < nb) tc_mma(tmem, ad, tc_desc(bb + nb1 * N * 32, 128, 256), i2, 1u);
+                        }
+                    tc_commit(empty + 8 * slot);                 // the input row is free once these are done
+                    if (b0 == 0) tc_commit(acc_full + 8 * ((G + k - 2) % kTcAcc));   // row k - 2 complete
                 }
                 if (bad) break;
-                // the item's last two input rows
-                tc_commit(empty + 8 * ((L0 + t.rows) % kTcSlots));
-                tc_commit(empty + 8 * ((L0 + t.rows + 1) % kTcSlots));
-                ld = L0 + t.rows + 2;
+                G += t.rows;
             }
             tc_commit(done);                  // arrives once every MMA issued above has completed
             for (long long i = 0; i < kTcWaitLimit; ++i)
@@ -348,18 +370,21 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm) k_conv_tc(const __gr
         float bias[N];
 #pragma unroll
         for (int n = 0; n < N; ++n) bias[n] = a.bias ? __ldg(a.bias + n) : 0.f;
-        uint32_t orow = 0;
+        uint32_t g = 0;
         bool go = true;
         for (int it = blockIdx.x; it < n_items && go; it += gridDim.x) {
             const TcItem t = tc_item(it, a.H, a.W);
-            for (int k = 0; k < t.rows; ++k, ++orow) {
-                const uint32_t buf = orow % kTcAcc;
+            for (int k = 0; k < t.rows; ++k, ++g) {
+                const uint32_t buf = g % kTcAcc;
                 // every lane polls; the warp proceeds only together (tcgen05.ld is warp-wide)
-                go = __all_sync(0xffffffffu, tc_wait(acc_full + 8 * buf, (orow / kTcAcc) & 1, &bad));
+                go = __all_sync(0xffffffffu, tc_wait(acc_full + 8 * buf, (g / kTcAcc) & 1, &bad));
                 if (!go) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 float v[N];
-                tc_ld<N>(tmem + ((uint32_t)(warp * 32) << 16) + buf * N, v);
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + buf * N;
+                tc_ld<N>(taddr, v);
+                tc_zero<N / 8>(taddr);
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 tc_arrive(acc_empty + 8 * buf);
                 const int px = t.x0 + warp * 32 + lane, py = t.y0 + k;
