@@ -744,15 +744,30 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const __grid_constant__
 // partials in a fixed order.
 constexpr int kNormBlocks = 64;
 
+__device__ __forceinline__ float flow_mag(float2 f)
+{
+    const float m = sqrtf(f.x * f.x + f.y * f.y);
+    return isfinite(m) ? m : 0.f;
+}
+
+// Partial sums of |flow| per (image, frame): grid (kNormBlocks, B*T). Eight
+// independent loads in flight per thread (a plain strided loop keeps one, too
+// few bytes in flight for the HBM bandwidth), added in index order.
 __global__ void k_flow_norm_sum(const void* flows, int f16, size_t N, float* partial)
 {
     const int bt = blockIdx.y;
+    const size_t stride = (size_t)gridDim.x * blockDim.x, base = (size_t)bt * N;
     float s = 0.f;
-    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
-        const float2 f = load_flow(flows, f16, (size_t)bt * N + p);
-        const float m = sqrtf(f.x * f.x + f.y * f.y);
-        s += isfinite(m) ? m : 0.f;
+    size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int kU = 8;
+    for (; p + (kU - 1) * stride < N; p += kU * stride) {
+        float2 f[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) f[u] = load_flow(flows, f16, base + p + u * stride);
+#pragma unroll
+        for (int u = 0; u < kU; ++u) s += flow_mag(f[u]);
     }
+    for (; p < N; p += stride) s += flow_mag(load_flow(flows, f16, base + p));
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     __shared__ float ws[32];
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
@@ -764,32 +779,35 @@ __global__ void k_flow_norm_sum(const void* flows, int f16, size_t N, float* par
     }
 }
 
-// One warp per (image, frame): sums[bt] = sum of the kNormBlocks partials.
-__global__ void k_flow_norm_fold(const float* partial, float* sums)
+// One warp per (image, frame): the frame's |flow| sum from the kNormBlocks
+// partials, stored as the scale of the network input, N / sum = 1 / mean |flow|
+// (0 for a frame without motion).
+__global__ void k_flow_norm_fold(const float* partial, float N, float* inv)
 {
     const int bt = blockIdx.x;
     float s = partial[(size_t)bt * kNormBlocks + threadIdx.x] + partial[(size_t)bt * kNormBlocks + threadIdx.x + 32];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (threadIdx.x == 0) sums[bt] = s;
+    if (threadIdx.x == 0) inv[bt] = s > 0.f ? N / s : 0.f;
 }
 
-__global__ void k_pack_input(const void* flows, int f16, int T, int H, int W, int B, const float* sums, bf16* in0)
+// grid (pixel blocks, B): pixel p of image b -> 16 bf16 channels (2T scaled flows, then zeros)
+__global__ void k_pack_input(const void* flows, int f16, int T, int N, const float* inv, bf16* in0)
 {
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t N = (size_t)H * W;
-    if (i >= N * B) return;
-    const size_t b = i / N, p = i % N;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (p >= N) return;
+    const int Tc = T < 8 ? T : 8;
+    float2 f[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+        if (t < Tc) f[t] = load_flow(flows, f16, ((size_t)b * T + t) * N + p);
     __align__(16) bf16 v[16];
-    for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(0.f);
-    for (int t = 0; t < T && t < 8; ++t) {
-        const size_t idx = (b * T + t) * N + p;
-        const float2 f = load_flow(flows, f16, idx);
-        const float s = sums[b * T + t];
-        const float inv = s > 0.f ? (float)N / s : 0.f;       // 1 / mean |flow| of the frame
-        v[2 * t] = __float2bfloat16_rn(f.x * inv);
-        v[2 * t + 1] = __float2bfloat16_rn(f.y * inv);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const float sc = t < Tc ? inv[b * T + t] : 0.f;
+        v[2 * t] = __float2bfloat16_rn(t < Tc ? f[t].x * sc : 0.f);
+        v[2 * t + 1] = __float2bfloat16_rn(t < Tc ? f[t].y * sc : 0.f);
     }
-    uint4* o = reinterpret_cast<uint4*>(in0 + i * 16);
+    uint4* o = reinterpret_cast<uint4*>(in0 + ((size_t)b * N + p) * 16);
     o[0] = *reinterpret_cast<uint4*>(v);
     o[1] = *reinterpret_cast<uint4*>(v + 8);
 }
@@ -993,7 +1011,7 @@ struct voldor_net {
     float* align = nullptr;          // [8] scale alignment state
     int* tc_err = nullptr;           // set by a convolution whose bounded wait expired
     unsigned* hist = nullptr;        // [2][kAlignBins]
-    float* fsum = nullptr;           // [cap_bt] sum of |flow| per (image, frame), then [cap_bt][kNormBlocks] partials
+    float* fsum = nullptr;           // [cap_bt] input scale N / sum |flow| per (image, frame), then [cap_bt][kNormBlocks] partials
     size_t cap_bt = 0;
     int step = 0;
     size_t cap_pix = 0;
@@ -1066,12 +1084,11 @@ bool conv(int cin_pad, int n_out_pad, const ConvArgs& a, cudaStream_t st)
 // False if a convolution could not be launched.
 bool forward(voldor_net* n, const void* flows, int f16, int B, int H, int W, cudaStream_t st)
 {
-    const size_t pix = (size_t)B * H * W;
     const size_t N = (size_t)H * W;
     float* partial = n->fsum + n->cap_bt;
     k_flow_norm_sum<<<dim3(kNormBlocks, B * n->T), 256, 0, st>>>(flows, f16, N, partial);
-    k_flow_norm_fold<<<B * n->T, 32, 0, st>>>(partial, n->fsum);
-    k_pack_input<<<(unsigned)((pix + 255) / 256), 256, 0, st>>>(flows, f16, n->T, H, W, B, n->fsum, n->in0);
+    k_flow_norm_fold<<<B * n->T, 32, 0, st>>>(partial, (float)N, n->fsum);
+    k_pack_input<<<dim3((unsigned)((N + 255) / 256), B), 256, 0, st>>>(flows, f16, n->T, (int)N, n->fsum, n->in0);
     const bf16* in = n->in0;
     int cin_g = 16;
     for (int l = 0; l < kNetLayers; ++l) {
@@ -1252,7 +1269,8 @@ voldor_status voldor_net_get_grads(voldor_net* n, float* host, size_t count)
 voldor_status voldor_net_forward(voldor_net* n, const void* flows, int flow_dtype, int B, int H, int W, float* pred,
                                  void* stream)
 {
-    if (!n || !flows || !pred || B < 1 || H < 1 || W < 1 || (size_t)B * n->T > 65535) return VOLDOR_ERR_INVALID_ARG;
+    if (!n || !flows || !pred || B < 1 || H < 1 || W < 1 || (size_t)B * n->T > 65535 || (size_t)H * W > 0x7fffffff)
+        return VOLDOR_ERR_INVALID_ARG;
     if (flow_dtype != VOLDOR_FLOW_F32 && flow_dtype != VOLDOR_FLOW_F16) return VOLDOR_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     voldor_status s = net_reserve(n, (size_t)B * H * W, (size_t)B * n->T);
@@ -1266,7 +1284,8 @@ voldor_status voldor_net_forward(voldor_net* n, const void* flows, int flow_dtyp
 voldor_status voldor_net_train_step(voldor_net* n, const void* flows, int flow_dtype, const float* target, int B, int H,
                                     int W, float lr, float lam_r, float* loss_host, void* stream)
 {
-    if (!n || !flows || !target || B < 1 || H < 1 || W < 1 || (size_t)B * n->T > 65535 || !(lr >= 0.f))
+    if (!n || !flows || !target || B < 1 || H < 1 || W < 1 || (size_t)B * n->T > 65535 || (size_t)H * W > 0x7fffffff ||
+        !(lr >= 0.f))
         return VOLDOR_ERR_INVALID_ARG;
     if (flow_dtype != VOLDOR_FLOW_F32 && flow_dtype != VOLDOR_FLOW_F16) return VOLDOR_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
