@@ -760,14 +760,14 @@ __global__ void k_flow_norm_sum(const void* flows, int f16, size_t N, float* par
     float s = 0.f;
     size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     constexpr int kU = 8;
-    for (; p + (kU - 1) * stride < N; p += kU * stride) {
+    for (; p < N; p += kU * stride) {               // the last round predicated, not a serial tail
         float2 f[kU];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) f[u] = load_flow(flows, f16, base + p + u * stride);
+        for (int u = 0; u < kU; ++u)
+            f[u] = p + u * stride < N ? load_flow(flows, f16, base + p + u * stride) : make_float2(0.f, 0.f);
 #pragma unroll
         for (int u = 0; u < kU; ++u) s += flow_mag(f[u]);
     }
-    for (; p < N; p += stride) s += flow_mag(load_flow(flows, f16, base + p));
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     __shared__ float ws[32];
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;

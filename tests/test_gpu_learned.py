@@ -1,22 +1,32 @@
 """The learned proposal end to end at a small size (256x192, f = 210, T = 4):
 plain-EM labels, training with the library's kernels, and the learned
 initialisation against the plain one on held-out windows."""
+import os
+
 import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
 
 SIZE = dict(W=256, H=192, f=210.0, T=4)
+# Training is not bit-reproducible (the weight gradients are summed with FP32
+# atomics), and the plain EM's median error is flat within a few percent from
+# its third iteration on: 96 training windows and 16 held-out ones made the
+# outcome vary between runs of the same build. These sizes average both out.
+N_TRAIN, TRAIN_STEPS, N_HELD = 256, 4000, 48
 
 
 @pytest.fixture(scope="module")
 def trained():
     from paper_2104_06789_gb300 import build, learned, voldor
     build.build()
-    ds = learned.build_dataset([learned.TRAIN_SEED0 + i for i in range(96)], S=1024, label_iters=5, **SIZE)
+    workers = max(1, min(8, (os.cpu_count() or 2) - 1))
+    ds = learned.build_dataset([learned.TRAIN_SEED0 + i for i in range(N_TRAIN)], S=1024, label_iters=5,
+                               workers=workers, **SIZE)
     net = voldor.Net(SIZE["T"], learned.init_weights(SIZE["T"], seed=0))
-    losses = learned.train(net, ds, 2000, batch=4, lr=2e-3)
-    held = learned.build_dataset([learned.HELDOUT_SEED0 + i for i in range(16)], label_iters=0, **SIZE)
+    losses = learned.train(net, ds, TRAIN_STEPS, batch=4, lr=2e-3)
+    held = learned.build_dataset([learned.HELDOUT_SEED0 + i for i in range(N_HELD)], label_iters=0, workers=workers,
+                                 **SIZE)
     res = learned.compare(net, held, S=1024, max_iters=6, plain_iters=5,
                           K=(SIZE["f"], SIZE["f"], (SIZE["W"] - 1) / 2.0, (SIZE["H"] - 1) / 2.0))
     yield losses, res
