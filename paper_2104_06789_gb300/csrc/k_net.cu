@@ -504,6 +504,8 @@ struct WgradArgs {
     int cout_g;
     float* dw;              // [n_out][9][cin_real]
     float* db;              // [n_out]
+    float* part;            // [gridDim.x][9 CIN + 1][NCO] each CTA's sums
+    float* part2;           // [ceil(gridDim.x / kWgGroup)][9 CIN + 1][NCO] their group sums
     int n_out, cin_real;
     int H, W, B;
     int* err;               // set to 1 if a bounded wait expired
@@ -535,6 +537,8 @@ struct WgradArgs {
 // ---------------------------------------------------------------------------
 constexpr int kWgKP = 64;                                 // pixels per work item (K)
 constexpr int kWgThreads = 128;
+constexpr int kWgCtasPerSm = 3;                          // weight-gradient grid: at most this many CTAs per SM
+constexpr int kWgPartRows = 9 * 32 + 1;                   // largest per-CTA partial: rows x 32 columns
 
 template <int CIN, int NCO>
 struct WgShape {
@@ -712,18 +716,21 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const __grid_constant__
     }
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!bad && local > 0) {
+    if (!bad) {
+        // this CTA's sums, row m (tap * CIN + ci, then the bias row) of its partial
 #pragma unroll
         for (int mt = 0; mt < S::kMT; ++mt) {
             float v[NCO];
             tc_ld<NCO>(tmem + ((uint32_t)(warp * 32) << 16) + mt * NCO, v);
+            if (local == 0) {
+#pragma unroll
+                for (int co = 0; co < NCO; ++co) v[co] = 0.f;
+            }
             const int m = mt * 128 + warp * 32 + lane;
-            if (m < 9 * CIN) {
-                const int tap = m / CIN, ci = m % CIN;
-                if (ci < a.cin_real)
-                    for (int co = 0; co < a.n_out; ++co) atomicAdd(a.dw + ((size_t)co * 9 + tap) * a.cin_real + ci, v[co]);
-            } else if (m == 9 * CIN) {
-                for (int co = 0; co < a.n_out; ++co) atomicAdd(a.db + co, v[co]);
+            if (m < S::kRows) {
+                float4* o = reinterpret_cast<float4*>(a.part + ((size_t)blockIdx.x * S::kRows + m) * NCO);
+#pragma unroll
+                for (int q = 0; q < NCO / 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
             }
         }
     }
@@ -734,6 +741,50 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const __grid_constant__
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)S::kTmemCols));
     }
     if (tid == 0 && bad) atomicExch(a.err, 1);
+}
+
+// The layer's gradients from the CTAs' partial sums, in a fixed order (so
+// that a training run is bit-reproducible, unlike with floating-point
+// atomics), in two levels: k_wgrad_group sums groups of kWgGroup consecutive
+// CTAs (grid.y = group), k_wgrad_reduce the groups in order and writes
+// dw[co][tap][ci] (row m = tap * CIN + ci) or db[co] (m = 9 CIN). Entry
+// i = m * NCO + co.
+constexpr int kWgGroup = 16;
+
+template <int CIN, int NCO>
+__global__ void k_wgrad_group(const float* part, int n_cta, float* part2)
+{
+    constexpr int R = 9 * CIN + 1;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, g = blockIdx.y;
+    if (i >= R * NCO) return;
+    const size_t cs = (size_t)R * NCO;
+    const int c0 = g * kWgGroup, c1 = min(n_cta, c0 + kWgGroup);
+    float v[kWgGroup];
+#pragma unroll
+    for (int u = 0; u < kWgGroup; ++u) v[u] = c0 + u < c1 ? part[(size_t)(c0 + u) * cs + i] : 0.f;
+    float sum = 0.f;
+#pragma unroll
+    for (int u = 0; u < kWgGroup; ++u) sum += v[u];
+    part2[(size_t)g * cs + i] = sum;
+}
+
+template <int CIN, int NCO>
+__global__ void k_wgrad_reduce(const float* part2, int n_groups, float* dw, float* db, int n_out, int cin_real)
+{
+    constexpr int R = 9 * CIN + 1;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= R * NCO) return;
+    const int m = i / NCO, co = i % NCO;
+    if (co >= n_out) return;
+    const size_t cs = (size_t)R * NCO;
+    float sum = 0.f;
+    for (int g = 0; g < n_groups; ++g) sum += part2[(size_t)g * cs + i];
+    if (m < 9 * CIN) {
+        const int tap = m / CIN, ci = m % CIN;
+        if (ci < cin_real) dw[((size_t)co * 9 + tap) * cin_real + ci] = sum;
+    } else {
+        db[co] = sum;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1020,11 +1071,23 @@ struct voldor_net {
     float* pred = nullptr;          // [pix][8]
     bf16* g16 = nullptr;            // [pix][16] gradient at the output
     bf16 *ga = nullptr, *gb = nullptr;   // [pix][32] gradient ping-pong
+    float* wpart = nullptr;         // weight-gradient partial sums: [kWgCtasPerSm * SMs][kWgPartRows][32],
+                                    // then their group sums (the same layout, one entry per group of CTAs)
 };
 
 namespace {
 
 bool net_ok(cudaError_t e) { return e == cudaSuccess; }
+
+// SM count of the current device (the weight-gradient grid is sized by it).
+int net_sms()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms <= 0)
+        return 152;
+    return sms;
+}
 
 void net_free_acts(voldor_net* n)
 {
@@ -1129,8 +1192,12 @@ static bool launch_wgrad_tc(const WgradArgs& a, cudaStream_t st)
         sms = g_tc_sms[dev];
     }
     const int items = a.B * a.H * ((a.W + kWgKP - 1) / kWgKP);
-    const int grid = std::min(items, 3 * sms);
+    const int grid = std::min(items, kWgCtasPerSm * sms);
     k_wgrad_tc<CIN, NCO><<<grid, kWgThreads, S::kSmemBytes, st>>>(a);
+    const int n_groups = (grid + kWgGroup - 1) / kWgGroup;
+    const unsigned blocks = (unsigned)((S::kRows * NCO + 255) / 256);
+    k_wgrad_group<CIN, NCO><<<dim3(blocks, n_groups), 256, 0, st>>>(a.part, grid, a.part2);
+    k_wgrad_reduce<CIN, NCO><<<blocks, 256, 0, st>>>(a.part2, n_groups, a.dw, a.db, a.n_out, a.cin_real);
     return true;
 }
 
@@ -1139,6 +1206,8 @@ void wgrad(voldor_net* n, int l, const bf16* in, int cin_g, const bf16* dout, in
     WgradArgs a{};
     a.in = in; a.cin_g = cin_g; a.dout = dout; a.cout_g = cout_g;
     a.dw = n->grad + n->L.w_off[l]; a.db = n->grad + n->L.b_off[l];
+    a.part = n->wpart;
+    a.part2 = n->wpart + (size_t)kWgCtasPerSm * net_sms() * kWgPartRows * 32;
     a.n_out = n->L.cout[l]; a.cin_real = n->L.cin[l];
     a.H = H; a.W = W; a.B = B;
     a.err = n->tc_err;
@@ -1216,6 +1285,8 @@ voldor_status voldor_net_create(int T, voldor_net** out)
               net_ok(cudaMalloc(&n->grad, P * 4)) && net_ok(cudaMalloc(&n->fw, n->L.n_fw * sizeof(bf16))) &&
               net_ok(cudaMalloc(&n->bw, n->L.n_bw * sizeof(bf16))) && net_ok(cudaMalloc(&n->fbias, kNetLayers * kNetWidth * 4)) &&
               net_ok(cudaMalloc(&n->loss, 4)) && net_ok(cudaMalloc(&n->align, 8 * sizeof(float))) &&
+              net_ok(cudaMalloc(&n->wpart, (size_t)(kWgCtasPerSm * net_sms() + (kWgCtasPerSm * net_sms() + 15) / 16) *
+                                               kWgPartRows * 32 * sizeof(float))) &&
               net_ok(cudaMalloc(&n->hist, 2 * kAlignBins * sizeof(unsigned))) && net_ok(cudaMalloc(&n->tc_err, sizeof(int)));
     if (ok) ok = net_ok(cudaMemset(n->master, 0, P * 4)) && net_ok(cudaMemset(n->m, 0, P * 4)) &&
                  net_ok(cudaMemset(n->v, 0, P * 4)) && net_ok(cudaMemset(n->grad, 0, P * 4)) &&
@@ -1236,7 +1307,7 @@ void voldor_net_destroy(voldor_net* n)
     net_free_acts(n);
     cudaFree(n->master); cudaFree(n->m); cudaFree(n->v); cudaFree(n->grad);
     cudaFree(n->fw); cudaFree(n->bw); cudaFree(n->fbias); cudaFree(n->loss);
-    cudaFree(n->align); cudaFree(n->hist); cudaFree(n->fsum); cudaFree(n->tc_err);
+    cudaFree(n->align); cudaFree(n->hist); cudaFree(n->fsum); cudaFree(n->tc_err); cudaFree(n->wpart);
     cudaGetLastError();
     delete n;
 }

@@ -241,3 +241,27 @@ def test_gradients_batch_consistency(vd):
     for (key, a), (_, r) in zip(_blocks(T, g), _blocks(T, mean)):
         assert _rel(a, r) < 1e-3, (key, _rel(a, r))
     net.destroy()
+
+
+def test_gradients_are_reproducible(vd):
+    """The weight gradients are sums over hundreds of CTAs' partials, added in
+    CTA order: two identical training steps give bit-identical gradients, and
+    training from the same start gives bit-identical weights."""
+    import torch
+    T, H, W = 2, 375, 1242
+    rng = np.random.default_rng(9)
+    params = cn.he_init(T, seed=9) + rng.normal(0, 0.02, size=cn.he_init(T, seed=9).shape).astype(np.float32)
+    flows = rng.normal(0, 12.0, size=(2, T, H, W, 2)).astype(np.float32)
+    target = np.stack([rng.normal(1.5, 0.5, size=(2, H, W)), rng.uniform(0, 1, size=(2, H, W))], -1).astype(np.float32)
+    f, t = torch.from_numpy(flows).cuda(), torch.from_numpy(target).cuda()
+    grads, weights = [], []
+    for _ in range(2):
+        net = vd.Net(T, params)
+        net.train_step(f, t, lr=0.0, lam_r=0.5)
+        grads.append(net.get_grads())
+        for _ in range(3):
+            net.train_step(f, t, lr=1e-3, lam_r=0.5)
+        weights.append(net.get_weights())
+        net.destroy()
+    assert np.array_equal(grads[0], grads[1])
+    assert np.array_equal(weights[0], weights[1])
