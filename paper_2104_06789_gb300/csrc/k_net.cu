@@ -1143,9 +1143,10 @@ bool conv(int cin_pad, int n_out_pad, const ConvArgs& a, cudaStream_t st)
     return false;
 }
 
-// Forward pass of B images of H x W; predictions in n->pred (8 floats per pixel).
+// Forward pass of B images of H x W; predictions (8 floats per pixel) in
+// `out`, a 16-byte aligned device buffer, or in n->pred when out is null.
 // False if a convolution could not be launched.
-bool forward(voldor_net* n, const void* flows, int f16, int B, int H, int W, cudaStream_t st)
+bool forward(voldor_net* n, const void* flows, int f16, int B, int H, int W, cudaStream_t st, float* out = nullptr)
 {
     const size_t N = (size_t)H * W;
     float* partial = n->fsum + n->cap_bt;
@@ -1158,7 +1159,7 @@ bool forward(voldor_net* n, const void* flows, int f16, int B, int H, int W, cud
         const bool last = l == kNetLayers - 1;
         ConvArgs a{};
         a.in = in; a.cin_g = cin_g; a.w = n->fw + n->L.fw_off[l]; a.bias = n->fbias + l * kNetWidth;
-        a.out = last ? nullptr : n->act[l]; a.out_f = last ? n->pred : nullptr;
+        a.out = last ? nullptr : n->act[l]; a.out_f = last ? (out ? out : n->pred) : nullptr;
         a.cout_g = last ? 8 : 32; a.n_out = last ? 8 : 32; a.mask = nullptr; a.relu = last ? 0 : 1; a.H = H; a.W = W;
         a.B = B; a.w_rows = n->L.cout_pad[l]; a.err = n->tc_err;
         if (!conv(n->L.cin_pad[l], last ? 16 : 32, a, st)) return false;
@@ -1346,8 +1347,20 @@ voldor_status voldor_net_forward(voldor_net* n, const void* flows, int flow_dtyp
     cudaStream_t st = (cudaStream_t)stream;
     voldor_status s = net_reserve(n, (size_t)B * H * W, (size_t)B * n->T);
     if (s != VOLDOR_OK) return s;
-    if (!forward(n, flows, flow_dtype == VOLDOR_FLOW_F16, B, H, W, st)) return VOLDOR_ERR_CUDA;
-    if (!net_ok(cudaMemcpyAsync(pred, n->pred, (size_t)B * H * W * 8 * sizeof(float), cudaMemcpyDeviceToDevice, st)))
+    // The last layer writes the caller's buffer directly when the epilogue's
+    // 16-byte stores can reach it (device memory, 16-byte aligned); otherwise
+    // it writes the network's own buffer, which is then copied.
+    cudaPointerAttributes pa{};
+    bool direct = false;
+    if (((uintptr_t)pred & 15) == 0) {
+        if (cudaPointerGetAttributes(&pa, pred) == cudaSuccess)
+            direct = pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged;
+        else
+            cudaGetLastError();   // a failed attribute query is not an error of the forward pass
+    }
+    if (!forward(n, flows, flow_dtype == VOLDOR_FLOW_F16, B, H, W, st, direct ? pred : nullptr)) return VOLDOR_ERR_CUDA;
+    if (!direct &&
+        !net_ok(cudaMemcpyAsync(pred, n->pred, (size_t)B * H * W * 8 * sizeof(float), cudaMemcpyDeviceToDevice, st)))
         return VOLDOR_ERR_CUDA;
     return net_status(n, st);
 }

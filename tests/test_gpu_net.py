@@ -108,6 +108,30 @@ def test_forward_matches_reference(vd, T, H, W):
     net.destroy()
 
 
+def test_forward_into_unaligned_output(vd):
+    """The last layer writes the caller's buffer directly when it is 16-byte
+    aligned device memory, else the network's own buffer, which is copied:
+    both give the same predictions bit for bit."""
+    import ctypes
+
+    import torch
+    T, H, W = 2, 10, 37
+    params, flows, _ = _case(T, H, W, seed=3)
+    net = vd.Net(T, params)
+    fl = torch.from_numpy(flows[None]).cuda()
+    direct = net.forward(fl).cpu().numpy()
+    n = H * W * 8
+    buf = torch.full((n + 4,), -7.0, dtype=torch.float32, device="cuda")
+    assert buf.data_ptr() % 16 == 0
+    st = vd.lib().voldor_net_forward(net._h, ctypes.c_void_p(fl.data_ptr()), net._flow_dtype(fl), 1, H, W,
+                                     ctypes.c_void_p(buf.data_ptr() + 4), ctypes.c_void_p(0))
+    assert st == vd.OK
+    got = buf.cpu().numpy()
+    assert got[0] == -7.0 and np.all(got[n + 1:] == -7.0)
+    assert np.array_equal(got[1:n + 1].reshape(direct.shape), direct)
+    net.destroy()
+
+
 @pytest.mark.parametrize("T,H,W", [(2, 10, 37), (8, 9, 70), (5, 33, 41)])
 def test_gradients_match_reference(vd, T, H, W):
     import torch
