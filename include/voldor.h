@@ -368,7 +368,10 @@ voldor_status voldor_net_get_weights(voldor_net* net, float* host, size_t count)
 /* Gradient of the last voldor_net_train_step's loss (before its update). */
 voldor_status voldor_net_get_grads(voldor_net* net, float* host, size_t count);
 /* Forward pass on B images of H x W: flows device [B][T][H][W][2], pred device
- * [B][H][W][8] floats (channel 0 log-depth, 1 rigidness logit, rest zero). */
+ * [B][H][W][8] floats (channel 0 log-depth, 1 rigidness logit, rest zero).
+ * The last layer writes pred directly when it is 16-byte aligned memory of
+ * the current device, else the network's own buffer, copied to pred on the
+ * stream; the results are the same. Synchronises the stream. */
 voldor_status voldor_net_forward(voldor_net* net, const void* flows, int flow_dtype, int B, int H, int W, float* pred,
                                  void* cuda_stream);
 /* One training step: forward, loss = mean over pixels of Huber(delta 0.1) on

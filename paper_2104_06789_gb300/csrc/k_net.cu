@@ -1348,13 +1348,15 @@ voldor_status voldor_net_forward(voldor_net* n, const void* flows, int flow_dtyp
     voldor_status s = net_reserve(n, (size_t)B * H * W, (size_t)B * n->T);
     if (s != VOLDOR_OK) return s;
     // The last layer writes the caller's buffer directly when the epilogue's
-    // 16-byte stores can reach it (device memory, 16-byte aligned); otherwise
-    // it writes the network's own buffer, which is then copied.
+    // 16-byte stores can reach it (memory of the current device, 16-byte
+    // aligned); otherwise it writes the network's own buffer, which is then
+    // copied.
     cudaPointerAttributes pa{};
     bool direct = false;
-    if (((uintptr_t)pred & 15) == 0) {
+    int dev = -1;
+    if (((uintptr_t)pred & 15) == 0 && cudaGetDevice(&dev) == cudaSuccess) {
         if (cudaPointerGetAttributes(&pa, pred) == cudaSuccess)
-            direct = pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged;
+            direct = (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged) && pa.device == dev;
         else
             cudaGetLastError();   // a failed attribute query is not an error of the forward pass
     }
