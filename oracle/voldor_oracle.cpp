@@ -17,9 +17,10 @@
 // enumeration; P3P against the generating pose and a resultant computed by
 // sympy; se(3) exp against scipy's matrix exponential; geometry, bilinear
 // sampling and triangulation against noiseless synthetic scenes; the full loop
-// against the noiseless fixed point. No function here is "parity unpinned"
-// except the noisy full loop, whose randomised heuristics the paper does not
-// pin.
+// against the noiseless fixed point and, on a noisy window, against the scale
+// equivariance of monocular inference (scale taken from T_1). The paper does
+// not fix the noisy trajectory itself: it follows the readings of the
+// randomised steps listed with each function.
 
 #include <cmath>
 #include <cstdint>

@@ -488,6 +488,37 @@ def test_full_loop_noiseless_fixed_point(oracle_lib):
     assert np.max(np.abs(ow.theta - depth)) < 1e-12
 
 
+def test_full_loop_is_scale_equivariant(oracle_lib):
+    """A monocular window fixes the scene only up to scale, and the loop takes
+    its scale from T_1 (Sec. 5.3): on a noisy window, scaling T_1's
+    translation, the depth-sample range and the translation variance of the
+    pose kernel (a length squared, Eq. 18) by s = 2, 2 and 4 must scale every
+    depth and translation of two full iterations by exactly 2 and leave the
+    rotations and rigidness maps unchanged; only the meanshift's stopping test
+    on the mixed (translation, rotation) step is not scale-free, so poses and
+    rigidness agree to its tolerance. Unit-inconsistent arithmetic anywhere in
+    the loop (a variance read as a standard deviation, the translation and
+    rotation variances swapped: both checked by planting them) breaks it."""
+    from tests.helpers import small_window
+    w = small_window(seed=1000, W=48, H=36, f=36.0, T=3)
+    flows = w.flows.astype(np.float64)
+
+    def run(s):
+        T1 = w.poses[0].copy()
+        T1[:3, 3] *= s
+        ow = oracle_lib.OracleWindow(flows, w.K, S=64, inv_depth_min=w.inv_depth_range[0] / s,
+                                     inv_depth_max=w.inv_depth_range[1] / s, sigma_t=0.1 * s * s)
+        ow.bootstrap(T1)
+        assert ow.run(0, 2) == 0
+        return ow
+
+    a, b = run(1.0), run(2.0)
+    assert np.array_equal(b.theta, 2.0 * a.theta)
+    assert np.abs(b.poses[:, :3, 3] - 2.0 * a.poses[:, :3, 3]).max() < 1e-9
+    assert np.abs(b.poses[:, :3, :3] - a.poses[:, :3, :3]).max() < 1e-9
+    assert np.abs(b.wmap - a.wmap).max() < 1e-7
+
+
 # ---------------------------------------------------------------------------
 # MIE sweep: neighbour propagation (Fig. 5, Sec. 5.1)
 # ---------------------------------------------------------------------------
