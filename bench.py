@@ -637,119 +637,60 @@ def run_batch(args):
     error against the scenes' ground truth. Tuning is not timed."""
     import torch
 
-    from paper_2104_06789_gb300 import build, tuning, voldor
+    from paper_2104_06789_gb300 import build, tuning
     torch.cuda.set_device(0)
     build.build()
     wl = batch_workload(args.batch)
     S = 4096
-    stream = torch.cuda.Stream()
-
-    def make(tune_hyps):
-        wins, shapes, hyps = [], {}, {}
-        for i, (b, T) in enumerate(wl):
-            flows = np.ascontiguousarray(b.flows[:T].astype(np.float16))
-            p = voldor.default_params(hyps_per_frame=S, inv_depth_min=b.inv_depth_range[0],
-                                      inv_depth_max=b.inv_depth_range[1], window_id=i)
-            if tune_hyps:
-                s_win, _, _ = tuning.autotune_hyps(flows, b.K, p, b.poses[0], iters=args.iters)
-                p.hyps_per_frame, p.groups_per_frame = s_win, 4 * s_win
-            hyps[p.hyps_per_frame] = hyps.get(p.hyps_per_frame, 0) + 1
-            g = voldor.Window(flows, b.K, p)
-            g.bootstrap(b.poses[0])
-            hpt, ch, _ = g.autotune()
-            shapes[f"{hpt}x{ch}"] = shapes.get(f"{hpt}x{ch}", 0) + 1
-            wins.append((g, b, T))
-        return wins, shapes, hyps
-
-    def measure(wins):
-        def boot_all():
-            for g, b, T in wins:
-                g.bootstrap(b.poses[0])
-
-        batch = voldor.Batch([g for g, _, _ in wins], args.iters)
-        for _ in range(args.warmup):
-            boot_all()
-            batch.run(stream)
-        lat, walls = [], []
-        for _ in range(args.steps):
-            boot_all()
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            lat.extend(batch.run(stream).tolist())
-            e1.record(stream)
-            torch.cuda.synchronize()
-            walls.append(e0.elapsed_time(e1))
-        errs = []
-        for g, b, T in wins:
-            P, _, _ = g.get_pose_depth_rigidness(depth=False, rigidness=False)
-            errs.append(float(np.mean(np.linalg.norm(P[:, :3, 3] - b.poses[:T, :3, 3], axis=1))))
-        batch.destroy()
-        return float(np.median(walls)), lat, float(np.median(errs))
-
-    fixed, fixed_shapes, _ = make(False)
-    wall_f, _, err_f = measure(fixed)
-    for g, _, _ in fixed:
-        g.destroy()
-    wins, shapes, hyps = make(True)
-    wall, lat, err = measure(wins)
-    # the same windows one after another (em_step each), for comparison
-    seq = []
-    for _ in range(max(1, args.steps // 2)):
-        for g, b, _ in wins:
-            g.bootstrap(b.poses[0])
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for g, _, _ in wins:
-            g.em_step(args.iters)
-        torch.cuda.synchronize()
-        seq.append((time.perf_counter() - t0) * 1e3)
-    n = len(wins)
-    units = sum(b.H * b.W * T * args.iters for _, b, T in wins)
+    fixed, fixed_shapes, _ = _batch_windows(wl, S, args.iters, tune_hyps=False)
+    res_f = _batch_measure(fixed, args.iters, None, args.warmup, args.steps)
+    tuned, shapes, hyps = _batch_windows(wl, S, args.iters, tune_hyps=True)
+    res = _batch_measure(tuned, args.iters, None, args.warmup, args.steps)
+    n = len(wl)
     line = {"metric": "windows/s, mixed 320x240/640x480/1242x375 windows, T in [3,8], one CUDA graph",
-            "value": n / (wall / 1e3), "unit": "windows/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": wall, "higher_is_better": True, "data": "synthetic", "dtype": "f32",
+            "value": res["windows_per_s"], "unit": "windows/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["ms_per_batch"], "higher_is_better": True,
+            "data": "synthetic", "dtype": "f32",
             "config": {"workload": "batch_mixed", "windows": n, "em_iters": args.iters,
                        "hyps_per_frame": f"autotuned per window from {sorted(tuning.default_candidates(S) + [S])}",
-                       "flows": "fp16", "resolutions": sorted({f"{b.W}x{b.H}" for _, b, _ in wins})},
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "max": float(np.max(lat))},
-            "mpixel_frame_per_s": units / (wall / 1e3) / 1e6,
-            "autotuned_hyps": {str(k): v for k, v in sorted(hyps.items())}, "autotuned_shapes": shapes,
-            "median_translation_error_m": err,
-            "fixed_S4096": {"windows_per_s": n / (wall_f / 1e3), "ms_per_step": wall_f,
-                            "median_translation_error_m": err_f, "autotuned_shapes": fixed_shapes},
-            "sequential_em_step_ms": float(np.median(seq)), "batch_speedup_vs_sequential": float(np.median(seq)) / wall}
+                       "flows": "fp16", "resolutions": sorted({f"{b.W}x{b.H}" for b, _ in wl})},
+            "autotuned_hyps": hyps, "autotuned_shapes": shapes, **res,
+            "fixed_S4096": {"autotuned_shapes": fixed_shapes, **res_f}}
     print(json.dumps(line), flush=True)
-    for g, _, _ in wins:
-        g.destroy()
 
 
-def batch_summary(iters, pair_rate, warmup=2, steps=3, n=64, S=4096):
-    """Config 4 inside the default run: n windows of the mixed workload
-    (batch_workload) at a fixed S per frame, each window's dense-scoring tile
-    shape autotuned, in one CUDA graph; windows/s from the median batch wall
-    time, per-window latency p50/p99 from the graph's own events, and the
-    same windows one after another (em_step each) beside it. The batch's
-    dense-scoring pairs (hypotheses x valid pixels, read from every window's
-    scoring log) over `pair_rate` (the driving window's measured pairs/s)
-    give the time the scoring alone needs at full-GPU occupancy: a lower
-    bound for any batching of these windows with this scoring kernel."""
-    import torch
-
-    from paper_2104_06789_gb300 import voldor
-    wl = batch_workload(n)
-    stream = torch.cuda.Stream()
-    wins, shapes = [], {}
+def _batch_windows(wl, S, iters, tune_hyps):
+    """The windows of `wl` as library windows: each window's hypothesis count
+    autotuned (tuning.autotune_hyps, from S/8, S/4, S/2 and S) or fixed at S,
+    then its dense-scoring tile shape (voldor_autotune). Tuning is not timed."""
+    from paper_2104_06789_gb300 import tuning, voldor
+    wins, shapes, hyps = [], {}, {}
     for i, (b, T) in enumerate(wl):
         flows = np.ascontiguousarray(b.flows[:T].astype(np.float16))
         p = voldor.default_params(hyps_per_frame=S, inv_depth_min=b.inv_depth_range[0],
                                   inv_depth_max=b.inv_depth_range[1], window_id=i)
+        if tune_hyps:
+            s_win, _, _ = tuning.autotune_hyps(flows, b.K, p, b.poses[0], iters=iters)
+            p.hyps_per_frame, p.groups_per_frame = s_win, 4 * s_win
+        hyps[str(p.hyps_per_frame)] = hyps.get(str(p.hyps_per_frame), 0) + 1
         g = voldor.Window(flows, b.K, p)
         g.bootstrap(b.poses[0])
         hpt, ch, _ = g.autotune()
         shapes[f"{hpt}x{ch}"] = shapes.get(f"{hpt}x{ch}", 0) + 1
         wins.append((g, b, T))
+    return wins, shapes, dict(sorted(hyps.items(), key=lambda kv: int(kv[0])))
+
+
+def _batch_measure(wins, iters, pair_rate, warmup, steps):
+    """One CUDA graph over `wins`: windows/s from the median batch wall time,
+    per-window latency p50/p99 from the graph's own events, the same windows
+    one after another (em_step each), the dense-scoring pairs (every window's
+    scoring log) over `pair_rate` as the scoring-only lower bound, and the
+    median over windows of the mean translation error. Destroys the windows."""
+    import torch
+
+    from paper_2104_06789_gb300 import voldor
+    stream = torch.cuda.Stream()
     batch = voldor.Batch([g for g, _, _ in wins], iters)
     lat, walls = [], []
     for rep in range(warmup + steps):
@@ -788,16 +729,36 @@ def batch_summary(iters, pair_rate, warmup=2, steps=3, n=64, S=4096):
         errs.append(float(np.mean(np.linalg.norm(P[:, :3, 3] - b.poses[:T, :3, 3], axis=1))))
         g.destroy()
     wall = float(np.median(walls))
+    n = len(wins)
     units = sum(b.W * b.H * T * iters for _, b, T in wins)
-    return {"workload": f"{n} windows, resolutions uniform over 320x240 / 640x480 / 1242x375, T uniform in [3, 8]",
-            "hyps_per_frame": S, "tile_shape": "autotuned per window", "shapes": shapes, "em_iters": iters,
-            "windows_per_s": n / (wall / 1e3), "ms_per_batch": wall,
+    return {"windows_per_s": n / (wall / 1e3), "ms_per_batch": wall,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "mpixel_frame_per_s": units / (wall / 1e3) / 1e6,
             "sequential_ms": float(np.median(seq)), "speedup_vs_sequential": float(np.median(seq)) / wall,
             "scoring_pairs": pairs, "scoring_bound_ms": pairs / pair_rate * 1e3 if pair_rate else None,
             "scoring_bound_frac": (pairs / pair_rate * 1e3) / wall if pair_rate else None,
             "median_translation_error_m": float(np.median(errs))}
+
+
+def batch_summary(iters, pair_rate, warmup=2, steps=3, n=64, S=4096):
+    """Config 4 inside the default run: n windows of the mixed workload
+    (batch_workload) in one CUDA graph, each window's hypothesis count and
+    dense-scoring tile shape autotuned; beside it the same windows at a fixed
+    S = 4096 with autotuned tile shapes. For each: windows/s, per-window
+    latency p50/p99, the windows one after another, and the time the dense
+    scoring alone needs at the driving window's measured pair rate (full-GPU
+    occupancy), a lower bound for any batching of these windows with this
+    scoring kernel."""
+    from paper_2104_06789_gb300 import tuning
+    wl = batch_workload(n)
+    fixed, fixed_shapes, _ = _batch_windows(wl, S, iters, tune_hyps=False)
+    res_fixed = _batch_measure(fixed, iters, pair_rate, warmup, steps)
+    tuned, shapes, hyps = _batch_windows(wl, S, iters, tune_hyps=True)
+    res = _batch_measure(tuned, iters, pair_rate, warmup, steps)
+    return {"workload": f"{n} windows, resolutions uniform over 320x240 / 640x480 / 1242x375, T uniform in [3, 8]",
+            "hyps_per_frame": f"autotuned per window from {sorted(tuning.default_candidates(S) + [S])}",
+            "autotuned_hyps": hyps, "tile_shape": "autotuned per window", "shapes": shapes, "em_iters": iters,
+            **res, "fixed_S4096": {"shapes": fixed_shapes, **res_fixed}}
 
 
 WEIGHTS = os.path.join(ROOT, "paper_2104_06789_gb300", "weights", "proposal_handheld_1242x375_T8.npy")
