@@ -126,6 +126,12 @@ def _check(st, where, allow=(), handle=None):
     return st
 
 
+def _require_shape(name, a, shape):
+    # the C calls read exactly this many elements from the pointer they get
+    if tuple(a.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(a.shape)}")
+
+
 def _f64(a):
     a = np.ascontiguousarray(a, dtype=np.float64)
     return a, a.ctypes.data_as(C.POINTER(C.c_double))
@@ -204,6 +210,7 @@ class Window:
 
     def bootstrap(self, T1):
         T1, p = _f64(T1)
+        _require_shape("T1", T1, (4, 4))
         _check(lib().voldor_bootstrap(self._h, BOOT_GIVEN_POSE, p), "voldor_bootstrap", handle=self._h)
 
     def bootstrap_epipolar(self, n_samples=512, baseline=1.0):
@@ -255,14 +262,17 @@ class Window:
     def set_state(self, poses=None, depth=None, rigidness=None, iteration=0):
         keep = []
 
-        def arg(a, conv):
+        def arg(a, conv, name, shape):
             if a is None:
                 return None
             a, p = conv(a)
+            _require_shape(name, a, shape)
             keep.append(a)
             return p
 
-        _check(lib().voldor_set_state(self._h, arg(poses, _f64), arg(depth, _f32), arg(rigidness, _f32),
+        _check(lib().voldor_set_state(self._h, arg(poses, _f64, "poses", (self.T, 4, 4)),
+                                      arg(depth, _f32, "depth", (self.H, self.W)),
+                                      arg(rigidness, _f32, "rigidness", (self.T, self.H, self.W)),
                                       int(iteration)), "voldor_set_state", handle=self._h)
 
     def pose_update(self, k, t):
@@ -272,6 +282,8 @@ class Window:
         R, pR = _f64(R)
         tv, pt = _f64(tv)
         n = R.shape[0]
+        _require_shape("R", R, (n, 3, 3))
+        _require_shape("tv", tv, (n, 3))
         L = np.zeros(n)
         _check(lib().voldor_score_hypotheses(self._h, int(t), n, pR, pt, L.ctypes.data_as(C.POINTER(C.c_double))),
                "voldor_score_hypotheses", handle=self._h)

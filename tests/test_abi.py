@@ -95,3 +95,14 @@ def test_net_arguments_are_checked_on_the_host(vd):
     assert L.voldor_bootstrap_epipolar(None, 64, 1.0, None) == vd.ERR_INVALID_ARG
     assert L.voldor_ground_scale(None, 1.65, 0.17, 0, None) == vd.ERR_INVALID_ARG
     L.voldor_net_destroy(None)
+
+
+def test_binding_checks_the_shapes_the_c_calls_read(vd):
+    """The C calls that take host arrays read a size implied by the window
+    (T x 4 x 4 poses, H x W depth, n x 3 x 3 rotations ...): the binding
+    rejects arrays of any other shape before the call."""
+    import numpy as np
+    vd._require_shape("T1", np.eye(4), (4, 4))
+    for bad in (np.eye(3), np.zeros(16), np.zeros((2, 4, 4))):
+        with pytest.raises(ValueError):
+            vd._require_shape("T1", bad, (4, 4))
