@@ -148,10 +148,11 @@ voldor_status voldor_bootstrap_epipolar(voldor_ctx* ctx, int n_samples, double b
  * sampling-propagation along directed 1-D chains (Eq. 10, Fig. 5); the
  * unsmoothed W update. Iteration k uses sweep direction
  * [left->right, top->bottom, right->left, bottom->top][k mod 4] and smoothing
- * along rows for even k mod 4, columns otherwise. Asynchronous on the
- * context's stream except when it returns DEGENERATE or TIMEOUT, which it
- * learns by synchronising at the end. Errors: NOT_BOOTSTRAPPED, CUDA,
- * DEGENERATE (state stays valid), TIMEOUT. */
+ * along rows for even k mod 4, columns otherwise. The iterations run as one
+ * CUDA graph on the context's stream; the call then synchronises that stream
+ * to read the device status word, from which it learns DEGENERATE and
+ * TIMEOUT. Errors: NOT_BOOTSTRAPPED, CUDA, DEGENERATE (state stays valid),
+ * TIMEOUT. */
 voldor_status voldor_em_step(voldor_ctx* ctx, int n_iters);
 
 /* Copies the outputs into caller-owned host buffers and synchronises.
