@@ -98,15 +98,19 @@ void voldor_default_params(voldor_params* p);
  *                   otherwise. Copied on `cuda_stream` (a cudaStream_t or NULL).
  *  params:          NULL = voldor_default_params().
  * Errors: INVALID_ARG (width or height < 2 or > 4096, T < 1 or > 16, non-finite or
- * non-positive focal lengths, invalid params), OOM, CUDA. *out is NULL on
- * error. */
+ * non-positive focal lengths, invalid params, a non-finite flow or a flow
+ * vector longer than 16384 px: four times the largest image side; the Fisk
+ * model's outlier density (Eq. 7, with alpha = a1 e^{a2 |v|} of Eq. 5) leaves
+ * FP32's normal range just beyond it), OOM, CUDA. *out is NULL on error. */
 voldor_status voldor_init_window(voldor_ctx** out, int width, int height, int T,
                                  const voldor_intrinsics* K, const voldor_params* params,
                                  const void* flows, int flow_dtype, int flows_on_device,
                                  void* cuda_stream);
 
 /* Replaces the flow stack of an existing context (same size and dtype), with
- * no allocation. The state is unchanged; call voldor_bootstrap next. */
+ * no allocation. The state is unchanged; call voldor_bootstrap next.
+ * INVALID_ARG for flows voldor_init_window would reject; the context then
+ * holds zero flows and must be bootstrapped again (NOT_BOOTSTRAPPED until). */
 voldor_status voldor_set_flows(voldor_ctx* ctx, const void* flows, int flows_on_device);
 
 /* Bootstrap (Table 1, first three lines): W := 1 everywhere; T_1 := the given

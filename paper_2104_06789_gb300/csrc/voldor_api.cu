@@ -23,7 +23,7 @@ struct voldor_ctx {
     void* arena = nullptr;
     size_t arena_bytes = 0;
     size_t flows_bytes = 0;
-    int* flag_dev = nullptr;          // inside the arena: non-finite counter
+    int* flag_dev = nullptr;          // inside the arena: counter of rejected flow blocks
     bool bootstrapped = false;
     bool poisoned = false;
     bool timing = false;
@@ -177,13 +177,23 @@ size_t layout(voldor_ctx& c, char* base)
     return off;
 }
 
-__global__ void k_count_nonfinite(const void* flows, int f16, size_t n, int* out)
+// Longest flow vector a window may hold: four times the largest image side
+// (a longer flow sends its pixel far outside every image the library
+// accepts). Up to this length the Fisk constants of a pixel stay inside FP32:
+// alpha = a1 e^{a2 |v|} reaches 2^2120 (kept as log2), mu / beta falls to
+// ~4e-39, just below the normal range with 22 significant bits left; near
+// 19,600 px the exponentials of the likelihood overflow and a pixel's
+// likelihood would become inf or NaN.
+constexpr float kMaxFlowPx = 16384.f;
+
+// Counts the blocks that saw a non-finite flow or one longer than kMaxFlowPx.
+__global__ void k_count_bad_flows(const void* flows, int f16, size_t n, int* out)
 {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     int bad = 0;
     for (; i < n; i += (size_t)gridDim.x * blockDim.x) {
         float2 v = f16 ? __half22float2(reinterpret_cast<const __half2*>(flows)[i]) : reinterpret_cast<const float2*>(flows)[i];
-        bad |= !(isfinite(v.x) && isfinite(v.y));
+        bad |= !(isfinite(v.x) && isfinite(v.y) && fmaf(v.x, v.x, v.y * v.y) <= kMaxFlowPx * kMaxFlowPx);
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicAdd(out, 1);
 }
@@ -195,13 +205,20 @@ voldor_status upload_flows(voldor_ctx* c, const void* flows, int on_device)
         return kCuda;
     if (!cuda_ok(c, cudaMemsetAsync(c->flag_dev, 0, 4, c->stream))) return kCuda;
     const size_t n = (size_t)c->T * c->N;
-    k_count_nonfinite<<<304, 256, 0, c->stream>>>(c->ds.flows, c->flow_dtype == VOLDOR_FLOW_F16, n, c->flag_dev);
+    k_count_bad_flows<<<304, 256, 0, c->stream>>>(c->ds.flows, c->flow_dtype == VOLDOR_FLOW_F16, n, c->flag_dev);
     c->launches += 1;
     if (!launched(c)) return kCuda;
     int bad = 0;
     if (!cuda_ok(c, cudaMemcpyAsync(&bad, c->flag_dev, 4, cudaMemcpyDeviceToHost, c->stream))) return kCuda;
     if (!cuda_ok(c, cudaStreamSynchronize(c->stream))) return kCuda;
-    if (bad) return VOLDOR_ERR_INVALID_ARG;
+    if (bad) {
+        // the context keeps no flow it rejects: zero flows, and the state must
+        // be bootstrapped again before the next iteration
+        if (!cuda_ok(c, cudaMemsetAsync((void*)c->ds.flows, 0, c->flows_bytes, c->stream))) return kCuda;
+        if (!cuda_ok(c, cudaStreamSynchronize(c->stream))) return kCuda;
+        c->bootstrapped = false;
+        return VOLDOR_ERR_INVALID_ARG;
+    }
     return VOLDOR_OK;
 }
 

@@ -53,3 +53,34 @@ def f32_hypotheses(rng, R0, t0, n, rot=0.02, trans=0.02):
         Rs.append(np.eye(3) + E)
         ts.append(t.astype(np.float32).astype(np.float64))
     return np.array(Rs), np.array(ts)
+
+
+def tie_runs(ow, k, q, th0, lab_ref, lab_gpu, margin=1e-5):
+    """Pixels whose sweep decision FP32 scoring cannot be held to: walking each
+    chain in the sweep's order, a pixel where the oracle's best two candidate
+    scores (prev, the carried neighbour, the depth sample) are within `margin`
+    relative (the per-pixel likelihood tolerance) starts a tie, and the pixels
+    after it stay tied while either side carries its neighbour's value (label
+    1); the first pixel where both sides take their own value ends it. Every
+    other pixel's label and depth must equal the oracle's."""
+    H, W = th0.shape
+    rows = k % 2 == 0
+    n_ch, ln = (H, W) if rows else (W, H)
+    tied = np.zeros((H, W), bool)
+    for c in range(n_ch):
+        carried, run = None, False
+        for i in range(ln):
+            x, y = [(i, c), (c, i), (W - 1 - i, c), (c, H - 1 - i)][k % 4]
+            j = y * W + x
+            sc = [ow.mie_score(q, j, float(th0[y, x])), ow.mie_score(q, j, ow.depth_sample(k, j))]
+            if carried is not None:
+                sc.append(ow.mie_score(q, j, carried))
+            sc = sorted(sc, reverse=True)
+            tie = len(sc) > 1 and sc[0] - sc[1] <= margin * abs(sc[0])
+            if tie:
+                run = True
+            elif lab_ref[y, x] != 1 and lab_gpu[y, x] != 1:
+                run = False
+            tied[y, x] = run
+            carried = float(ow.theta[y, x])
+    return tied

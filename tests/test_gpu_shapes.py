@@ -8,7 +8,7 @@ Per shape, teacher-forced as in the stage parity tests (both sides get the
 same FP32-representable state): the smoothed rigidness along rows and along
 columns (Eqs. 11-14), the MIE sweep in all four directions (Eq. 10, Fig. 5:
 labels and depths equal to the oracle's at every pixel outside the runs that
-follow a near tie, see _tie_runs; on the strips the depth varies so slowly
+follow a near tie, see helpers.tie_runs; on the strips the depth varies so slowly
 along a chain that candidates often score within 1e-7 of each other, below
 what FP32 candidate scores can order),
 the unsmoothed rigidness (Table 1) and the dense scores of a few hypotheses
@@ -23,7 +23,7 @@ P3P is ill-conditioned and two correct solvers need not agree to 1e-9."""
 import numpy as np
 import pytest
 
-from tests.helpers import f32_hypotheses, f32_state, oracle_window, small_window
+from tests.helpers import f32_hypotheses, f32_state, oracle_window, small_window, tie_runs
 
 pytestmark = pytest.mark.gpu
 
@@ -53,37 +53,6 @@ def _pair(vd, oracle_lib, w, rng, k):
     return g, ow
 
 
-def _tie_runs(ow, k, q, th0, lab_ref, lab_gpu, margin=1e-5):
-    """Pixels whose sweep decision FP32 scoring cannot be held to: walking each
-    chain in the sweep's order, a pixel where the oracle's best two candidate
-    scores (prev, the carried neighbour, the depth sample) are within `margin`
-    relative (the per-pixel likelihood tolerance) starts a tie, and the pixels
-    after it stay tied while either side carries its neighbour's value (label
-    1); the first pixel where both sides take their own value ends it. Every
-    other pixel's label and depth must equal the oracle's."""
-    H, W = th0.shape
-    rows = k % 2 == 0
-    n_ch, ln = (H, W) if rows else (W, H)
-    tied = np.zeros((H, W), bool)
-    for c in range(n_ch):
-        carried, run = None, False
-        for i in range(ln):
-            x, y = [(i, c), (c, i), (W - 1 - i, c), (c, H - 1 - i)][k % 4]
-            j = y * W + x
-            sc = [ow.mie_score(q, j, float(th0[y, x])), ow.mie_score(q, j, ow.depth_sample(k, j))]
-            if carried is not None:
-                sc.append(ow.mie_score(q, j, carried))
-            sc = sorted(sc, reverse=True)
-            tie = len(sc) > 1 and sc[0] - sc[1] <= margin * abs(sc[0])
-            if tie:
-                run = True
-            elif lab_ref[y, x] != 1 and lab_gpu[y, x] != 1:
-                run = False
-            tied[y, x] = run
-            carried = float(ow.theta[y, x])
-    return tied
-
-
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
 def test_stages_on_extreme_shapes(vd, oracle_lib, shape):
     w = _window(shape)
@@ -104,7 +73,7 @@ def test_stages_on_extreme_shapes(vd, oracle_lib, shape):
         _, D_gpu, _ = g.get_pose_depth_rigidness(poses=False, rigidness=False)
         th0 = ow.theta.copy()
         lab_ref = ow.mie_sweep(k, q.astype(np.float64))
-        tied = _tie_runs(ow, k, q.astype(np.float64), th0, lab_ref, lab_gpu)
+        tied = tie_runs(ow, k, q.astype(np.float64), th0, lab_ref, lab_gpu)
         assert tied.mean() <= 0.25, (k, tied.mean())   # most pixels are held to exact agreement
         same = lab_gpu == lab_ref
         assert np.all(same[~tied]), (k, np.argwhere(~same & ~tied)[:5])
