@@ -87,6 +87,44 @@ def test_lambda_is_the_indistinguishable_epe(oracle_lib):
             assert o[8] == pytest.approx(math.log(0.5), abs=1e-12)
 
 
+def test_mie_term_at_long_flows_matches_scipy(oracle_lib):
+    """Past |v_ob| = 454.5 px the shape B = b1 |v_ob| + b2 of Eq. 6 would be
+    non-positive; the oracle floors it at beta_min (reading 3) while the scale
+    alpha = a1 e^{a2 |v_ob|} of Eq. 5 keeps growing. At flows of 500-6000 px
+    the per-(t, j) MIE term log rho/(rho + mu) must equal the one scipy's Fisk
+    density gives with that beta and alpha, the residual and lambda^2 |v|^2
+    (Eq. 7) clamped as the oracle clamps them."""
+    from scipy import stats
+    from tests.helpers import small_window
+    w = small_window(seed=1000, W=64, H=48, f=48.0, T=2)
+    rng = np.random.default_rng(5)
+    fl = w.flows.astype(np.float64).copy()
+    mag = rng.uniform(500.0, 6000.0, size=fl.shape[:3])
+    ang = rng.uniform(0.0, 2.0 * np.pi, size=fl.shape[:3])
+    fl[..., 0], fl[..., 1] = mag * np.cos(ang), mag * np.sin(ang)
+    ow = oracle_lib.OracleWindow(fl, w.K)
+    ow.poses[:] = w.poses
+    p = oracle_lib.PAPER_DEFAULTS
+    checked = 0
+    for _ in range(200):
+        t = int(rng.integers(1, w.T + 1))
+        j = int(rng.integers(0, w.W * w.H))
+        depth = float(w.depth0.flat[j] * rng.uniform(0.8, 1.2))
+        v, diag = ow.frame_eval(t, j, depth)
+        if v < 2:
+            continue
+        res, vob = diag[0:2], diag[4:6]
+        n = np.hypot(*vob)                 # bilinear between long flows: mostly, not always, > 454.5
+        beta = max(p["b1"] * n + p["b2"], p["beta_min"])
+        alpha = p["a1"] * np.exp(p["a2"] * n)
+        x = np.clip(res @ res, p["x_min"], p["x_max"])
+        x_mu = np.clip(p["lambda_"] ** 2 * n * n, p["x_min"], p["x_max"])
+        ref = -np.logaddexp(0.0, stats.fisk.logpdf(x_mu, beta, scale=alpha) - stats.fisk.logpdf(x, beta, scale=alpha))
+        assert ow.frame_crit(t, j, depth) == pytest.approx(ref, rel=1e-9, abs=1e-12)
+        checked += n > 454.5
+    assert checked > 20
+
+
 # ---------------------------------------------------------------------------
 # Geometry, bilinear sampling, triangulation
 # ---------------------------------------------------------------------------
