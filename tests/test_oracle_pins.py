@@ -491,6 +491,39 @@ def test_dense_score_peaks_at_true_pose(oracle_lib):
     assert np.allclose(L2 * 2, L, rtol=1e-14)
 
 
+def test_dense_score_is_the_weighted_sum_of_the_pinned_terms(oracle_lib):
+    """L_h (the Eq. 10 criterion with the pose as the free variable) sums, over
+    the pixels whose pi_{t-1} is valid, the unsmoothed W_t^j times the
+    per-(t, j) term that the Fisk pins check against scipy, evaluated at T_t = h;
+    pixels without a correspondence add nothing and a point behind camera t
+    adds log 1/2. Checked on a noisy window with random W against the per-term
+    function (frame_crit) with the hypothesis set as the frame's pose."""
+    from paper_2104_06789_gb300 import synthetic as sy
+    w = sy.small_planes(W=24, H=18, f=18.0, T=3, seed=1003)
+    ow = oracle_lib.OracleWindow(w.flows, w.K, S=8)
+    rng = np.random.default_rng(9)
+    ow.theta[:] = w.depth0 * rng.uniform(0.8, 1.2, size=w.depth0.shape)
+    ow.wmap[:] = rng.uniform(0.0, 1.0, size=ow.wmap.shape)
+    ow.poses[:] = w.poses
+    t = 3
+    R0, t0 = w.poses[t - 1][:3, :3], w.poses[t - 1][:3, 3]
+    hyps = [(R0, t0), (_random_rotation(rng, 0.05) @ R0, t0 + rng.normal(size=3) * 0.05),
+            (R0, t0 + np.array([0.0, 0.0, -30.0]))]             # the last puts points behind camera t
+    L = ow.score(t, np.array([h[0] for h in hyps]), np.array([h[1] for h in hyps]))
+    behind = 0
+    for (R, tv), Lh in zip(hyps, L):
+        ow.poses[t - 1][:3, :3], ow.poses[t - 1][:3, 3] = R, tv
+        ref = 0.0
+        for j in range(w.W * w.H):
+            v, _ = ow.frame_eval(t, j, float(ow.theta.flat[j]))
+            if v >= 1:                                            # pi_{t-1} valid
+                c = ow.frame_crit(t, j, float(ow.theta.flat[j]))
+                behind += v == 1 and c == pytest.approx(math.log(0.5))
+                ref += ow.wmap[t - 1].flat[j] * c
+        assert Lh == pytest.approx(ref, rel=1e-12)
+    assert behind > 0
+
+
 def test_mie_sweep_monotone_and_fixed_point(oracle_lib):
     flows, K, poses, depth = fronto_parallel_window(T=3)
     ow = oracle_lib.OracleWindow(flows, K, S=8, inv_depth_min=0.05, inv_depth_max=1.0)
