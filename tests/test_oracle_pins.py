@@ -524,6 +524,45 @@ def test_dense_score_is_the_weighted_sum_of_the_pinned_terms(oracle_lib):
     assert behind > 0
 
 
+def test_rigidness_update_is_the_per_pixel_posterior(oracle_lib):
+    """The unsmoothed rigidness update (Table 1, last line; reading 11) sets
+    every W_t^j to the posterior rho/(rho + mu) of the rigid hypothesis under
+    a uniform prior, at the current depth and poses: rho the Fisk density of
+    the squared residual, mu that of lambda^2 |v_ob|^2 (Eqs. 3-7), from scipy;
+    1/2 where the pixel has no observation at pi_{t-1} or lies behind camera
+    t. Every (t, j) of a noisy window with a perturbed depth."""
+    from scipy import stats
+    from paper_2104_06789_gb300 import synthetic as sy
+    w = sy.small_planes(W=24, H=18, f=18.0, T=3, seed=1004)
+    ow = oracle_lib.OracleWindow(w.flows, w.K, S=8)
+    rng = np.random.default_rng(11)
+    ow.theta[:] = w.depth0 * rng.uniform(0.9, 1.1, size=w.depth0.shape)
+    ow.poses[:] = w.poses
+    ow.wmap[:] = rng.uniform(0.0, 1.0, size=ow.wmap.shape)      # overwritten by the update
+    expect = np.zeros_like(ow.wmap)
+    p = oracle_lib.PAPER_DEFAULTS
+    n_none = 0
+    for t in range(1, w.T + 1):
+        for j in range(w.W * w.H):
+            v, diag = ow.frame_eval(t, j, float(ow.theta.flat[j]))
+            if v < 2:
+                expect[t - 1].flat[j] = 0.5
+                n_none += 1
+                continue
+            res, vob = diag[0:2], diag[4:6]
+            n = np.hypot(*vob)
+            alpha = p["a1"] * np.exp(p["a2"] * n)
+            beta = max(p["b1"] * n + p["b2"], p["beta_min"])
+            x = np.clip(res @ res, p["x_min"], p["x_max"])
+            x_mu = np.clip(p["lambda_"] ** 2 * n * n, p["x_min"], p["x_max"])
+            lr = stats.fisk.logpdf(x, beta, scale=alpha)
+            lm = stats.fisk.logpdf(x_mu, beta, scale=alpha)
+            expect[t - 1].flat[j] = 1.0 / (1.0 + np.exp(lm - lr))
+    ow.rigidness()
+    assert np.allclose(ow.wmap, expect, rtol=1e-10, atol=1e-14)
+    assert 0 < n_none < expect.size                             # both conventions occur
+
+
 def test_mie_sweep_monotone_and_fixed_point(oracle_lib):
     flows, K, poses, depth = fronto_parallel_window(T=3)
     ow = oracle_lib.OracleWindow(flows, K, S=8, inv_depth_min=0.05, inv_depth_max=1.0)
