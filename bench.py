@@ -419,6 +419,16 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def _guarded(fn, *a):
+    """fn(*a), or {"error": ...} if it raises (printed to stderr)."""
+    try:
+        return fn(*a)
+    except Exception as e:                    # noqa: BLE001 -- reported, not swallowed
+        import traceback
+        traceback.print_exc(file=sys.stderr)
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
 def run_ours(args):
     import torch
 
@@ -569,8 +579,10 @@ def run_ours(args):
         err = error_vs_oracle(win, w, flows16, params, variant_overrides(args))
     batch = learned_cmp = None
     if world == 1 and not args.no_extra and (args.criterion, args.residual) == ("mie", "fisk"):
-        batch = batch_summary(args.iters, pair_rate)
-        learned_cmp = learned_summary(args.iters)
+        # measured after the timed region: a failure here is reported in its
+        # own object and does not take the headline measurement with it
+        batch = _guarded(batch_summary, args.iters, pair_rate)
+        learned_cmp = _guarded(learned_summary, args.iters)
 
     cfg = config_dict(w, args, world)
     if hyps_scored is not None:
