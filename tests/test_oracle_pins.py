@@ -380,6 +380,26 @@ def test_forward_backward_brute_force(oracle_lib, L):
         assert np.abs(q - _brute_marginals(w, gamma)).max() < 1e-12
 
 
+@pytest.mark.parametrize("axis", [0, 1])
+def test_smoothing_runs_independent_chains_along_rows_or_columns(oracle_lib, axis):
+    """The E-step smooths each frame's emissions on 1-D chains (Eqs. 11-14):
+    along image rows for axis 0 (horizontal sweeps) and columns for axis 1,
+    frames independent (readings 8, 10). Every chain of a 5 x 4 window with
+    T = 2 against brute-force enumeration of its 2^L labelings."""
+    from paper_2104_06789_gb300 import synthetic as sy
+    w = sy.small_planes(W=5, H=4, f=4.0, T=2, seed=1006)
+    ow = oracle_lib.OracleWindow(w.flows, w.K, S=8)
+    rng = np.random.default_rng(17 + axis)
+    emis = rng.uniform(0.01, 0.99, size=(w.T, w.H, w.W))
+    q = ow.smooth(axis, emis)
+    g = oracle_lib.PAPER_DEFAULTS["gamma"]
+    for t in range(w.T):
+        chains = emis[t] if axis == 0 else emis[t].T
+        out = q[t] if axis == 0 else q[t].T
+        for c in range(chains.shape[0]):
+            assert np.abs(out[c] - _brute_marginals(chains[c], g)).max() < 1e-12
+
+
 def test_forward_backward_special_cases(oracle_lib):
     rng = np.random.default_rng(9)
     w = rng.uniform(0.01, 0.99, size=50)
