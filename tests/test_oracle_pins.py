@@ -201,6 +201,22 @@ def test_triangulation_without_parallax_goes_far(oracle_lib):
     assert np.allclose(ow.theta, 1 / 0.05)
 
 
+def test_triangulation_clamps_to_the_depth_range(oracle_lib):
+    """Reading 19: the bootstrap's inverse depth is clamped to [inv_min,
+    inv_max]. On a noiseless window, whose triangulation is exact (the pin
+    above), a range set inside the scene's puts the nearest pixels exactly on
+    1/inv_max, the farthest on 1/inv_min, and leaves every other depth exact."""
+    from paper_2104_06789_gb300 import synthetic as sy
+    w = sy.small_planes(noise=False, nonrigid=False)
+    inv = 1.0 / w.depth0
+    lo, hi = 0.07, 0.3                        # the scene spans inverse depths 0.05 (background) to 0.48
+    ow = oracle_lib.OracleWindow(w.flows, w.K, S=8, inv_depth_min=lo, inv_depth_max=hi)
+    ow.bootstrap(w.poses[0])
+    expect = 1.0 / np.clip(inv, lo, hi)
+    assert np.max(np.abs(ow.theta - expect) / expect) < 1e-10
+    assert np.any(inv > hi) and np.any(inv < lo)
+
+
 # ---------------------------------------------------------------------------
 # P3P (Eq. 17)
 # ---------------------------------------------------------------------------
