@@ -106,3 +106,15 @@ def test_binding_checks_the_shapes_the_c_calls_read(vd):
     for bad in (np.eye(3), np.zeros(16), np.zeros((2, 4, 4))):
         with pytest.raises(ValueError):
             vd._require_shape("T1", bad, (4, 4))
+
+
+def test_header_is_plain_c():
+    """include/voldor.h is consumable from C (C99) as well as C++."""
+    import shutil
+    import subprocess
+    hdr = os.path.join(ROOT, "include", "voldor.h")
+    for cc, args in (("gcc", ["-std=c99", "-x", "c"]), ("g++", ["-std=c++11", "-x", "c++"])):
+        if shutil.which(cc) is None:
+            pytest.skip(f"{cc} not found")
+        r = subprocess.run([cc, "-fsyntax-only", "-Wall", "-Werror", *args, hdr], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
